@@ -1,0 +1,1151 @@
+/*
+ * Plain FP64 CPU oracle of the explicit Eulerian diffuse-interface step of
+ * Wallis, Barton & Nikiforakis (arXiv 2210.04037).  TEST INFRASTRUCTURE ONLY:
+ * it is loaded by tests/, by __graft_entry__.smoke() and by the cpu_baseline
+ * and reference legs of bench.py, never by the product path.  It shares no
+ * code with the CUDA library.
+ *
+ * The paper states the governing system (Sec. 2.1), the closures (Sec. 2.1.1,
+ * 2.1.2), the damage laws (Sec. 2.1.1, Sec. 4.3), the perturbation field
+ * (Sec. 2.1.3, 3.2) and RK4 for damage (Sec. 3.1), and defers the hyperbolic
+ * solver, the mixture rules and the plastic update to earlier papers (start
+ * of Sec. 3).  The readings used for those (R1..R26) are written out beside
+ * each routine; every step is done plainly, one cell or one face at a time,
+ * in the order the method takes them:
+ *
+ *   one time step = dt from the CFL rule (R-CFL)
+ *                   -> sweep x -> sweep y -> sweep z  (dimensional split, R8)
+ *                   -> per-cell sources: phi0(X) lookup, plastic return,
+ *                      RK4 damage (Godunov split, R12)
+ *   one sweep     = primitive recovery -> van Leer slopes on primitives (R9)
+ *                   -> MUSCL-Hancock half step -> HLLC flux (R11)
+ *                   -> conservative update + non-conservative terms
+ */
+#include "oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define MAXF 32
+#define LDIM 3
+
+struct or_grid {
+  int dim, nmat, nhist, nF, nfield;
+  long n[3], ncell;
+  double lo[3], hi[3], dx[3];
+  int bc[3][2];
+  or_material mat[OR_MAXMAT];
+  int hslot[OR_MAXMAT]; /* history slot of material l, or -1 */
+  int Fidx[9];          /* row-major index (3i+j) of each stored Fbar comp */
+  int o_phi, o_arho, o_mom, o_E, o_F, o_hist, o_X;
+  double *U, *V; /* conserved state and sweep output, [nfield][ncell] */
+  float *phi0;
+  long pn[3];
+  double plo[3], ph[3];
+  double t, dt_last, smax;
+  long steps, bad_cell;
+};
+
+/* Derived quantities of one state that the flux and the Riemann solver use. */
+typedef struct {
+  double u[3];     /* velocity */
+  double sig[9];   /* Cauchy stress, tension positive (R5) */
+  double F[9];     /* full deformation tensor Fbar */
+  double rho, p, cL;
+  double G;        /* mixture shear modulus */
+} aux_t;
+
+/* ------------------------------------------------------------------------ */
+/* Closures: one material (Sec. 2.1.1 and 2.1.2, Romenskii forms)           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Reference curve of one material at phasic density rho, damage factor
+ * psi = 1 - D and shear invariant J2 = tr(devH devH^T).
+ *   e_ref = e_c + e_s,  p_ref = rho^2 d e_ref / d rho,  dp_ref/drho,
+ *   G and the Grueneisen coefficient Gamma.
+ * Romenskii cold energy, printed with 1/rho (Eq. Romenskii, R3):
+ *   e_c = psi K0 / (2 rho alpha^2) (eta^alpha - 1)^2,  eta = rho/rho0,
+ * degraded by (1-D) (Eq. coldCompressionDegradation); shear modulus
+ *   G = psi G0 eta^(beta+1)  (Romenskii G, degraded linearly, Sec. 2.1.1);
+ * shear energy e_s = G J^2 / rho (Eq. shearEnergy); theta = eta^Gamma0 gives
+ * a constant Gamma = Gamma0, hence the Mie-Grueneisen form
+ *   p = p_ref + rho Gamma (e - e_ref).
+ * Ideal gas is the G = 0 case with e_ref = p_ref = 0, Gamma = gamma - 1.
+ */
+void or_thermo(const or_material* m, double rho, double psi, double J2,
+               double* out) {
+  if (m->eos == 0) {
+    out[0] = 0.0;
+    out[1] = 0.0;
+    out[2] = 0.0;
+    out[3] = 0.0;
+    out[4] = m->gamma_gas - 1.0;
+    return;
+  }
+  const double a = m->alpha;
+  const double eta = rho / m->rho0;
+  const double ea = pow(eta, a);
+  const double q = ea - 1.0;
+  /* cold energy and its pressure p_c = rho^2 de_c/drho */
+  const double ec = psi * m->K0 / (2.0 * rho * a * a) * (q * q);
+  const double pc = psi * m->K0 / (2.0 * a * a) * (2.0 * a * q * ea - q * q);
+  /* d p_c / d rho = psi K0 eta^(a-1) ((2a-1) eta^a + 1 - a) / (a rho0) */
+  const double dpc = psi * m->K0 * pow(eta, a - 1.0) *
+                     ((2.0 * a - 1.0) * ea + (1.0 - a)) / (a * m->rho0);
+  /* shear part: G(rho), e_s = G J2/rho, p_s = rho^2 de_s/drho = beta G J2 */
+  const double G = psi * m->G0 * pow(eta, m->beta + 1.0);
+  const double es = G * J2 / rho;
+  const double ps = m->beta * G * J2;
+  const double dps = m->beta * (m->beta + 1.0) * G * J2 / rho;
+  out[0] = ec + es;
+  out[1] = pc + ps;
+  out[2] = dpc + dps;
+  out[3] = G;
+  out[4] = m->Gamma0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hencky strain devH = dev(ln Vbar) = dev(1/2 ln(Fbar Fbar^T)) (Sec. 2.1.1) */
+/* by the cyclic Jacobi method (symmetric Schur rotations).                 */
+/* ------------------------------------------------------------------------ */
+
+static void jacobi_rotate(double a[9], double Q[9], int p, int q) {
+  const double apq = a[3 * p + q];
+  if (apq == 0.0) return;
+  const double app = a[3 * p + p], aqq = a[3 * q + q];
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+  if (theta < 0.0) t = -t;
+  const double c = 1.0 / sqrt(t * t + 1.0);
+  const double s = t * c;
+  a[3 * p + p] = app - t * apq;
+  a[3 * q + q] = aqq + t * apq;
+  a[3 * p + q] = 0.0;
+  a[3 * q + p] = 0.0;
+  const int r = 3 - p - q;
+  const double arp = a[3 * r + p], arq = a[3 * r + q];
+  a[3 * r + p] = a[3 * p + r] = c * arp - s * arq;
+  a[3 * r + q] = a[3 * q + r] = s * arp + c * arq;
+  for (int k = 0; k < 3; ++k) {
+    const double qp = Q[3 * k + p], qq = Q[3 * k + q];
+    Q[3 * k + p] = c * qp - s * qq;
+    Q[3 * k + q] = s * qp + c * qq;
+  }
+}
+
+/* Eigen-decomposition A = Q diag(lam) Q^T of a symmetric 3x3 matrix. */
+static void jacobi3(const double A[9], double lam[3], double Q[9]) {
+  double a[9];
+  memcpy(a, A, sizeof a);
+  for (int k = 0; k < 9; ++k) Q[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+    const double dd = a[0] * a[0] + a[4] * a[4] + a[8] * a[8];
+    if (off <= 1e-32 * dd) break;
+    jacobi_rotate(a, Q, 0, 1);
+    jacobi_rotate(a, Q, 0, 2);
+    jacobi_rotate(a, Q, 1, 2);
+  }
+  lam[0] = a[0];
+  lam[1] = a[4];
+  lam[2] = a[8];
+}
+
+/* devH and its eigen-pairs: h = dev eigenvalues of 1/2 ln b, b = F F^T. */
+static int hencky_eig(const double F[9], double devH[9], double h[3],
+                      double Q[9], double lam[3]) {
+  double b[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      const double s = F[3 * i + 0] * F[3 * j + 0] +
+                       F[3 * i + 1] * F[3 * j + 1] +
+                       F[3 * i + 2] * F[3 * j + 2];
+      b[3 * i + j] = s;
+      b[3 * j + i] = s;
+    }
+  jacobi3(b, lam, Q);
+  for (int k = 0; k < 3; ++k)
+    if (!(lam[k] > 0.0) || !isfinite(lam[k])) return -1;
+  for (int k = 0; k < 3; ++k) h[k] = 0.5 * log(lam[k]);
+  const double tr = (h[0] + h[1] + h[2]) / 3.0;
+  for (int k = 0; k < 3; ++k) h[k] -= tr;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      devH[3 * i + j] = Q[3 * i + 0] * h[0] * Q[3 * j + 0] +
+                        Q[3 * i + 1] * h[1] * Q[3 * j + 1] +
+                        Q[3 * i + 2] * h[2] * Q[3 * j + 2];
+  return 0;
+}
+
+int or_hencky(const double F[9], double devH[9], double lam[3], double Q[9]) {
+  double h[3];
+  return hencky_eig(F, devH, h, Q, lam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field layout                                                              */
+/* ------------------------------------------------------------------------ */
+
+static int is_damaged(const or_material* m) { return m->damage != 0; }
+
+/* Full local views of a stored state vector (inactive components: 0 / I). */
+static void full_F(const or_grid* g, const double* w, double F[9]) {
+  for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  for (int c = 0; c < g->nF; ++c) F[g->Fidx[c]] = w[g->o_F + c];
+}
+
+static void vol_fracs(const or_grid* g, const double* w, double phi[]) {
+  double s = 0.0;
+  for (int l = 0; l + 1 < g->nmat; ++l) {
+    phi[l] = w[g->o_phi + l];
+    s += phi[l];
+  }
+  phi[g->nmat - 1] = 1.0 - s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mixture (R7: Allaire isobaric closure, single Fbar, Sec. 2.1 and 2.1.2)  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double th[OR_MAXMAT][5];
+  double xi, Gmix;
+  double devH[9], J2;
+} mix_t;
+
+static int mixture(const or_grid* g, const double* phi, const double* rho_l,
+                   const double* Dl, const double F[9], mix_t* mx) {
+  double h[3], Q[9], lam[3];
+  if (hencky_eig(F, mx->devH, h, Q, lam) != 0) return -1;
+  mx->J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+  mx->xi = 0.0;
+  mx->Gmix = 0.0;
+  for (int l = 0; l < g->nmat; ++l) {
+    const double psi = is_damaged(&g->mat[l]) ? 1.0 - Dl[l] : 1.0;
+    or_thermo(&g->mat[l], rho_l[l], psi, mx->J2, mx->th[l]);
+    mx->xi += phi[l] / mx->th[l][4];
+    mx->Gmix += phi[l] * mx->th[l][3];
+  }
+  return 0;
+}
+
+/* Stress sigma = -p I + 2 G dev(H) (R5) and longitudinal sound speed (R6). */
+static int finish_aux(const or_grid* g, const double* phi, const double* rho_l,
+                      const double* arho, const mix_t* mx, aux_t* ax) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      ax->sig[3 * i + j] =
+          (i == j ? -ax->p : 0.0) + 2.0 * mx->Gmix * mx->devH[3 * i + j];
+  /* frozen mixture sound speed: xi c^2 = sum_l y_l xi_l c_l^2 */
+  double s = 0.0;
+  for (int l = 0; l < g->nmat; ++l) {
+    const double Gam = mx->th[l][4];
+    const double cl2 = mx->th[l][2] + (Gam + 1.0) * (ax->p - mx->th[l][1]) /
+                                          rho_l[l];
+    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;
+  }
+  (void)phi;
+  const double c2 = s / mx->xi;
+  ax->G = mx->Gmix;
+  const double cL2 = c2 + (4.0 / 3.0) * mx->Gmix / ax->rho;
+  if (!(cL2 > 0.0) || !isfinite(cL2)) return -1;
+  ax->cL = sqrt(cL2);
+  return 0;
+}
+
+/* Primitive W -> conserved U (+ derived quantities). Returns 0 if valid. */
+static int w2u(const or_grid* g, const double* w, double* u, aux_t* ax) {
+  double phi[OR_MAXMAT], rho_l[OR_MAXMAT], arho[OR_MAXMAT], Dl[OR_MAXMAT];
+  vol_fracs(g, w, phi);
+  ax->rho = 0.0;
+  for (int l = 0; l < g->nmat; ++l) {
+    if (!(phi[l] > 0.0)) return -1;
+    rho_l[l] = w[g->o_arho + l];
+    if (!(rho_l[l] > 0.0)) return -1;
+    arho[l] = phi[l] * rho_l[l];
+    ax->rho += arho[l];
+    Dl[l] = g->hslot[l] >= 0 ? w[g->o_hist + 2 * g->hslot[l] + 1] : 0.0;
+  }
+  for (int k = 0; k < 3; ++k) ax->u[k] = k < g->dim ? w[g->o_mom + k] : 0.0;
+  ax->p = w[g->o_E];
+  full_F(g, w, ax->F);
+  mix_t mx;
+  if (mixture(g, phi, rho_l, Dl, ax->F, &mx) != 0) return -1;
+  /* rho e = sum_l phi_l rho_l e_l with p = p_ref,l + rho_l Gamma_l (e_l - e_ref,l) */
+  double rhoe = 0.0;
+  for (int l = 0; l < g->nmat; ++l)
+    rhoe += arho[l] * mx.th[l][0] + phi[l] * (ax->p - mx.th[l][1]) / mx.th[l][4];
+  const double ke = 0.5 * ax->rho *
+                    (ax->u[0] * ax->u[0] + ax->u[1] * ax->u[1] + ax->u[2] * ax->u[2]);
+  for (int l = 0; l + 1 < g->nmat; ++l) u[g->o_phi + l] = phi[l];
+  for (int l = 0; l < g->nmat; ++l) u[g->o_arho + l] = arho[l];
+  for (int k = 0; k < g->dim; ++k) u[g->o_mom + k] = ax->rho * ax->u[k];
+  u[g->o_E] = rhoe + ke;
+  for (int c = 0; c < g->nF; ++c) u[g->o_F + c] = w[g->o_F + c];
+  for (int l = 0; l < g->nmat; ++l) {
+    const int h = g->hslot[l];
+    if (h < 0) continue;
+    u[g->o_hist + 2 * h] = arho[l] * w[g->o_hist + 2 * h];
+    u[g->o_hist + 2 * h + 1] = arho[l] * w[g->o_hist + 2 * h + 1];
+  }
+  for (int k = 0; k < g->dim; ++k) u[g->o_X + k] = w[g->o_X + k];
+  return finish_aux(g, phi, rho_l, arho, &mx, ax);
+}
+
+/* Conserved U -> primitive W (+ derived quantities). Returns 0 if valid. */
+static int u2w(const or_grid* g, const double* u, double* w, aux_t* ax) {
+  double phi[OR_MAXMAT], rho_l[OR_MAXMAT], arho[OR_MAXMAT], Dl[OR_MAXMAT];
+  vol_fracs(g, u, phi);
+  ax->rho = 0.0;
+  for (int l = 0; l < g->nmat; ++l) {
+    arho[l] = u[g->o_arho + l];
+    if (!(phi[l] > 0.0) || !(arho[l] > 0.0)) return -1;
+    rho_l[l] = arho[l] / phi[l];
+    ax->rho += arho[l];
+  }
+  for (int l = 0; l < g->nmat; ++l) {
+    const int h = g->hslot[l];
+    Dl[l] = 0.0;
+    if (h < 0) continue;
+    w[g->o_hist + 2 * h] = u[g->o_hist + 2 * h] / arho[l];
+    w[g->o_hist + 2 * h + 1] = u[g->o_hist + 2 * h + 1] / arho[l];
+    Dl[l] = w[g->o_hist + 2 * h + 1];
+  }
+  for (int k = 0; k < 3; ++k)
+    ax->u[k] = k < g->dim ? u[g->o_mom + k] / ax->rho : 0.0;
+  full_F(g, u, ax->F);
+  mix_t mx;
+  if (mixture(g, phi, rho_l, Dl, ax->F, &mx) != 0) return -1;
+  const double ke = 0.5 * ax->rho *
+                    (ax->u[0] * ax->u[0] + ax->u[1] * ax->u[1] + ax->u[2] * ax->u[2]);
+  const double rhoe = u[g->o_E] - ke;
+  double num = rhoe;
+  for (int l = 0; l < g->nmat; ++l)
+    num += -arho[l] * mx.th[l][0] + phi[l] * mx.th[l][1] / mx.th[l][4];
+  ax->p = num / mx.xi;
+  for (int l = 0; l + 1 < g->nmat; ++l) w[g->o_phi + l] = phi[l];
+  for (int l = 0; l < g->nmat; ++l) w[g->o_arho + l] = rho_l[l];
+  for (int k = 0; k < g->dim; ++k) w[g->o_mom + k] = ax->u[k];
+  w[g->o_E] = ax->p;
+  for (int c = 0; c < g->nF; ++c) w[g->o_F + c] = u[g->o_F + c];
+  for (int k = 0; k < g->dim; ++k) w[g->o_X + k] = u[g->o_X + k];
+  for (int k = 0; k < g->nfield; ++k)
+    if (!isfinite(w[k]) || !isfinite(u[k])) return -1;
+  return finish_aux(g, phi, rho_l, arho, &mx, ax);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Physical flux in direction d of the system of Sec. 2.1 (G4-G9, G13, R1)  */
+/* ------------------------------------------------------------------------ */
+
+static void phys_flux(const or_grid* g, int d, const double* u,
+                      const aux_t* ax, double* f) {
+  const double ud = ax->u[d];
+  for (int l = 0; l + 1 < g->nmat; ++l) f[g->o_phi + l] = u[g->o_phi + l] * ud;
+  for (int l = 0; l < g->nmat; ++l) f[g->o_arho + l] = u[g->o_arho + l] * ud;
+  for (int k = 0; k < g->dim; ++k)
+    f[g->o_mom + k] = u[g->o_mom + k] * ud - ax->sig[3 * k + d];
+  f[g->o_E] = u[g->o_E] * ud -
+              (ax->sig[3 * d + 0] * ax->u[0] + ax->sig[3 * d + 1] * ax->u[1] +
+               ax->sig[3 * d + 2] * ax->u[2]);
+  for (int c = 0; c < g->nF; ++c) {
+    const int i = g->Fidx[c] / 3, j = g->Fidx[c] % 3;
+    f[g->o_F + c] = (i == d) ? 0.0
+                             : u[g->o_F + c] * ud - ax->F[3 * d + j] * ax->u[i];
+  }
+  for (int k = 0; k < 2 * g->nhist; ++k) f[g->o_hist + k] = u[g->o_hist + k] * ud;
+  for (int k = 0; k < g->dim; ++k) f[g->o_X + k] = u[g->o_X + k] * ud;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Riemann solver (R11), HLLD type for the elastic mixture: Davis outer     */
+/* longitudinal waves S_L, S_R; contact S*; in each star region a shear     */
+/* wave S* -/+ c_s.  Every intermediate state follows from the Rankine-     */
+/* Hugoniot conditions across its wave: across S_K the tangential velocity  */
+/* and traction are unchanged; across the shear waves the normal velocity,  */
+/* normal stress, densities and the row d of Fbar are unchanged; at the     */
+/* contact the normal stress, the tangential velocity and traction are      */
+/* continuous.  With G = 0 it is the HLLC solver.                           */
+/* ------------------------------------------------------------------------ */
+
+static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
+                    const double* UR, const aux_t* aR, double* Fo,
+                    double* uface, double Frow[3]) {
+  const double uL = aL->u[d], uR = aR->u[d];
+  const double a1 = uL - aL->cL, a2 = uR - aR->cL;
+  const double b1 = uL + aL->cL, b2 = uR + aR->cL;
+  const double SL = a1 < a2 ? a1 : a2;
+  const double SR = b1 > b2 ? b1 : b2;
+  const double sL = aL->sig[3 * d + d], sR = aR->sig[3 * d + d];
+  const double rL = aL->rho, rR = aR->rho;
+  const double Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+                    (rL * (SL - uL) - rR * (SR - uR));
+  double FK[MAXF];
+  if (SL >= 0.0 || SR <= 0.0) {
+    const aux_t* aK = SL >= 0.0 ? aL : aR;
+    phys_flux(g, d, SL >= 0.0 ? UL : UR, aK, Fo);
+    *uface = aK->u[d];
+    for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
+    return;
+  }
+  const int left = Ss >= 0.0;
+  const double* UK = left ? UL : UR;
+  const aux_t* aK = left ? aL : aR;
+  const double SK = left ? SL : SR;
+  phys_flux(g, d, UK, aK, FK);
+  const double uK = aK->u[d];
+  for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
+  /* star state of side K */
+  const double chi = (SK - uK) / (SK - Ss);
+  const double rK = aK->rho;
+  double Us[MAXF];
+  for (int l = 0; l + 1 < g->nmat; ++l) Us[g->o_phi + l] = UK[g->o_phi + l] * chi;
+  for (int l = 0; l < g->nmat; ++l) Us[g->o_arho + l] = UK[g->o_arho + l] * chi;
+  for (int k = 0; k < g->dim; ++k)
+    Us[g->o_mom + k] = (k == d) ? rK * chi * Ss : UK[g->o_mom + k] * chi;
+  Us[g->o_E] = chi * (UK[g->o_E] + rK * Ss * (Ss - uK) -
+                      aK->sig[3 * d + d] * (Ss - uK) / (SK - uK));
+  for (int c = 0; c < g->nF; ++c) {
+    const int i = g->Fidx[c] / 3;
+    Us[g->o_F + c] = (i == d) ? UK[g->o_F + c] : UK[g->o_F + c] * chi;
+  }
+  for (int k = 0; k < 2 * g->nhist; ++k) Us[g->o_hist + k] = UK[g->o_hist + k] * chi;
+  for (int k = 0; k < g->dim; ++k) Us[g->o_X + k] = UK[g->o_X + k] * chi;
+  for (int k = 0; k < g->nfield; ++k) Fo[k] = FK[k] + SK * (Us[k] - UK[k]);
+  *uface = uK + SK * (chi - 1.0);
+  /* shear waves: speeds from the star densities, kept inside [S_L, S_R] */
+  const double rsL = rL * ((SL - uL) / (SL - Ss));
+  const double rsR = rR * ((SR - uR) / (SR - Ss));
+  double csL = sqrt(aL->G / rsL), csR = sqrt(aR->G / rsR);
+  if (csL > Ss - SL) csL = Ss - SL;
+  if (csR > SR - Ss) csR = SR - Ss;
+  const double ZL = rsL * csL, ZR = rsR * csR;
+  const double csK = left ? csL : csR;
+  if (!(ZL + ZR > 0.0)) return;
+  if (left ? !(Ss - csL < 0.0) : !(Ss + csR > 0.0)) return;
+  double Uss[MAXF];
+  for (int k = 0; k < g->nfield; ++k) Uss[k] = Us[k];
+  const double sgn = left ? 1.0 : -1.0;
+  const double rsK = left ? rsL : rsR;
+  for (int t = 0; t < g->dim; ++t) {
+    if (t == d) continue;
+    const double uLt = aL->u[t], uRt = aR->u[t];
+    const double tauL = aL->sig[3 * t + d], tauR = aR->sig[3 * t + d];
+    const double uss = (tauR - tauL + ZL * uLt + ZR * uRt) / (ZL + ZR);
+    const double tss = tauL + ZL * (uss - uLt);
+    const double uKt = left ? uLt : uRt, tauK = left ? tauL : tauR;
+    const double du = uss - uKt;
+    Uss[g->o_mom + t] = rsK * uss;
+    for (int c = 0; c < g->nF; ++c) {
+      const int i = g->Fidx[c] / 3, j = g->Fidx[c] % 3;
+      if (i == t) Uss[g->o_F + c] = Us[g->o_F + c] + sgn * aK->F[3 * d + j] * du / csK;
+    }
+    Uss[g->o_E] += sgn * (tss * uss - tauK * uKt) / csK;
+  }
+  const double SSK = left ? Ss - csL : Ss + csR;
+  for (int k = 0; k < g->nfield; ++k) Fo[k] += SSK * (Uss[k] - Us[k]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction: van Leer slopes on primitives (R9), positivity fallback   */
+/* to first order (R10).                                                     */
+/* ------------------------------------------------------------------------ */
+
+static double van_leer(double a, double b) {
+  if (a * b > 0.0) return 2.0 * a * b / (a + b);
+  return 0.0;
+}
+
+/* Non-conservative terms, per unit of 1/dx: phi and X take q_c * du; the
+ * deformation tensor takes 2/3 F_ij du - u_i dF_dj (Eq. for Vbar, R1, R20). */
+static void noncons(const or_grid* g, int d, const double* wc, const aux_t* ac,
+                    double du, const double dFrow[3], double* nc) {
+  for (int k = 0; k < g->nfield; ++k) nc[k] = 0.0;
+  for (int l = 0; l + 1 < g->nmat; ++l) nc[g->o_phi + l] = wc[g->o_phi + l] * du;
+  for (int k = 0; k < g->dim; ++k) nc[g->o_X + k] = wc[g->o_X + k] * du;
+  for (int c = 0; c < g->nF; ++c) {
+    const int i = g->Fidx[c] / 3, j = g->Fidx[c] % 3;
+    nc[g->o_F + c] = (2.0 / 3.0) * ac->F[3 * i + j] * du - ac->u[i] * dFrow[j];
+  }
+  (void)d;
+}
+
+/* Face states of one cell after the MUSCL-Hancock half step.  Falls back to
+ * the cell average on both faces when a state leaves the admissible set. */
+static void face_states(const or_grid* g, int d, double lam, const double* wm,
+                        const double* wc, const double* wp, const double* uc,
+                        const aux_t* ac, double* UL, aux_t* aL, double* UR,
+                        aux_t* aR) {
+  double wL[MAXF], wR[MAXF];
+  for (int k = 0; k < g->nfield; ++k) {
+    const double s = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
+    wL[k] = wc[k] - 0.5 * s;
+    wR[k] = wc[k] + 0.5 * s;
+  }
+  double uL0[MAXF], uR0[MAXF];
+  aux_t xL, xR;
+  int ok = w2u(g, wL, uL0, &xL) == 0 && w2u(g, wR, uR0, &xR) == 0;
+  if (ok) {
+    double FL[MAXF], FR[MAXF], nc[MAXF], dF[3];
+    phys_flux(g, d, uL0, &xL, FL);
+    phys_flux(g, d, uR0, &xR, FR);
+    for (int j = 0; j < 3; ++j) dF[j] = xR.F[3 * d + j] - xL.F[3 * d + j];
+    noncons(g, d, wc, ac, xR.u[d] - xL.u[d], dF, nc);
+    double uL1[MAXF], uR1[MAXF], tmp[MAXF];
+    for (int k = 0; k < g->nfield; ++k) {
+      const double inc = 0.5 * lam * ((FL[k] - FR[k]) + nc[k]);
+      uL1[k] = uL0[k] + inc;
+      uR1[k] = uR0[k] + inc;
+    }
+    ok = u2w(g, uL1, tmp, aL) == 0 && u2w(g, uR1, tmp, aR) == 0;
+    if (ok) {
+      memcpy(UL, uL1, sizeof(double) * g->nfield);
+      memcpy(UR, uR1, sizeof(double) * g->nfield);
+      return;
+    }
+  }
+  memcpy(UL, uc, sizeof(double) * g->nfield);
+  memcpy(UR, uc, sizeof(double) * g->nfield);
+  *aL = *ac;
+  *aR = *ac;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boundaries: two ghost cells per side along the sweep axis.               */
+/* ------------------------------------------------------------------------ */
+
+static void mirror_state(const or_grid* g, int d, double* u, double wall) {
+  u[g->o_mom + d] = -u[g->o_mom + d];
+  for (int c = 0; c < g->nF; ++c) {
+    const int i = g->Fidx[c] / 3, j = g->Fidx[c] % 3;
+    if ((i == d) != (j == d)) u[g->o_F + c] = -u[g->o_F + c];
+  }
+  u[g->o_X + d] = 2.0 * wall - u[g->o_X + d];
+}
+
+/* ext[c+2] holds cell c of the line, c = -2 .. n+1. */
+static void fill_ghosts(const or_grid* g, int d, long n, double* ext) {
+  const int nf = g->nfield;
+  const double L = g->hi[d] - g->lo[d];
+  for (int side = 0; side < 2; ++side) {
+    for (int m = 0; m < 2; ++m) {
+      double* dst = side == 0 ? ext + (size_t)(1 - m) * nf
+                              : ext + (size_t)(n + 2 + m) * nf;
+      const int bc = g->bc[d][side];
+      long src;
+      if (bc == OR_BC_PERIODIC)
+        src = side == 0 ? n - 1 - m : m;
+      else if (bc == OR_BC_REFLECTIVE)
+        src = side == 0 ? m : n - 1 - m;
+      else
+        src = side == 0 ? 0 : n - 1;
+      if (src < 0) src = 0;
+      if (src > n - 1) src = n - 1;
+      memcpy(dst, ext + (size_t)(src + 2) * nf, sizeof(double) * nf);
+      if (bc == OR_BC_PERIODIC)
+        dst[g->o_X + d] += side == 0 ? -L : L;
+      else if (bc == OR_BC_REFLECTIVE)
+        mirror_state(g, d, dst, side == 0 ? g->lo[d] : g->hi[d]);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One sweep along axis d over one line of cells.                            */
+/* ------------------------------------------------------------------------ */
+
+static long line_stride(const or_grid* g, int d) {
+  return d == 0 ? 1 : (d == 1 ? g->n[0] : g->n[0] * g->n[1]);
+}
+
+static long line_base(const or_grid* g, int d, long line) {
+  if (d == 0) return line * g->n[0];
+  if (d == 1) {
+    const long i = line % g->n[0], k = line / g->n[0];
+    return i + k * g->n[0] * g->n[1];
+  }
+  return line;
+}
+
+static int sweep_line(const or_grid* g, int d, double dt, long line,
+                      long* bad) {
+  const long n = g->n[d];
+  const int nf = g->nfield;
+  const long base = line_base(g, d, line), stride = line_stride(g, d);
+  const double lam = dt / g->dx[d];
+  const size_t ne = (size_t)n + 4;
+  double* ext = malloc(sizeof(double) * ne * nf);
+  double* W = malloc(sizeof(double) * ne * nf);
+  aux_t* A = malloc(sizeof(aux_t) * ne);
+  double* FS = malloc(sizeof(double) * ne * 2 * nf); /* face states per cell */
+  aux_t* FA = malloc(sizeof(aux_t) * ne * 2);
+  double* FX = malloc(sizeof(double) * ne * nf);     /* face fluxes */
+  double* UF = malloc(sizeof(double) * ne);          /* face velocity */
+  double* FR = malloc(sizeof(double) * ne * 3);      /* face Fbar row d */
+  int rc = OR_OK;
+  for (long c = 0; c < n; ++c)
+    for (int k = 0; k < nf; ++k)
+      ext[(size_t)(c + 2) * nf + k] = g->U[(size_t)k * g->ncell + base + c * stride];
+  fill_ghosts(g, d, n, ext);
+  /* 1. primitive recovery on every cell of the extended line */
+  for (size_t e = 0; e < ne; ++e) {
+    if (u2w(g, ext + e * nf, W + e * nf, &A[e]) != 0) {
+      long c = (long)e - 2;
+      if (c < 0) c = 0;
+      if (c > n - 1) c = n - 1;
+      *bad = base + c * stride;
+      rc = OR_ENONFINITE;
+      goto done;
+    }
+  }
+  /* 2. reconstruction + half step on cells -1 .. n (ext 1 .. n+2) */
+  for (size_t e = 1; e <= (size_t)n + 2; ++e) {
+    face_states(g, d, lam, W + (e - 1) * nf, W + e * nf, W + (e + 1) * nf,
+                ext + e * nf, &A[e], FS + (2 * e) * nf, &FA[2 * e],
+                FS + (2 * e + 1) * nf, &FA[2 * e + 1]);
+  }
+  /* 3. HLLC on faces between ext e and e+1, e = 1 .. n+1 */
+  for (size_t e = 1; e <= (size_t)n + 1; ++e) {
+    riemann(g, d, FS + (2 * e + 1) * nf, &FA[2 * e + 1], FS + (2 * (e + 1)) * nf,
+         &FA[2 * (e + 1)], FX + e * nf, &UF[e], FR + 3 * e);
+  }
+  /* 4. update of cells 0 .. n-1 (ext 2 .. n+1): face e-1 is left, e right */
+  for (size_t e = 2; e <= (size_t)n + 1; ++e) {
+    const double* uc = ext + e * nf;
+    const double du = UF[e] - UF[e - 1];
+    double dF[3], nc[MAXF];
+    for (int j = 0; j < 3; ++j) dF[j] = FR[3 * e + j] - FR[3 * (e - 1) + j];
+    noncons(g, d, W + e * nf, &A[e], du, dF, nc);
+    const long cell = base + ((long)e - 2) * stride;
+    for (int k = 0; k < nf; ++k)
+      g->V[(size_t)k * g->ncell + cell] =
+          uc[k] + lam * ((FX[(e - 1) * nf + k] - FX[e * nf + k]) + nc[k]);
+  }
+done:
+  free(ext); free(W); free(A); free(FS); free(FA); free(FX); free(UF); free(FR);
+  return rc;
+}
+
+static int sweep(or_grid* g, int d, double dt) {
+  const long nlines = g->ncell / g->n[d];
+  int rc = OR_OK;
+  long bad = -1;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long line = 0; line < nlines; ++line) {
+    long b = -1;
+    const int r = sweep_line(g, d, dt, line, &b);
+    if (r != OR_OK) {
+#pragma omp critical
+      {
+        if (rc == OR_OK || b < bad) { rc = r; bad = b; }
+      }
+    }
+  }
+  if (rc != OR_OK) {
+    g->bad_cell = bad;
+    return rc;
+  }
+  double* t = g->U;
+  g->U = g->V;
+  g->V = t;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Perturbation field phi(x,t) = phi0(X(x,t)) (Eq. for phi, Sec. 3.2.2):    */
+/* multilinear interpolation on the lattice, 1 outside it (R13).            */
+/* ------------------------------------------------------------------------ */
+
+double or_lookup(int dim, const float* phi0, const long pn[3],
+                 const double plo[3], const double ph[3], const double X[3]) {
+  if (!phi0) return 1.0;
+  long i0[3] = {0, 0, 0};
+  double w[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < dim; ++k) {
+    const double s = (X[k] - plo[k]) / ph[k];
+    if (!(s >= 0.0) || !(s <= (double)(pn[k] - 1))) return 1.0;
+    long i = (long)floor(s);
+    if (i > pn[k] - 2) i = pn[k] - 2;
+    i0[k] = i;
+    w[k] = s - (double)i;
+  }
+  double v = 0.0;
+  const int corners = 1 << dim;
+  for (int c = 0; c < corners; ++c) {
+    double wt = 1.0;
+    long idx = 0, str = 1;
+    for (int k = 0; k < dim; ++k) {
+      const int b = (c >> k) & 1;
+      wt *= b ? w[k] : 1.0 - w[k];
+      idx += (i0[k] + b) * str;
+      str *= pn[k];
+    }
+    v += wt * (double)phi0[idx];
+  }
+  return v;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Damage (Sec. 2.1.1: Bonora rate, Pirondi-Bonora gate, threshold;         */
+/* Sec. 4.3: simple model), RK4 over the step (Sec. 3.1).                    */
+/* ------------------------------------------------------------------------ */
+
+/* Triaxiality-dependent threshold plastic strain (Eq. after the gate). */
+double or_eps_thresh(double eps_t, double eps_c, double n, double Rt) {
+  const double num = pow(eps_c, 2.0 * n) - pow(eps_t, 2.0 * n);
+  const double den = pow(eps_c, 2.0 * n / Rt) - pow(eps_t, 2.0 * n / Rt);
+  return pow(eps_t, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));
+}
+
+/* Stress triaxiality function, first form with the hydrostatic pressure
+ * (the R_t printed with rho0/rho, used with p instead of p_c, R17). */
+double or_Rt(double poisson, double rho0, double rho, double p, double seq) {
+  const double x = p / seq;
+  return 2.0 / 3.0 * (1.0 + poisson) +
+         3.0 * (1.0 - 2.0 * poisson) * (rho0 / rho) * (x * x);
+}
+
+static double damage_rate(const or_material* m, double D, double eps,
+                          double epsdot, double p, double Rt, double thresh) {
+  if (m->damage == 2) return m->Ddot0 * (1.0 - D) * epsdot;
+  /* Bonora, D0 = 0 (R18); active only under tension above threshold */
+  if (!(p < 0.0) || !(eps > thresh)) return 0.0;
+  if (D >= m->D_crit) return 0.0;
+  const double aD = m->alpha_D, Dc = m->D_crit;
+  return aD * pow(Dc, 1.0 / aD) / log(m->eps_c / m->eps_t) * Rt *
+         pow(Dc - D, (aD - 1.0) / aD) * epsdot / eps;
+}
+
+double or_damage_rk4(const or_material* m, double D, double eps0, double deps,
+                     double dt, double p, double seq, double rho) {
+  if (m->damage == 0 || !(deps > 0.0)) return D;
+  double Rt = 1.0, thresh = 0.0;
+  if (m->damage == 1) {
+    if (!(seq > 0.0)) return D;
+    Rt = or_Rt(m->poisson, m->rho0, rho, p, seq);
+    thresh = or_eps_thresh(m->eps_t, m->eps_c, m->n_hard, Rt);
+  }
+  const double ed = deps / dt;
+  const double k1 = damage_rate(m, D, eps0, ed, p, Rt, thresh);
+  const double k2 = damage_rate(m, D + 0.5 * dt * k1, eps0 + 0.5 * deps, ed, p, Rt, thresh);
+  const double k3 = damage_rate(m, D + 0.5 * dt * k2, eps0 + 0.5 * deps, ed, p, Rt, thresh);
+  const double k4 = damage_rate(m, D + dt * k3, eps0 + deps, ed, p, Rt, thresh);
+  double Dn = D + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+  if (Dn < 0.0) Dn = 0.0;
+  if (Dn > m->D_crit) Dn = m->D_crit;
+  return Dn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plastic return (Phi of Sec. 2.1 with chi -> infinity, R15): radial return */
+/* in Hencky space to the perturbed, damaged Johnson-Cook yield stress      */
+/* sigma'_Y = phi sigma_Y (Eq. perturbed yield), (1-D) (Sec. 2.1.1), and 0  */
+/* at critical damage (Sec. 3.1).                                            */
+/* ------------------------------------------------------------------------ */
+
+static double yield_mix(const or_material* mats, int nmat, const double* phi,
+                        const double* eps, const double* D, double phihat,
+                        double dt, double dl, double* dY) {
+  double Y = 0.0, dYs = 0.0;
+  for (int l = 0; l < nmat; ++l) {
+    const or_material* m = &mats[l];
+    if (m->plasticity != 1) continue;
+    if (is_damaged(m) && D[l] >= m->D_crit) continue;
+    const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;
+    /* advection can leave a rounding-level negative plastic strain; the
+     * hardening law sees it as zero (R27) */
+    const double e = (eps[l] > 0.0 ? eps[l] : 0.0) + dl;
+    double hard = m->c1, dhard = 0.0;
+    if (m->c2 != 0.0) {
+      hard += m->c2 * pow(e, m->n_hard);
+      if (e > 0.0) dhard = m->c2 * m->n_hard * pow(e, m->n_hard - 1.0);
+    }
+    double R = 1.0, dR = 0.0;
+    if (m->c3 != 0.0 && dl > 0.0) {
+      const double r = 1.0 + m->c3 * log(dl / (dt * m->edot0));
+      if (r > 1.0) {
+        R = r;
+        dR = m->c3 / dl;
+      }
+    }
+    const double wgt = phi[l] * phihat * psi;
+    Y += wgt * hard * R;
+    dYs += wgt * (dhard * R + hard * dR);
+  }
+  if (dY) *dY = dYs;
+  return Y;
+}
+
+/* Solve sigma_tr - 3 G dl - Y(dl) = 0 for the plastic increment dl >= 0. */
+static int return_increment(const or_material* mats, int nmat,
+                            const double* phi, const double* eps,
+                            const double* D, double phihat, double dt,
+                            double G, double str, double* dl_out) {
+  const double Y0 = yield_mix(mats, nmat, phi, eps, D, phihat, dt, 0.0, NULL);
+  if (!(str > Y0)) {
+    *dl_out = 0.0;
+    return OR_OK;
+  }
+  /* Safeguarded Newton on the bracket [0, sigma_tr/(3G)], iterated down to
+   * the rounding floor: the residual is a difference of terms no larger than
+   * sigma_tr, so |g| <= 8 eps sigma_tr is converged; so is a step below the
+   * rounding scale of the bracket. */
+  const double b0 = str / (3.0 * G);
+  double a = 0.0, b = b0;
+  double dl = (str - Y0) / (3.0 * G);
+  for (int it = 0; it < 200; ++it) {
+    double dY;
+    const double Y = yield_mix(mats, nmat, phi, eps, D, phihat, dt, dl, &dY);
+    const double gv = str - 3.0 * G * dl - Y;
+    if (fabs(gv) <= 8.0 * DBL_EPSILON * str) {
+      *dl_out = dl;
+      return OR_OK;
+    }
+    if (gv > 0.0) a = dl; else b = dl;
+    double nx = dl - gv / (-3.0 * G - dY);
+    if (!(nx > a && nx < b)) nx = 0.5 * (a + b);
+    if (fabs(nx - dl) <= 4.0 * DBL_EPSILON * b0) {
+      *dl_out = nx;
+      return OR_OK;
+    }
+    dl = nx;
+  }
+  return OR_ENOCONV;
+}
+
+static double det3(const double F[9]) {
+  return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+         F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+/* F <- exp((k-1) devH) F = Q diag(exp((k-1) h)) Q^T F */
+static void scale_stretch(double F[9], const double Q[9], const double h[3],
+                          double k) {
+  double m[3], S[9], out[9];
+  for (int i = 0; i < 3; ++i) m[i] = exp((k - 1.0) * h[i]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S[3 * i + j] = Q[3 * i + 0] * m[0] * Q[3 * j + 0] +
+                     Q[3 * i + 1] * m[1] * Q[3 * j + 1] +
+                     Q[3 * i + 2] * m[2] * Q[3 * j + 2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      out[3 * i + j] = S[3 * i + 0] * F[0 + j] + S[3 * i + 1] * F[3 + j] +
+                       S[3 * i + 2] * F[6 + j];
+  memcpy(F, out, sizeof out);
+}
+
+/* Shear modulus of the mixture G_mix = sum phi_l G_l and whether the cell
+ * may yield (every material with G0 > 0 has a plasticity model). */
+static int mix_shear(const or_material* mats, int nmat, const double* phi,
+                     const double* rho, const double* D, double* Gmix) {
+  int can_yield = 1;
+  *Gmix = 0.0;
+  for (int l = 0; l < nmat; ++l) {
+    double th[5];
+    const double psi = is_damaged(&mats[l]) ? 1.0 - D[l] : 1.0;
+    or_thermo(&mats[l], rho[l], psi, 0.0, th);
+    *Gmix += phi[l] * th[3];
+    if (mats[l].eos == 1 && mats[l].G0 > 0.0 && mats[l].plasticity != 1)
+      can_yield = 0;
+  }
+  return can_yield;
+}
+
+int or_plastic_return_cell(const or_material* mats, int nmat,
+                           const double* phi, const double* rho,
+                           const double* eps, const double* D, double phihat,
+                           double dt, double F[9], double* dEps) {
+  double Gm;
+  const int can_yield = mix_shear(mats, nmat, phi, rho, D, &Gm);
+  const double dt3 = cbrt(det3(F));
+  for (int k = 0; k < 9; ++k) F[k] /= dt3;
+  double devH[9], h[3], Q[9], lam[3];
+  if (hencky_eig(F, devH, h, Q, lam) != 0) return OR_ENONFINITE;
+  *dEps = 0.0;
+  if (!can_yield || !(Gm > 0.0)) return OR_OK;
+  const double J = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+  const double str = sqrt(6.0) * Gm * J;
+  double dl;
+  const int rc = return_increment(mats, nmat, phi, eps, D, phihat, dt, Gm, str, &dl);
+  if (rc != OR_OK) return rc;
+  if (dl > 0.0) {
+    const double k = (str - 3.0 * Gm * dl) / str;
+    scale_stretch(F, Q, h, k);
+  }
+  *dEps = dl;
+  return OR_OK;
+}
+
+/* Sources of one cell after the sweeps (R12). */
+static int source_cell(or_grid* g, long cell, double dt) {
+  double u[MAXF], w[MAXF];
+  aux_t ax;
+  for (int k = 0; k < g->nfield; ++k) u[k] = g->U[(size_t)k * g->ncell + cell];
+  if (u2w(g, u, w, &ax) != 0) return OR_ENONFINITE;
+  double phi[OR_MAXMAT], rho[OR_MAXMAT], eps[OR_MAXMAT], D[OR_MAXMAT];
+  vol_fracs(g, u, phi);
+  for (int l = 0; l < g->nmat; ++l) {
+    rho[l] = w[g->o_arho + l];
+    const int h = g->hslot[l];
+    eps[l] = h >= 0 ? w[g->o_hist + 2 * h] : 0.0;
+    D[l] = h >= 0 ? w[g->o_hist + 2 * h + 1] : 0.0;
+  }
+  double X[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < g->dim; ++k) X[k] = w[g->o_X + k];
+  const double phihat = or_lookup(g->dim, g->phi0, g->pn, g->plo, g->ph, X);
+  double F[9];
+  full_F(g, u, F);
+  double dl;
+  const int rc = or_plastic_return_cell(g->mat, g->nmat, phi, rho, eps, D,
+                                        phihat, dt, F, &dl);
+  if (rc != OR_OK) return rc;
+  for (int c = 0; c < g->nF; ++c) u[g->o_F + c] = F[g->Fidx[c]];
+  if (dl > 0.0) {
+    /* pressure and equivalent stress of the returned state for the damage law */
+    double ws[MAXF];
+    aux_t as;
+    if (u2w(g, u, ws, &as) != 0) return OR_ENONFINITE;
+    mix_t mx;
+    if (mixture(g, phi, rho, D, F, &mx) != 0) return OR_ENONFINITE;
+    const double seq = sqrt(6.0) * mx.Gmix * sqrt(mx.J2);
+    for (int l = 0; l < g->nmat; ++l) {
+      const int h = g->hslot[l];
+      if (h < 0) continue;
+      const double arho = u[g->o_arho + l];
+      const double Dn = or_damage_rk4(&g->mat[l], D[l], eps[l], dl, dt, as.p,
+                                      seq, rho[l]);
+      u[g->o_hist + 2 * h] = arho * (eps[l] + dl);
+      u[g->o_hist + 2 * h + 1] = arho * Dn;
+    }
+  }
+  for (int k = 0; k < g->nfield; ++k) g->U[(size_t)k * g->ncell + cell] = u[k];
+  return OR_OK;
+}
+
+static int sources(or_grid* g, double dt) {
+  int rc = OR_OK;
+  long bad = -1;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < g->ncell; ++c) {
+    const int r = source_cell(g, c, dt);
+    if (r != OR_OK) {
+#pragma omp critical
+      {
+        if (rc == OR_OK || c < bad) { rc = r; bad = c; }
+      }
+    }
+  }
+  if (rc != OR_OK) g->bad_cell = bad;
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CFL time step: dt = cfl * min_d dx_d / max_cells (max_d |u_d| + c_L).    */
+/* ------------------------------------------------------------------------ */
+
+int or_cfl_dt(or_grid* g, double cfl, double* dt, double* smax) {
+  double s = 0.0;
+  int rc = OR_OK;
+  long bad = -1;
+#pragma omp parallel for reduction(max : s) schedule(static)
+  for (long c = 0; c < g->ncell; ++c) {
+    double u[MAXF], w[MAXF];
+    aux_t ax;
+    for (int k = 0; k < g->nfield; ++k) u[k] = g->U[(size_t)k * g->ncell + c];
+    if (u2w(g, u, w, &ax) != 0) {
+#pragma omp critical
+      {
+        if (rc == OR_OK || c < bad) { rc = OR_ENONFINITE; bad = c; }
+      }
+      continue;
+    }
+    double v = 0.0;
+    for (int k = 0; k < g->dim; ++k) {
+      const double a = fabs(ax.u[k]);
+      if (a > v) v = a;
+    }
+    v += ax.cL;
+    if (v > s) s = v;
+  }
+  if (rc != OR_OK) {
+    g->bad_cell = bad;
+    return rc;
+  }
+  double dxm = g->dx[0];
+  for (int k = 1; k < g->dim; ++k)
+    if (g->dx[k] < dxm) dxm = g->dx[k];
+  *smax = s;
+  *dt = cfl * dxm / s;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* API                                                                       */
+/* ------------------------------------------------------------------------ */
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int or_nfield(const or_grid* g) { return g->nfield; }
+long or_ncell(const or_grid* g) { return g->ncell; }
+
+or_grid* or_create(int dim, const long n[3], const double lo[3],
+                   const double hi[3], const int bc[6], int nmat,
+                   const or_material* mats, const double* prim,
+                   const float* phi0, const long pn[3], const double plo[3],
+                   const double ph[3], int* status) {
+  *status = OR_EINVAL;
+  if (dim < 1 || dim > 3 || nmat < 1 || nmat > OR_MAXMAT) return NULL;
+  or_grid* g = calloc(1, sizeof(or_grid));
+  g->dim = dim;
+  g->nmat = nmat;
+  g->ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    g->n[k] = k < dim ? n[k] : 1;
+    g->lo[k] = k < dim ? lo[k] : 0.0;
+    g->hi[k] = k < dim ? hi[k] : 1.0;
+    g->dx[k] = (g->hi[k] - g->lo[k]) / (double)g->n[k];
+    g->ncell *= g->n[k];
+    g->bc[k][0] = k < dim ? bc[2 * k] : 0;
+    g->bc[k][1] = k < dim ? bc[2 * k + 1] : 0;
+    if (k < dim && g->n[k] < 2) { free(g); return NULL; }
+  }
+  g->nhist = 0;
+  for (int l = 0; l < nmat; ++l) {
+    g->mat[l] = mats[l];
+    g->hslot[l] = mats[l].plasticity == 1 ? g->nhist++ : -1;
+  }
+  static const int F1[] = {0, 4, 8};
+  static const int F2[] = {0, 1, 3, 4, 8};
+  g->nF = dim == 1 ? 3 : (dim == 2 ? 5 : 9);
+  for (int c = 0; c < g->nF; ++c)
+    g->Fidx[c] = dim == 1 ? F1[c] : (dim == 2 ? F2[c] : c);
+  g->o_phi = 0;
+  g->o_arho = nmat - 1;
+  g->o_mom = g->o_arho + nmat;
+  g->o_E = g->o_mom + dim;
+  g->o_F = g->o_E + 1;
+  g->o_hist = g->o_F + g->nF;
+  g->o_X = g->o_hist + 2 * g->nhist;
+  g->nfield = g->o_X + dim;
+  g->U = malloc(sizeof(double) * g->nfield * g->ncell);
+  g->V = malloc(sizeof(double) * g->nfield * g->ncell);
+  if (phi0) {
+    long np = 1;
+    for (int k = 0; k < dim; ++k) {
+      g->pn[k] = pn[k];
+      g->plo[k] = plo[k];
+      g->ph[k] = ph[k];
+      np *= pn[k];
+    }
+    g->phi0 = malloc(sizeof(float) * np);
+    memcpy(g->phi0, phi0, sizeof(float) * np);
+  }
+  g->bad_cell = -1;
+  *status = OR_OK;
+  for (long c = 0; c < g->ncell; ++c) {
+    double w[MAXF], u[MAXF];
+    aux_t ax;
+    for (int k = 0; k < g->nfield; ++k) w[k] = prim[(size_t)k * g->ncell + c];
+    if (w2u(g, w, u, &ax) != 0) {
+      *status = OR_ENONFINITE;
+      g->bad_cell = c;
+    }
+    for (int k = 0; k < g->nfield; ++k) g->U[(size_t)k * g->ncell + c] = u[k];
+  }
+  return g;
+}
+
+void or_destroy(or_grid* g) {
+  if (!g) return;
+  free(g->U);
+  free(g->V);
+  free(g->phi0);
+  free(g);
+}
+
+int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed, double* info) {
+  int rc = OR_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    double dt, smax = 0.0;
+    if (dt_fixed > 0.0) {
+      dt = dt_fixed;
+    } else {
+      rc = or_cfl_dt(g, cfl, &dt, &smax);
+      if (rc != OR_OK) break;
+    }
+    for (int d = 0; d < g->dim && rc == OR_OK; ++d) rc = sweep(g, d, dt);
+    if (rc != OR_OK) break;
+    rc = sources(g, dt);
+    if (rc != OR_OK) break;
+    g->t += dt;
+    g->dt_last = dt;
+    g->smax = smax;
+    g->steps += 1;
+  }
+  if (info) {
+    info[0] = g->t;
+    info[1] = g->dt_last;
+    info[2] = g->smax;
+    info[3] = (double)g->steps;
+    info[4] = (double)g->bad_cell;
+  }
+  return rc;
+}
+
+int or_read(const or_grid* g, int primitive, double* out) {
+  if (!primitive) {
+    memcpy(out, g->U, sizeof(double) * g->nfield * g->ncell);
+    return OR_OK;
+  }
+  int rc = OR_OK;
+  for (long c = 0; c < g->ncell; ++c) {
+    double u[MAXF], w[MAXF];
+    aux_t ax;
+    for (int k = 0; k < g->nfield; ++k) u[k] = g->U[(size_t)k * g->ncell + c];
+    if (u2w(g, u, w, &ax) != 0) rc = OR_ENONFINITE;
+    for (int k = 0; k < g->nfield; ++k) out[(size_t)k * g->ncell + c] = w[k];
+  }
+  return rc;
+}
+
+int or_write_conserved(or_grid* g, const double* U) {
+  memcpy(g->U, U, sizeof(double) * g->nfield * g->ncell);
+  return OR_OK;
+}
+
+/* Totals sum dV (phi rho)_l, sum dV rho u (3 comps), sum dV rho E, each
+ * with compensated (Kahan) summation. */
+int or_totals(const or_grid* g, double* out) {
+  double dV = 1.0;
+  for (int k = 0; k < g->dim; ++k) dV *= g->dx[k];
+  const int nq = g->nmat + 4;
+  for (int q = 0; q < nq; ++q) {
+    int field = -1;
+    if (q < g->nmat) field = g->o_arho + q;
+    else if (q < g->nmat + 3) field = (q - g->nmat) < g->dim ? g->o_mom + (q - g->nmat) : -1;
+    else field = g->o_E;
+    double s = 0.0, comp = 0.0;
+    if (field >= 0)
+      for (long c = 0; c < g->ncell; ++c) {
+        const double y = g->U[(size_t)field * g->ncell + c] * dV - comp;
+        const double t = s + y;
+        comp = (t - s) - y;
+        s = t;
+      }
+    out[q] = s;
+  }
+  return OR_OK;
+}

@@ -1,0 +1,104 @@
+/*
+ * Plain FP64 CPU oracle of the explicit Eulerian step of the diffuse-interface
+ * multi-material elastoplastic method of Wallis, Barton & Nikiforakis,
+ * "A multi-physics method for fracture and fragmentation at high strain-rates"
+ * (arXiv 2210.04037).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load this library.  It shares
+ * no code, header, table or helper with the CUDA path under
+ * paper_2210_04037_gb300/; the two agree only on the documented field order.
+ *
+ * What it computes (paper sections in brackets; where the paper defers to
+ * earlier work the reading is named R<k> and listed in the design notes):
+ *   - state and transport equations (Sec. 2.1, Eqs. for phi, phi*rho,
+ *     phi*rho*alpha, rho*u, rho*E, the unimodular deformation tensor, X),
+ *   - closures: Mie-Grueneisen split with the Romenskii cold energy, the
+ *     Romenskii shear modulus, constant Grueneisen coefficient, Hencky strain,
+ *     shear energy G*J^2/rho, stress -p I + 2 G dev(H) (Sec. 2.1.1, 2.1.2),
+ *   - ideal gas as the G=0 special case,
+ *   - damage degradation of G and of the cold energy, the Bonora damage rate
+ *     with the tension gate and the triaxiality-dependent threshold, the
+ *     simple damage model of the expanding-ring test, RK4 integration
+ *     (Sec. 2.1.1, Sec. 3.1, Sec. 4.3),
+ *   - the yield stress perturbed by phi0(X) looked up on a lattice
+ *     (Sec. 2.1.3, Sec. 3.2.2).
+ * Parity unpinned parts: none of the functions below is without a pin; the
+ * choice of MUSCL-Hancock + HLLC itself is a reading (the paper defers the
+ * hyperbolic solver), pinned only through the closed-form tests.
+ */
+#ifndef MMFRAC_ORACLE_H
+#define MMFRAC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXMAT 4
+
+/* Boundary kinds per face of the box. */
+#define OR_BC_TRANSMISSIVE 0
+#define OR_BC_PERIODIC 1
+#define OR_BC_REFLECTIVE 2
+
+/* Error codes. */
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_ENONFINITE (-4)
+#define OR_ENOCONV (-5)
+
+typedef struct {
+  int eos;                /* 0 ideal gas, 1 Romenskii solid */
+  double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
+  int plasticity;         /* 0 none, 1 Johnson-Cook (no thermal term) */
+  double c1, c2, c3, n_hard, edot0;
+  int damage;             /* 0 none, 1 Bonora, 2 simple (Ddot0 (1-D) epsdot) */
+  double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+} or_material;
+
+typedef struct or_grid or_grid;
+
+/* Create a grid and set its initial state from primitive fields.
+ * prim: [nfield][ncell] doubles, x fastest, in the primitive field order
+ * (phi_0..phi_{N-2}, rho_0..rho_{N-1}, u (dim), p, Fbar (active comps),
+ *  (eps_p, D) per plastic material, X (dim)).
+ * bc: [dim][2] flattened as bc[2*d + side].
+ * phi0: perturbation lattice (float, x fastest) or NULL.              */
+or_grid* or_create(int dim, const long n[3], const double lo[3],
+                   const double hi[3], const int bc[6], int nmat,
+                   const or_material* mats, const double* prim,
+                   const float* phi0, const long pn[3], const double plo[3],
+                   const double ph[3], int* status);
+void or_destroy(or_grid* g);
+int or_nfield(const or_grid* g);
+long or_ncell(const or_grid* g);
+/* Advance nsteps.  dt_fixed > 0 imposes that dt; otherwise the CFL rule. */
+int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed,
+            double* info /* [t, dt_last, smax, steps, bad_cell] */);
+/* Time step the CFL rule gives for the present state. */
+int or_cfl_dt(or_grid* g, double cfl, double* dt, double* smax);
+int or_read(const or_grid* g, int primitive, double* out);
+int or_write_conserved(or_grid* g, const double* U);
+int or_totals(const or_grid* g, double* out /* N + 4 */);
+void or_set_threads(int n);
+
+/* ---- single-point routines exported for the pins ---- */
+void or_thermo(const or_material* m, double rho, double psi, double J2,
+               double* out /* e_ref, p_ref, dpref_drho, G, Gamma */);
+int or_hencky(const double F[9], double devH[9], double lam[3], double Q[9]);
+double or_lookup(int dim, const float* phi0, const long pn[3],
+                 const double plo[3], const double ph[3], const double X[3]);
+double or_eps_thresh(double eps_t, double eps_c, double n, double Rt);
+double or_Rt(double poisson, double rho0, double rho, double p, double seq);
+double or_damage_rk4(const or_material* m, double D, double eps0,
+                     double deps, double dt, double p, double seq,
+                     double rho);
+int or_plastic_return_cell(const or_material* mats, int nmat,
+                           const double* phi, const double* rho,
+                           const double* eps, const double* D, double phihat,
+                           double dt, double F[9], double* dEps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
