@@ -1,0 +1,333 @@
+"""Throughput of the explicit diffuse-interface step on GB300.
+
+One step = CFL time step + the dimensionally split sweeps + the per-cell
+sources, over the whole grid of the workload.  Metric: cell-updates/s (one
+update = one cell through one full step), for the FP32-split path (the
+headline) beside the FP64 path, with the HBM roofline fraction of the
+dominant kernel.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload ring_2d|cylinder_3d|spall_1d]
+                    [--precision fp32split|fp64] [--impl mmfrac|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload (the step does not shard on one grid here: replicas only); the
+value is the aggregate over ranks.  ``--impl reference`` times the CPU
+oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2210_04037_gb300 import workloads as W  # noqa: E402
+
+METRIC = ("cell-updates/s and % HBM roofline at 1 GB300, FP32-split vs FP64 at stated error")
+L2_BYTES = 129 * 2 ** 20
+DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000}
+WORKLOAD_TEXT = {
+    "ring_2d": "2D expanding ring, {n}x{n} cells, Al-H32 annulus r 20-24 mm at 200 m/s in air, "
+               "simple damage, phi0 ~ U(0.9,1.1) on a 0.5 mm lattice",
+    "cylinder_3d": "3D expanding thin cylinder, {n}^3 cells, CuBe shell r 18-20 mm at 250 m/s in "
+                   "air, Bonora damage, phi0 ~ rectified N(1,0.1^2) on a 0.5 mm lattice",
+    "spall_1d": "1D plate impact spall, {n} cells, CuBe flyer 2 mm at 300 m/s onto a 6 mm "
+                "target, Bonora damage, phi0 ~ rectified N(1,0.05^2) per cell",
+}
+
+
+def make_case(name: str, n: int):
+    return W.WORKLOADS[name](n)
+
+
+def state_bytes(case, precision: int) -> int:
+    nf = case.layout.nfield
+    per = 8 * nf if precision == W.FP64 else 4 * (nf - 1) + 8
+    return per * case.ncell
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(case_name: str, n: int, budget_s: float = 12.0, max_steps: int = 50):
+    """The FP64 CPU oracle as it stands, on the host cores, over a bounded
+    number of steps of the same workload (the CPU reference)."""
+    from oracle import OracleGrid
+    case = make_case(case_name, n)
+    cores = os.cpu_count() or 1
+    g = OracleGrid(case, threads=cores)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (time.perf_counter() - t0) < budget_s:
+        g.step(1)
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": case.ncell * steps / el, "unit": "cell-updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 steps of the same {case.ncell}-cell workload from its "
+                      f"initial state ({el:.1f} s wall)"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n = args.size or DEFAULT_SIZE[args.workload]
+    from oracle import OracleGrid
+    case = make_case(args.workload, n)
+    cores = os.cpu_count() or 1
+    g = OracleGrid(case, threads=cores)
+    g.step(args.warmup)
+    t0 = time.perf_counter()
+    g.step(args.steps)
+    el = time.perf_counter() - t0
+    value = case.ncell * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=n), "cells": case.ncell,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} timed FP64 steps of the full workload "
+                                       f"after {args.warmup} warm-up steps"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True):
+    """Device time of `steps` single-step calls (CUDA events on the grid's
+    stream), L2 flushed between steps when the state fits in L2."""
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    g = mmfrac.Grid(case, precision, stream=stream.cuda_stream)
+    g.step(warmup)
+    mmfrac.profile_enable(g.h, profile)
+    mmfrac.profile_read(g.h, reset=True)
+    start = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stop = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches = 0
+    torch.cuda.synchronize()
+    for s in range(steps):
+        if flush_buf is not None:
+            flush_buf.add_(1)
+        start[s].record(stream)
+        g.step(1)
+        stop[s].record(stream)
+        launches += g.launches()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(start, stop))
+    prof = mmfrac.profile_read(g.h, reset=True)
+    return g, ms, prof, launches
+
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.size or DEFAULT_SIZE[args.workload]
+    case = make_case(args.workload, n)
+    prec = W.FP32_SPLIT if args.precision == "fp32split" else W.FP64
+    # a dedicated stream: the library orders its work on it and the timing
+    # events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sbytes = state_bytes(case, prec)
+    flush = None
+    if 2 * sbytes < 2 * L2_BYTES:
+        flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        g, ms, prof, launches = time_device(case, prec, args.steps, args.warmup, stream, flush)
+        torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * case.ncell * args.steps / (ms * 1e-3)
+    # dominant kernel and its roofline (algorithmic bytes: one read and one
+    # write of the state per launch for the sweeps and the sources)
+    peak, peak_kind = read_peaks()
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    algo = 2 * sbytes if dom.startswith("sweep") or dom == "sources" else sbytes
+    achieved = algo / (dom_ms * 1e-3) / 1e9
+    fp32_state = g.read()
+    g.close()
+    # FP64 beside it (same workload, same steps) and the FP32-split error
+    fp64 = None
+    if prec == W.FP32_SPLIT and not args.no_fp64:
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        g64, ms64, prof64, _ = time_device(case, W.FP64, k64, args.warmup, stream, flush)
+        fp64 = {"value": world * case.ncell * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
+                "steps": k64}
+        g64.close()
+        ga = mmfrac.Grid(case, W.FP64, stream=stream.cuda_stream)
+        ga.step(args.warmup + args.steps)
+        ref = ga.read()
+        ga.close()
+        num = np.abs(fp32_state - ref).sum(axis=1)
+        den = np.abs(ref).sum(axis=1)
+        rel = np.where(den > 0, num / np.where(den > 0, den, 1), num)
+        names = case.layout.names()
+        fp64["fp32split_rel_l1_vs_fp64"] = {names[i]: float(rel[i]) for i in range(len(names))}
+    # end-to-end through the C ABI with host buffers: upload the initial
+    # state from pinned memory, K steps each returning the conserved totals,
+    # read the final primitive fields back
+    prim_pinned = torch.from_numpy(np.ascontiguousarray(case.prim)).pin_memory()
+    out_pinned = torch.empty(case.prim.shape, dtype=torch.float64).pin_memory()
+    h = mmfrac.create_grid(case, prec, stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mmfrac.set_materials(h, case, prim=prim_pinned.numpy())
+    for _ in range(args.steps):
+        mmfrac.step(h, 1, case.cfl)
+        mmfrac.conserved_totals(h, len(case.materials))
+    mmfrac.read_fields(h, True, out=out_pinned.numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    mmfrac.destroy(h)
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (case.prim.nbytes + (case.phi0.nbytes if case.phi0 is not None else 0)) / args.steps
+    d2h = (len(case.materials) + 4) * 8 + out_pinned.numel() * 8 / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == W.FP32_SPLIT else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=n), "cells": case.ncell,
+                   "precision": args.precision,
+                   "l2": "flushed between steps (256 MiB write)" if flush is not None
+                   else "state larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": algo,
+                     "avg_launch_ms": dom_ms},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+        "e2e": {"value": world * case.ncell * args.steps / e2e_s, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if fp64:
+        line["fp64"] = fp64
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload, n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mmfrac", choices=["mmfrac", "reference"])
+    ap.add_argument("--workload", default="ring_2d", choices=list(DEFAULT_SIZE))
+    ap.add_argument("--precision", default="fp32split", choices=["fp32split", "fp64"])
+    ap.add_argument("--size", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * mmfrac: GB300-native explicit Eulerian step of the diffuse-interface
+ * multi-material elastoplastic method with damage and a perturbed yield
+ * stress (Wallis, Barton & Nikiforakis, "A multi-physics method for fracture
+ * and fragmentation at high strain-rates", arXiv 2210.04037).
+ *
+ * C ABI.  All device memory is owned by the library.  Host buffers passed to
+ * a call belong to the caller and are only read or written during that call.
+ * Every call is ordered on the grid's CUDA stream; calls that return data to
+ * the host synchronise that stream.  All functions return MM_OK or a negative
+ * mm_status; mm_last_error() gives a thread-local message for the last
+ * failure.
+ *
+ * Problem statement (Sec. 2.1): per material l, volume fraction phi_l,
+ * partial density phi_l rho_l and history phi_l rho_l (eps_p, D); shared
+ * momentum rho u, total energy rho E, unimodular elastic deformation tensor
+ * Fbar and Lagrangian coordinates X.  The step is dimensionally split
+ * (x, y, z sweeps), followed by the per-cell plastic return to the perturbed
+ * yield stress phi0(X) sigma_Y (Sec. 2.1.3) and RK4 damage growth with loss
+ * of strength (Sec. 3.1).
+ *
+ * Field order (primitive / conserved), dim d, N materials, H plastic ones:
+ *   phi_0..phi_{N-2} / same;  rho_0..rho_{N-1} / phi_l rho_l;
+ *   u_0..u_{d-1} / rho u;     p / rho E;
+ *   Fbar comps / same  (d=1: xx yy zz; d=2: xx xy yx yy zz; d=3: 9, row-major);
+ *   (eps_p, D) per plastic material / phi rho (eps_p, D);  X_0..X_{d-1} / same.
+ * Arrays of fields are [field][cell], cells x fastest, then y, then z.
+ */
+#ifndef MMFRAC_H
+#define MMFRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = -1,     /* an argument is out of range or inconsistent */
+  MM_ENOMEM = -2,     /* device allocation failed */
+  MM_ECUDA = -3,      /* a CUDA call failed (no device, launch error, ...) */
+  MM_ENONFINITE = -4, /* a cell left the admissible set (rho_l <= 0, phi_l <= 0,
+                         c_L^2 <= 0 or a non-finite value) */
+  MM_ENOCONV = -5,    /* the plastic return did not converge */
+  MM_EDT = -6,        /* non-positive or non-finite time step */
+  MM_ETIMEOUT = -7,   /* reserved */
+  MM_ESTATE = -8      /* call out of order (e.g. step before set_materials) */
+} mm_status;
+
+enum { MM_BC_TRANSMISSIVE = 0, MM_BC_PERIODIC = 1, MM_BC_REFLECTIVE = 2 };
+enum { MM_FP64 = 0, MM_FP32_SPLIT = 1 };
+enum { MM_EOS_IDEAL_GAS = 0, MM_EOS_ROMENSKII = 1 };
+enum { MM_PL_NONE = 0, MM_PL_JOHNSON_COOK = 1 };
+enum { MM_DMG_NONE = 0, MM_DMG_BONORA = 1, MM_DMG_SIMPLE = 2 };
+
+/* Grid: dim in {1,2,3}; n[k] cells on [lo[k], hi[k]] for k < dim (n[k] >= 2);
+ * bc[k][side] one of MM_BC_*; precision MM_FP64 (every step in FP64) or
+ * MM_FP32_SPLIT (reconstruction and fluxes in FP32, total energy, energy
+ * recovery, plastic return iteration and totals in FP64); n_materials 1..2. */
+typedef struct {
+  int dim;
+  int64_t n[3];
+  double lo[3], hi[3];
+  int bc[3][2];
+  int precision;
+  int n_materials;
+} mm_grid_desc;
+
+/* Material (Sec. 2.1.1-2.1.2 and the parameter tables): Romenskii cold
+ * energy K0, rho0, alpha; shear modulus G0 (rho/rho0)^(beta+1); Grueneisen
+ * Gamma0; ideal gas gamma_gas.  Johnson-Cook yield (c1 + c2 eps^n_hard)
+ * max(1, 1 + c3 ln(epsdot/edot0)).  Damage: Bonora (D_crit, eps_t = the
+ * threshold strain, eps_c = the critical strain, alpha_D, poisson) or the
+ * simple law Ddot = Ddot0 (1-D) epsdot (Sec. 4.3).  SI units. */
+typedef struct {
+  int eos;
+  double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
+  int plasticity;
+  double c1, c2, c3, n_hard, edot0;
+  int damage;
+  double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+} mm_material;
+
+/* Initial state: prim = [nfield][ncell] primitive fields in the order above
+ * (host, copied).  phi0 = perturbation lattice of phi0_n points per axis
+ * (x fastest) with origin phi0_lo and spacing phi0_h (host, copied), or NULL
+ * for phi = 1 everywhere (Sec. 3.2.2: phi(x) = phi0(X(x)), multilinear,
+ * 1 outside the lattice). */
+typedef struct {
+  const double* prim;
+  const float* phi0;
+  int64_t phi0_n[3];
+  double phi0_lo[3], phi0_h[3];
+} mm_init;
+
+typedef struct {
+  double t, dt_last, smax;
+  int64_t steps_done, bad_cell;
+} mm_step_info;
+
+typedef struct mm_grid mm_grid;
+
+/* Create a grid and allocate its state on the current CUDA device.
+ * cuda_stream: a cudaStream_t to order work on, or NULL for a stream the
+ * library creates.  Errors: MM_EINVAL, MM_ENOMEM, MM_ECUDA (no device). */
+mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** out);
+
+/* Set the materials and the initial state (Sec. 2.1; conversion of the
+ * primitive state to the conserved one by the closures of Sec. 2.1.1).
+ * n must equal desc.n_materials.  Errors: MM_EINVAL, MM_ENONFINITE (an
+ * initial cell is inadmissible; bad_cell in mm_last_error). */
+mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_init* init);
+
+/* Advance n_steps explicit steps with dt = cfl * min_k dx_k / max_cells
+ * (max_k |u_k| + c_L), each step = sweeps x, y, z then the sources.
+ * info (may be NULL) receives time, last dt, last signal speed, steps done
+ * and the first bad cell.  On MM_ENONFINITE / MM_ENOCONV the state after
+ * the failing step is undefined.  Errors: MM_ESTATE (no materials yet),
+ * MM_EINVAL, MM_ENONFINITE, MM_ENOCONV, MM_EDT, MM_ECUDA. */
+mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info);
+
+/* Copy fields to host_dst ([popcount(field_mask)][ncell] doubles, fields
+ * in order; bit f of field_mask selects field f, ~0 for all).
+ * primitive = 1 returns the primitive fields, 0 the conserved ones.
+ * dst_len is the capacity of host_dst in doubles.  Errors: MM_EINVAL. */
+mm_status mm_read_fields(mm_grid* g, uint64_t field_mask, int primitive,
+                         double* host_dst, size_t dst_len);
+
+/* Conserved totals sum_cells dV (phi rho)_l (N values), sum dV rho u
+ * (3 values, 0 for k >= dim), sum dV rho E: N + 4 doubles, accumulated in
+ * FP64.  out_len >= N + 4.  Errors: MM_EINVAL. */
+mm_status mm_conserved_totals(mm_grid* g, double* out, size_t out_len);
+
+/* Number of fields and cells of the grid (for sizing buffers). */
+int mm_num_fields(const mm_grid* g);
+int64_t mm_num_cells(const mm_grid* g);
+
+/* Release every device resource of the grid. */
+mm_status mm_destroy(mm_grid* g);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* mm_last_error(void);
+
+/* Kernels launched by the last mm_step call (for launch accounting). */
+int64_t mm_kernel_launches(const mm_grid* g);
+
+/* Kernel timing (tracing aid, no counterpart in the paper).  With enable = 1
+ * every later mm_step brackets each of its launches with CUDA events on the
+ * grid's stream and accumulates the elapsed device time per kernel kind:
+ * MM_K_CFL, MM_K_DT, MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES.
+ * mm_profile_read copies min(n, MM_K_COUNT) accumulated milliseconds and
+ * launch counts (either pointer may be NULL) and, if reset = 1, zeroes them.
+ * Errors: MM_EINVAL, MM_ECUDA. */
+enum { MM_K_CFL = 0, MM_K_DT = 1, MM_K_SWEEP_X = 2, MM_K_SWEEP_Y = 3, MM_K_SWEEP_Z = 4,
+       MM_K_SOURCES = 5, MM_K_COUNT = 6 };
+mm_status mm_profile_enable(mm_grid* g, int enable);
+mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1054,17 +1054,22 @@ or_grid* or_create(int dim, const long n[3], const double lo[3],
     memcpy(g->phi0, phi0, sizeof(float) * np);
   }
   g->bad_cell = -1;
-  *status = OR_OK;
+  long bad = -1;
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < g->ncell; ++c) {
     double w[MAXF], u[MAXF];
     aux_t ax;
     for (int k = 0; k < g->nfield; ++k) w[k] = prim[(size_t)k * g->ncell + c];
     if (w2u(g, w, u, &ax) != 0) {
-      *status = OR_ENONFINITE;
-      g->bad_cell = c;
+#pragma omp critical
+      {
+        if (bad < 0 || c < bad) bad = c;
+      }
     }
     for (int k = 0; k < g->nfield; ++k) g->U[(size_t)k * g->ncell + c] = u[k];
   }
+  g->bad_cell = bad;
+  *status = bad >= 0 ? OR_ENONFINITE : OR_OK;
   return g;
 }
 

@@ -1,0 +1,496 @@
+// C-ABI host side of the mmfrac library: grid lifetime, initial state,
+// the step driver loop (dt stays on the device), read-back and totals.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mm_internal.h"
+#include "mmfrac.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+mm_status fail(mm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess)                                                      \
+      return fail(MM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+__global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin) {
+  const double smax = __longlong_as_double((long long)info->smax_bits);
+  info->smax_bits = 0ull;
+  info->steps += 1;
+  const double dt = cfl * dxmin / smax;
+  if (!(dt > 0.0) || !isfinite(dt)) {
+    if (atomicCAS(&err->code, 0, MM_EDT) == 0) {
+      err->cell = -1;
+      err->step = info->steps;
+    }
+  }
+  info->dt = dt;
+  info->smax = smax;
+  info->t += dt;
+}
+
+}  // namespace
+
+namespace mm {
+// Sum of the per-block partial totals, one warp per quantity, scaled by dV.
+__global__ void k_totals_final(const double* partial, int nblocks, int nq, double dV,
+                               double* out) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * nq + q];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[q] = s * dV;
+}
+}  // namespace mm
+
+struct mm_grid {
+  mm_grid_desc desc;
+  int dim = 0, nmat = 0, nhist = 0, nfield = 0, prec = 0;
+  long long ncell = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* U[2] = {nullptr, nullptr};
+  double* E[2] = {nullptr, nullptr};
+  int cur = 0;
+  DevInfo* info = nullptr;
+  DevErr* err = nullptr;
+  double* prim = nullptr;
+  double* partial = nullptr;
+  double* tot = nullptr;
+  int tot_blocks = 0;
+  float* phi0 = nullptr;
+  bool ready = false;
+  long long launches = 0;
+  KArgs base;
+  // kernel timing
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;      // pool, two per timed launch
+  std::vector<int> ev_kind;         // kind of each started pair
+  double prof_ms[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+  long long prof_n[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+size_t elem_size(const mm_grid* g) { return g->prec == MM_FP64 ? sizeof(double) : sizeof(float); }
+
+void free_state(mm_grid* g) {
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(g->U[i]);
+    cudaFree(g->E[i]);
+    g->U[i] = nullptr;
+    g->E[i] = nullptr;
+  }
+  cudaFree(g->prim);
+  cudaFree(g->phi0);
+  g->prim = nullptr;
+  g->phi0 = nullptr;
+  g->ready = false;
+}
+
+cudaError_t go(mm_grid* g, int what, int axis, int flag, const KArgs& a, double* out = nullptr,
+               int nblocks = 0) {
+  g->launches += (what == 5) ? 2 : 1;
+  typedef cudaError_t (*launcher)(int, int, int, const KArgs&, double*, int, cudaStream_t);
+  static const launcher table[2][3] = {{mm_p64_d1, mm_p64_d2, mm_p64_d3},
+                                       {mm_p32_d1, mm_p32_d2, mm_p32_d3}};
+  return table[g->prec == MM_FP64 ? 0 : 1][g->dim - 1](what, axis, flag, a, out, nblocks,
+                                                        g->stream);
+}
+
+mm_status check_device_error(mm_grid* g, const char* where) {
+  DevErr e;
+  cudaError_t ce = cudaMemcpyAsync(&e, g->err, sizeof e, cudaMemcpyDeviceToHost, g->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->stream);
+  if (ce != cudaSuccess) return fail(MM_ECUDA, "%s: %s", where, cudaGetErrorString(ce));
+  if (e.code != 0) {
+    cudaMemsetAsync(g->err, 0, sizeof(DevErr), g->stream);
+    const char* what = e.code == MM_ENONFINITE ? "inadmissible state"
+                       : e.code == MM_ENOCONV  ? "plastic return did not converge"
+                       : e.code == MM_EDT      ? "non-positive time step"
+                                               : "device error";
+    return fail((mm_status)e.code, "%s: %s at cell %lld, step %lld", where, what, e.cell, e.step);
+  }
+  return MM_OK;
+}
+
+// Start / stop the timing of one launch of the given kind.
+void prof_begin(mm_grid* g, int kind) {
+  if (!g->prof) return;
+  const size_t i = g->ev_kind.size();
+  while (g->ev.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g->ev.push_back(e);
+  }
+  g->ev_kind.push_back(kind);
+  cudaEventRecord(g->ev[2 * i], g->stream);
+}
+
+void prof_end(mm_grid* g) {
+  if (!g->prof) return;
+  cudaEventRecord(g->ev[2 * (g->ev_kind.size() - 1) + 1], g->stream);
+}
+
+// After a stream synchronisation: accumulate the recorded pairs.
+void prof_collect(mm_grid* g) {
+  if (!g->prof) return;
+  for (size_t i = 0; i < g->ev_kind.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
+      g->prof_ms[g->ev_kind[i]] += ms;
+      g->prof_n[g->ev_kind[i]] += 1;
+    }
+  }
+  g->ev_kind.clear();
+}
+
+KArgs args_for(mm_grid* g) {
+  KArgs a = g->base;
+  a.Uin = g->U[g->cur];
+  a.Uout = g->U[g->cur];
+  a.Ein = g->E[g->cur];
+  a.Eout = g->E[g->cur];
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mm_last_error(void) { return g_error.c_str(); }
+
+mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** out) {
+  if (!desc || !out) return fail(MM_EINVAL, "mm_create_grid: null argument");
+  *out = nullptr;
+  if (desc->dim < 1 || desc->dim > 3) return fail(MM_EINVAL, "dim must be 1, 2 or 3");
+  if (desc->n_materials < 1 || desc->n_materials > MM_MAXMAT)
+    return fail(MM_EINVAL, "n_materials must be 1..%d", MM_MAXMAT);
+  if (desc->precision != MM_FP64 && desc->precision != MM_FP32_SPLIT)
+    return fail(MM_EINVAL, "precision must be MM_FP64 or MM_FP32_SPLIT");
+  long long ncell = 1;
+  for (int k = 0; k < desc->dim; ++k) {
+    if (desc->n[k] < 2 || desc->n[k] > (1 << 24)) return fail(MM_EINVAL, "n[%d] out of range", k);
+    if (!(desc->hi[k] > desc->lo[k])) return fail(MM_EINVAL, "hi[%d] must exceed lo[%d]", k, k);
+    for (int s = 0; s < 2; ++s)
+      if (desc->bc[k][s] < 0 || desc->bc[k][s] > 2) return fail(MM_EINVAL, "bad boundary kind");
+    if ((desc->bc[k][0] == MM_BC_PERIODIC) != (desc->bc[k][1] == MM_BC_PERIODIC))
+      return fail(MM_EINVAL, "periodic boundaries must be set on both sides");
+    ncell *= desc->n[k];
+  }
+  if (ncell > (1LL << 31)) return fail(MM_EINVAL, "too many cells");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+    return fail(MM_ECUDA, "no CUDA device available");
+  mm_grid* g = new mm_grid();
+  g->desc = *desc;
+  g->dim = desc->dim;
+  g->nmat = desc->n_materials;
+  g->prec = desc->precision;
+  g->ncell = ncell;
+  if (cuda_stream) {
+    g->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete g;
+      return fail(MM_ECUDA, "cudaStreamCreate failed");
+    }
+    g->own_stream = true;
+  }
+  g->tot_blocks = 1024;
+  if (cudaMalloc(&g->info, sizeof(DevInfo)) != cudaSuccess ||
+      cudaMalloc(&g->err, sizeof(DevErr)) != cudaSuccess ||
+      cudaMalloc(&g->partial, sizeof(double) * g->tot_blocks * (MM_MAXMAT + 4)) != cudaSuccess ||
+      cudaMalloc(&g->tot, sizeof(double) * (MM_MAXMAT + 4)) != cudaSuccess) {
+    mm_destroy(g);
+    return fail(MM_ENOMEM, "device allocation failed");
+  }
+  cudaMemsetAsync(g->info, 0, sizeof(DevInfo), g->stream);
+  cudaMemsetAsync(g->err, 0, sizeof(DevErr), g->stream);
+  KArgs& a = g->base;
+  memset(&a, 0, sizeof a);
+  a.dim = g->dim;
+  a.nmat = g->nmat;
+  a.ncell = ncell;
+  a.dxmin = 1e300;
+  for (int k = 0; k < 3; ++k) {
+    a.n[k] = k < g->dim ? (int)desc->n[k] : 1;
+    a.lo[k] = k < g->dim ? desc->lo[k] : 0.0;
+    a.hi[k] = k < g->dim ? desc->hi[k] : 1.0;
+    a.dx[k] = (a.hi[k] - a.lo[k]) / a.n[k];
+    a.bc[k][0] = k < g->dim ? desc->bc[k][0] : 0;
+    a.bc[k][1] = k < g->dim ? desc->bc[k][1] : 0;
+    if (k < g->dim && a.dx[k] < a.dxmin) a.dxmin = a.dx[k];
+  }
+  a.info = g->info;
+  a.err = g->err;
+  a.partial = g->partial;
+  *out = g;
+  return MM_OK;
+}
+
+mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_init* init) {
+  if (!g || !mats || !init || !init->prim) return fail(MM_EINVAL, "mm_set_materials: null argument");
+  if (n != g->nmat) return fail(MM_EINVAL, "expected %d materials, got %d", g->nmat, n);
+  int nhist = 0;
+  int hslot[MM_MAXMAT] = {-1, -1};
+  MatK mk[MM_MAXMAT];
+  memset(mk, 0, sizeof mk);
+  for (int l = 0; l < n; ++l) {
+    const mm_material& m = mats[l];
+    if (m.eos != MM_EOS_IDEAL_GAS && m.eos != MM_EOS_ROMENSKII)
+      return fail(MM_EINVAL, "material %d: unknown eos", l);
+    if (m.eos == MM_EOS_IDEAL_GAS && !(m.gamma_gas > 1.0))
+      return fail(MM_EINVAL, "material %d: gamma_gas must exceed 1", l);
+    if (m.eos == MM_EOS_ROMENSKII &&
+        !(m.rho0 > 0 && m.K0 > 0 && m.G0 >= 0 && m.alpha > 0 && m.Gamma0 > 0))
+      return fail(MM_EINVAL, "material %d: Romenskii parameters out of range", l);
+    if (m.plasticity != MM_PL_NONE && m.plasticity != MM_PL_JOHNSON_COOK)
+      return fail(MM_EINVAL, "material %d: unknown plasticity model", l);
+    if (m.plasticity == MM_PL_JOHNSON_COOK && !(m.c1 >= 0 && m.c2 >= 0 && m.edot0 > 0))
+      return fail(MM_EINVAL, "material %d: Johnson-Cook parameters out of range", l);
+    if (m.damage != MM_DMG_NONE && m.damage != MM_DMG_BONORA && m.damage != MM_DMG_SIMPLE)
+      return fail(MM_EINVAL, "material %d: unknown damage model", l);
+    if (m.damage != MM_DMG_NONE && m.plasticity != MM_PL_JOHNSON_COOK)
+      return fail(MM_EINVAL, "material %d: damage needs a plasticity model", l);
+    if (m.damage == MM_DMG_BONORA &&
+        !(m.D_crit > 0 && m.D_crit < 1 && m.eps_c > m.eps_t && m.eps_t > 0 && m.alpha_D > 0 &&
+          m.n_hard > 0))
+      return fail(MM_EINVAL, "material %d: Bonora parameters out of range", l);
+    if (m.damage == MM_DMG_SIMPLE && !(m.D_crit > 0 && m.D_crit < 1))
+      return fail(MM_EINVAL, "material %d: D_crit out of range", l);
+    MatK& k = mk[l];
+    k.eos = m.eos;
+    k.plasticity = m.plasticity;
+    k.damage = m.damage;
+    k.rho0 = m.rho0;
+    k.K0 = m.K0;
+    k.G0 = m.G0;
+    k.alpha = m.alpha;
+    k.beta = m.beta;
+    k.Gamma0 = m.Gamma0;
+    k.gamma_gas = m.gamma_gas;
+    k.c1 = m.c1;
+    k.c2 = m.c2;
+    k.c3 = m.c3;
+    k.n_hard = m.n_hard;
+    k.edot0 = m.edot0;
+    k.D_crit = m.D_crit;
+    k.eps_t = m.eps_t;
+    k.eps_c = m.eps_c;
+    k.alpha_D = m.alpha_D;
+    k.poisson = m.poisson;
+    k.Ddot0 = m.Ddot0;
+    k.Gamma = m.eos == MM_EOS_IDEAL_GAS ? m.gamma_gas - 1.0 : m.Gamma0;
+    k.xi = 1.0 / k.Gamma;
+    if (m.plasticity == MM_PL_JOHNSON_COOK) hslot[l] = nhist++;
+  }
+  if (nhist > 1) return fail(MM_EINVAL, "at most one plastic material is supported");
+  const int nF = g->dim == 1 ? 3 : (g->dim == 2 ? 5 : 9);
+  const int nfield = (g->nmat - 1) + g->nmat + g->dim + 1 + nF + 2 * nhist + g->dim;
+  if (init->phi0) {
+    for (int k = 0; k < g->dim; ++k)
+      if (init->phi0_n[k] < 2 || !(init->phi0_h[k] > 0))
+        return fail(MM_EINVAL, "perturbation lattice needs >= 2 points and h > 0 per axis");
+  }
+  free_state(g);
+  g->nhist = nhist;
+  g->nfield = nfield;
+  const size_t es = elem_size(g);
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&g->U[i], es * nfield * g->ncell) != cudaSuccess) {
+      free_state(g);
+      return fail(MM_ENOMEM, "device allocation of the state failed");
+    }
+    if (g->prec == MM_FP32_SPLIT && cudaMalloc(&g->E[i], sizeof(double) * g->ncell) != cudaSuccess) {
+      free_state(g);
+      return fail(MM_ENOMEM, "device allocation of the state failed");
+    }
+  }
+  if (cudaMalloc(&g->prim, sizeof(double) * nfield * g->ncell) != cudaSuccess) {
+    free_state(g);
+    return fail(MM_ENOMEM, "device allocation of the staging buffer failed");
+  }
+  KArgs& a = g->base;
+  a.nhist = nhist;
+  a.nfield = nfield;
+  for (int l = 0; l < MM_MAXMAT; ++l) {
+    a.mat[l] = mk[l];
+    a.hslot[l] = hslot[l];
+  }
+  a.prim = g->prim;
+  a.phi0 = nullptr;
+  if (init->phi0) {
+    long long np = 1;
+    for (int k = 0; k < g->dim; ++k) {
+      a.pn[k] = (int)init->phi0_n[k];
+      a.plo[k] = init->phi0_lo[k];
+      a.ph[k] = init->phi0_h[k];
+      np *= init->phi0_n[k];
+    }
+    if (cudaMalloc(&g->phi0, sizeof(float) * np) != cudaSuccess) {
+      free_state(g);
+      return fail(MM_ENOMEM, "device allocation of the lattice failed");
+    }
+    CUDA_TRY(cudaMemcpyAsync(g->phi0, init->phi0, sizeof(float) * np, cudaMemcpyHostToDevice,
+                             g->stream));
+    a.phi0 = g->phi0;
+  }
+  CUDA_TRY(cudaMemcpyAsync(g->prim, init->prim, sizeof(double) * nfield * g->ncell,
+                           cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->info, 0, sizeof(DevInfo), g->stream));
+  CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(DevErr), g->stream));
+  g->cur = 0;
+  KArgs b = args_for(g);
+  CUDA_TRY(go(g, 0, 0, 0, b));
+  mm_status st = check_device_error(g, "mm_set_materials");
+  if (st != MM_OK) return st;
+  g->ready = true;
+  return MM_OK;
+}
+
+mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info) {
+  if (!g) return fail(MM_EINVAL, "mm_step: null grid");
+  if (!g->ready) return fail(MM_ESTATE, "mm_step before mm_set_materials");
+  if (n_steps < 0) return fail(MM_EINVAL, "n_steps must be >= 0");
+  if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(MM_EINVAL, "cfl must be in (0, 1]");
+  g->launches = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    KArgs a = args_for(g);
+    a.cfl = cfl;
+    prof_begin(g, MM_K_CFL);
+    CUDA_TRY(go(g, 2, 0, 0, a));
+    prof_end(g);
+    prof_begin(g, MM_K_DT);
+    k_dt<<<1, 1, 0, g->stream>>>(g->info, g->err, cfl, a.dxmin);
+    prof_end(g);
+    g->launches += 1;
+    CUDA_TRY(cudaGetLastError());
+    for (int d = 0; d < g->dim; ++d) {
+      KArgs b = args_for(g);
+      b.Uout = g->U[1 - g->cur];
+      b.Eout = g->E[1 - g->cur];
+      prof_begin(g, MM_K_SWEEP_X + d);
+      CUDA_TRY(go(g, 3, d, 0, b));
+      prof_end(g);
+      g->cur = 1 - g->cur;
+    }
+    KArgs c = args_for(g);
+    prof_begin(g, MM_K_SOURCES);
+    CUDA_TRY(go(g, 4, 0, 0, c));
+    prof_end(g);
+  }
+  mm_status st = check_device_error(g, "mm_step");
+  prof_collect(g);
+  if (info) {
+    DevInfo h;
+    CUDA_TRY(cudaMemcpy(&h, g->info, sizeof h, cudaMemcpyDeviceToHost));
+    info->t = h.t;
+    info->dt_last = h.dt;
+    info->smax = h.smax;
+    info->steps_done = h.steps;
+    info->bad_cell = -1;
+    if (st != MM_OK) {
+      // the message carries the cell; keep the struct consistent
+      const char* m = g_error.c_str();
+      const char* p = strstr(m, "cell ");
+      if (p) info->bad_cell = atoll(p + 5);
+    }
+  }
+  return st;
+}
+
+mm_status mm_read_fields(mm_grid* g, uint64_t field_mask, int primitive, double* host_dst,
+                         size_t dst_len) {
+  if (!g || !host_dst) return fail(MM_EINVAL, "mm_read_fields: null argument");
+  if (!g->ready) return fail(MM_ESTATE, "mm_read_fields before mm_set_materials");
+  int nsel = 0;
+  for (int f = 0; f < g->nfield; ++f)
+    if (field_mask >> f & 1ull) ++nsel;
+  if ((size_t)nsel * (size_t)g->ncell > dst_len)
+    return fail(MM_EINVAL, "destination holds %zu doubles, need %lld", dst_len,
+                (long long)nsel * g->ncell);
+  KArgs a = args_for(g);
+  CUDA_TRY(go(g, 1, 0, primitive ? 1 : 0, a));
+  int o = 0;
+  for (int f = 0; f < g->nfield; ++f) {
+    if (!(field_mask >> f & 1ull)) continue;
+    CUDA_TRY(cudaMemcpyAsync(host_dst + (size_t)o * g->ncell, g->prim + (size_t)f * g->ncell,
+                             sizeof(double) * g->ncell, cudaMemcpyDeviceToHost, g->stream));
+    ++o;
+  }
+  return check_device_error(g, "mm_read_fields");
+}
+
+mm_status mm_conserved_totals(mm_grid* g, double* out, size_t out_len) {
+  if (!g || !out) return fail(MM_EINVAL, "mm_conserved_totals: null argument");
+  if (!g->ready) return fail(MM_ESTATE, "mm_conserved_totals before mm_set_materials");
+  if (out_len < (size_t)g->nmat + 4) return fail(MM_EINVAL, "out_len must be >= %d", g->nmat + 4);
+  KArgs a = args_for(g);
+  CUDA_TRY(go(g, 5, 0, 0, a, g->tot, g->tot_blocks));
+  CUDA_TRY(cudaMemcpyAsync(out, g->tot, sizeof(double) * (g->nmat + 4), cudaMemcpyDeviceToHost,
+                           g->stream));
+  CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return MM_OK;
+}
+
+int mm_num_fields(const mm_grid* g) { return g ? g->nfield : 0; }
+int64_t mm_num_cells(const mm_grid* g) { return g ? g->ncell : 0; }
+int64_t mm_kernel_launches(const mm_grid* g) { return g ? g->launches : 0; }
+
+mm_status mm_profile_enable(mm_grid* g, int enable) {
+  if (!g) return fail(MM_EINVAL, "mm_profile_enable: null grid");
+  g->prof = enable != 0;
+  return MM_OK;
+}
+
+mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int reset) {
+  if (!g || n < 0) return fail(MM_EINVAL, "mm_profile_read: bad argument");
+  for (int k = 0; k < n && k < MM_K_COUNT; ++k) {
+    if (ms) ms[k] = g->prof_ms[k];
+    if (counts) counts[k] = g->prof_n[k];
+  }
+  if (reset)
+    for (int k = 0; k < MM_K_COUNT; ++k) {
+      g->prof_ms[k] = 0.0;
+      g->prof_n[k] = 0;
+    }
+  return MM_OK;
+}
+
+mm_status mm_destroy(mm_grid* g) {
+  if (!g) return MM_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  free_state(g);
+  cudaFree(g->info);
+  cudaFree(g->err);
+  cudaFree(g->partial);
+  cudaFree(g->tot);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return MM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// Internal declarations shared by the host API (mm_api.cu) and the kernel
+// translation units (mm_fp64.cu, mm_fp32.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MM_MAXMAT 2
+
+// Material constants as the kernels use them (copied from mm_material, plus
+// derived values computed once on the host).
+struct MatK {
+  int eos, plasticity, damage, pad;
+  double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
+  double c1, c2, c3, n_hard, edot0;
+  double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+  double xi;     // 1 / Grueneisen coefficient (ideal gas: 1/(gamma-1))
+  double Gamma;  // Grueneisen coefficient (ideal gas: gamma - 1)
+};
+
+// First failure seen on the device (sticky until the host clears it).
+struct DevErr {
+  int code;       // 0 or an mm_status
+  int pad;
+  long long cell; // linear cell index
+  long long step; // step counter at the failure
+};
+
+// Device-resident step bookkeeping; dt never leaves the device inside a step.
+struct DevInfo {
+  double t, dt, smax, pad;
+  long long steps;
+  unsigned long long smax_bits;  // running max of the signal speed (bits of a >= 0 double)
+};
+
+// Everything a kernel needs, passed by value.
+struct KArgs {
+  int dim, nmat, nhist, nfield;
+  int n[3];
+  long long ncell;
+  double dx[3], lo[3], hi[3];
+  int bc[3][2];
+  int hslot[MM_MAXMAT];
+  MatK mat[MM_MAXMAT];
+  const void* Uin;     // conserved fields [nfield][ncell] (double or float)
+  void* Uout;
+  const double* Ein;   // rho E [ncell] (FP32-split storage only)
+  double* Eout;
+  const float* phi0;
+  int pn[3];
+  double plo[3], ph[3];
+  DevInfo* info;
+  DevErr* err;
+  double cfl, dxmin;
+  double* prim;        // [nfield][ncell] doubles for init / read
+  double* partial;     // per-block partial totals
+  int tiles[3];        // tiles along the sweep axis, the transverse axis, the rest
+};
+
+// Launchers implemented in the precision x dimension translation units
+// (mm_fp64_d{1,2,3}.cu, mm_fp32_d{1,2,3}.cu).  what: 0 init, 1 read
+// (flag = primitive), 2 CFL reduction, 3 sweep along axis, 4 sources,
+// 5 totals into out (nblocks partials).
+#define MM_DECLARE_LAUNCHER(name)                                                          \
+  cudaError_t name(int what, int axis, int flag, const KArgs& a, double* out, int nblocks, \
+                   cudaStream_t s);
+MM_DECLARE_LAUNCHER(mm_p64_d1)
+MM_DECLARE_LAUNCHER(mm_p64_d2)
+MM_DECLARE_LAUNCHER(mm_p64_d3)
+MM_DECLARE_LAUNCHER(mm_p32_d1)
+MM_DECLARE_LAUNCHER(mm_p32_d2)
+MM_DECLARE_LAUNCHER(mm_p32_d3)
+#undef MM_DECLARE_LAUNCHER

@@ -1,0 +1,770 @@
+// Kernels of one explicit step: CFL reduction, the dimensionally split
+// MUSCL-Hancock sweeps (shared-memory tiles along the sweep axis), the
+// per-cell sources (perturbed plastic return + RK4 damage), initial-state
+// conversion, field read-back and FP64 totals.  Included by the precision
+// translation units, which instantiate them for FP64 and FP32-split.
+#pragma once
+
+#include "mm_phys.cuh"
+
+namespace mm {
+
+enum { ST_ENONFINITE = -4, ST_ENOCONV = -5, ST_EDT = -6 };
+enum { BC_T = 0, BC_P = 1, BC_R = 2 };
+
+__device__ __forceinline__ void report(DevErr* e, int code, long long cell, long long step) {
+  if (atomicCAS(&e->code, 0, code) == 0) {
+    e->cell = cell;
+    e->step = step;
+  }
+}
+
+// Derived quantities of a state kept beside it in shared memory (9 values).
+template <class R>
+__device__ __forceinline__ void put_aux(R* q, const Aux<R>& ax) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q[k] = ax.sd[k];
+    q[3 + k] = ax.sr[k];
+  }
+  q[6] = ax.rho;
+  q[7] = ax.cL;
+  q[8] = ax.G;
+}
+
+template <class R>
+__device__ __forceinline__ void get_aux(const R* q, Aux<R>& ax) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ax.sd[k] = q[k];
+    ax.sr[k] = q[3 + k];
+  }
+  ax.rho = q[6];
+  ax.cL = q[7];
+  ax.G = q[8];
+}
+
+template <class R>
+__device__ __forceinline__ R van_leer(R a, R b) {
+  return (a * b > R(0)) ? R(2) * a * b / (a + b) : R(0);
+}
+
+__device__ __forceinline__ long long cell_index(const KArgs& a, int x, int y, int z) {
+  return (long long)x + (long long)a.n[0] * ((long long)y + (long long)a.n[1] * z);
+}
+
+// Load the conserved state of the cell at axis position gi (ghost cells via
+// the boundary rule of that side), transverse position gw, rest rr.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, int rr,
+                                               typename P::R* c, E& e) {
+  typedef typename P::R R;
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int TD = (AX == 0) ? 1 : 0;
+  constexpr int RD = 3 - AX - TD;
+  const int n = a.n[AX];
+  int src = gi, side = -1, kind = BC_T;
+  if (gi < 0) {
+    side = 0;
+    kind = a.bc[AX][0];
+    src = kind == BC_P ? gi + n : (kind == BC_R ? -1 - gi : 0);
+  } else if (gi >= n) {
+    side = 1;
+    kind = a.bc[AX][1];
+    src = kind == BC_P ? gi - n : (kind == BC_R ? 2 * n - 1 - gi : n - 1);
+  }
+  src = src < 0 ? 0 : (src > n - 1 ? n - 1 : src);
+  int co[3];
+  co[AX] = src;
+  co[TD] = gw;
+  co[RD] = rr;
+  const long long idx = cell_index(a, co[0], co[1], co[2]);
+  const S* U = (const S*)a.Uin;
+#pragma unroll
+  for (int f = 0; f < L::NF; ++f) c[f] = (f == L::oE) ? R(0) : R(U[(long long)f * a.ncell + idx]);
+  e = P::split ? a.Ein[idx] : E(U[(long long)L::oE * a.ncell + idx]);
+  if (side >= 0 && kind == BC_P) {
+    const R Lx = R(a.hi[AX] - a.lo[AX]);
+    c[L::oX + AX] += side == 0 ? -Lx : Lx;
+  } else if (side >= 0 && kind == BC_R) {
+    c[L::oMOM + AX] = -c[L::oMOM + AX];
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) {
+      const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+      if ((i == AX) != (j == AX)) c[L::oF + k] = -c[L::oF + k];
+    }
+    const R wall = R(side == 0 ? a.lo[AX] : a.hi[AX]);
+    c[L::oX + AX] = R(2) * wall - c[L::oX + AX];
+  }
+  return idx;
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void store_cell(const KArgs& a, long long idx, const typename P::R* c,
+                                           E e) {
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  S* U = (S*)a.Uout;
+#pragma unroll
+  for (int f = 0; f < L::NF; ++f)
+    if (f != L::oE) U[(long long)f * a.ncell + idx] = S(c[f]);
+  if (P::split)
+    a.Eout[idx] = e;
+  else
+    U[(long long)L::oE * a.ncell + idx] = S(e);
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ long long load_plain(const KArgs& a, long long idx, typename P::R* c,
+                                                E& e) {
+  typedef typename P::R R;
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  const S* U = (const S*)a.Uin;
+#pragma unroll
+  for (int f = 0; f < L::NF; ++f) c[f] = (f == L::oE) ? R(0) : R(U[(long long)f * a.ncell + idx]);
+  e = P::split ? a.Ein[idx] : E(U[(long long)L::oE * a.ncell + idx]);
+  return idx;
+}
+
+// ------------------------------------------------------------------ sweep ----
+template <class P, int DIM, int AX> struct Tile;
+// FP64 (compute bound on GB300's FP64 rate): small tiles.
+template <> struct Tile<P64, 1, 0> { static constexpr int TL = 64, TW = 1, NT = 64; };
+template <> struct Tile<P64, 2, 0> { static constexpr int TL = 32, TW = 2, NT = 64; };
+template <> struct Tile<P64, 2, 1> { static constexpr int TL = 16, TW = 4, NT = 64; };
+template <> struct Tile<P64, 3, 0> { static constexpr int TL = 32, TW = 2, NT = 64; };
+template <> struct Tile<P64, 3, 1> { static constexpr int TL = 16, TW = 4, NT = 64; };
+template <> struct Tile<P64, 3, 2> { static constexpr int TL = 16, TW = 4, NT = 64; };
+// FP32-split
+template <> struct Tile<P32, 1, 0> { static constexpr int TL = 128, TW = 1, NT = 128; };
+template <> struct Tile<P32, 2, 0> { static constexpr int TL = 32, TW = 4, NT = 128; };
+template <> struct Tile<P32, 2, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 0> { static constexpr int TL = 32, TW = 4, NT = 128; };
+template <> struct Tile<P32, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
+
+template <class P, int DIM, int NMAT, int NH, int AX>
+struct SweepShape {
+  typedef typename P::R R;
+  static constexpr int TL = Tile<P, DIM, AX>::TL, TW = Tile<P, DIM, AX>::TW;
+  static constexpr int NT = Tile<P, DIM, AX>::NT;
+  static constexpr int NF = Lay<DIM, NMAT, NH>::NF;
+  static constexpr int C1 = NF + 9, C2 = NF + 9, C3 = NF + 4;
+  static constexpr int N1 = (TL + 4) * TW, N2 = (TL + 2) * TW, N3 = (TL + 1) * TW, N4 = TL * TW;
+  static constexpr size_t smem = sizeof(E) * (2 * N2 + N3) +
+                                 sizeof(R) * (size_t(N1) * C1 + 2 * size_t(N2) * C2 + size_t(N3) * C3);
+  __device__ static __forceinline__ int idx(int p, int w, int len) {
+    return AX == 0 ? w * len + p : p * TW + w;
+  }
+  __device__ static __forceinline__ void pos(int it, int len, int& p, int& w) {
+    if (AX == 0) {
+      p = it % len;
+      w = it / len;
+    } else {
+      w = it % TW;
+      p = it / TW;
+    }
+  }
+};
+
+// One sweep along AX: Uin -> Uout.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
+    k_sweep(KArgs a) {
+  typedef typename P::R R;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
+  constexpr int NF = L::NF, TL = SH::TL, TW = SH::TW, NT = SH::NT;
+  constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3;
+  constexpr int N1 = SH::N1, N2 = SH::N2, N3 = SH::N3, N4 = SH::N4;
+  constexpr int TD = (AX == 0) ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem[];
+  E* e2 = reinterpret_cast<E*>(smem);
+  E* e3 = e2 + 2 * N2;
+  R* r1 = reinterpret_cast<R*>(e3 + N3);
+  R* r2 = r1 + N1 * C1;
+  R* r3 = r2 + 2 * N2 * C2;
+  __shared__ unsigned char ok1[N1], ok2[N2];
+
+  int b = blockIdx.x;
+  const int ta = b % a.tiles[0];
+  b /= a.tiles[0];
+  const int tw = b % a.tiles[1];
+  const int rr = b / a.tiles[1];
+  const int na = a.n[AX], ntw = a.n[TD];
+  const int a0 = ta * TL, w0 = tw * TW;
+  const double dt = a.info->dt;
+  const long long step = a.info->steps;
+  const R lam = R(dt / a.dx[AX]);
+
+  // 1. primitive recovery of every tile cell, halo of two included
+  for (int it = threadIdx.x; it < N1; it += NT) {
+    int p, w;
+    SH::pos(it, TL + 4, p, w);
+    const int gi = a0 - 2 + p;
+    unsigned char okv = 0;
+    if (w0 + w < ntw && gi >= -2 && gi < na + 2) {
+      R c[NF];
+      E e;
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, e);
+      R* rec = r1 + it * C1;
+      Aux<R> ax;
+      if (PH::template u2w<AX>(a, c, e, rec, ax)) {
+        put_aux(rec + NF, ax);
+        okv = 1;
+      } else {
+        report(a.err, ST_ENONFINITE, idx, step);
+        okv = 2;
+      }
+    }
+    ok1[it] = okv;
+  }
+  __syncthreads();
+
+  // 2. van Leer reconstruction and MUSCL-Hancock half step on cells -1..TL
+  for (int it = threadIdx.x; it < N2; it += NT) {
+    int p2, w;
+    SH::pos(it, TL + 2, p2, w);
+    const int gi = a0 - 1 + p2;
+    const int im = SH::idx(p2, w, TL + 4), ic = SH::idx(p2 + 1, w, TL + 4),
+              ip = SH::idx(p2 + 2, w, TL + 4);
+    unsigned char okv = 0;
+    if (w0 + w < ntw && gi >= -1 && gi <= na && ok1[im] == 1 && ok1[ic] == 1 && ok1[ip] == 1) {
+      const R* wm = r1 + im * C1;
+      const R* wc = r1 + ic * C1;
+      const R* wp = r1 + ip * C1;
+      R uc[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
+      R cl[NF], cr[NF];
+      E el, er;
+      Aux<R> xl, xr;
+      bool good;
+      {
+        R wl[NF], wr[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const R s = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
+          wl[k] = wc[k] - R(0.5) * s;
+          wr[k] = wc[k] + R(0.5) * s;
+        }
+        good = PH::template w2u<AX>(a, wl, cl, el, xl) && PH::template w2u<AX>(a, wr, cr, er, xr);
+      }
+      if (good) {
+        R fl[NF], fr[NF], nc[NF], rowl[3], rowr[3], dF[3];
+        E fel, fer;
+        PH::template flux<AX>(cl, el, xl, fl, fel);
+        PH::template flux<AX>(cr, er, xr, fr, fer);
+        PH::template frow<AX>(cl, rowl);
+        PH::template frow<AX>(cr, rowr);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dF[j] = rowr[j] - rowl[j];
+        PH::template noncons<AX>(wc, uc, xr.u[AX] - xl.u[AX], dF, nc);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          const R inc = R(0.5) * lam * ((fl[k] - fr[k]) + nc[k]);
+          cl[k] += inc;
+          cr[k] += inc;
+        }
+        const E einc = 0.5 * E(lam) * (fel - fer);
+        el += einc;
+        er += einc;
+        R tmp[NF];
+        good = PH::template u2w<AX>(a, cl, el, tmp, xl) && PH::template u2w<AX>(a, cr, er, tmp, xr);
+      }
+      if (!good) {
+        // first order: both faces take the cell average
+        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, el);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) cr[k] = cl[k];
+        er = el;
+        get_aux(wc + NF, xl);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
+        xr = xl;
+      }
+      R* ql = r2 + (2 * it) * C2;
+      R* qr = r2 + (2 * it + 1) * C2;
+#pragma unroll
+      for (int k = 0; k < NF; ++k) {
+        ql[k] = cl[k];
+        qr[k] = cr[k];
+      }
+      put_aux(ql + NF, xl);
+      put_aux(qr + NF, xr);
+      e2[2 * it] = el;
+      e2[2 * it + 1] = er;
+      okv = 1;
+    }
+    ok2[it] = okv;
+  }
+  __syncthreads();
+
+  // 3. Riemann problem at faces -1/2 .. TL-1/2
+  for (int it = threadIdx.x; it < N3; it += NT) {
+    int f, w;
+    SH::pos(it, TL + 1, f, w);
+    const int il = SH::idx(f, w, TL + 2), ir = SH::idx(f + 1, w, TL + 2);
+    if (ok2[il] == 1 && ok2[ir] == 1) {
+      const R* ql = r2 + (2 * il + 1) * C2;  // right face state of the left cell
+      const R* qr = r2 + (2 * ir) * C2;      // left face state of the right cell
+      Aux<R> xl, xr;
+      get_aux(ql + NF, xl);
+      get_aux(qr + NF, xr);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        xl.u[k] = k < DIM ? ql[L::oMOM + k] / xl.rho : R(0);
+        xr.u[k] = k < DIM ? qr[L::oMOM + k] / xr.rho : R(0);
+      }
+      R fo[NF], row[3], uf;
+      E fe;
+      PH::template riemann<AX>(ql, e2[2 * il + 1], xl, qr, e2[2 * ir], xr, fo, fe, uf, row);
+      R* q3 = r3 + it * C3;
+#pragma unroll
+      for (int k = 0; k < NF; ++k) q3[k] = fo[k];
+      q3[NF] = uf;
+      q3[NF + 1] = row[0];
+      q3[NF + 2] = row[1];
+      q3[NF + 3] = row[2];
+      e3[it] = fe;
+    }
+  }
+  __syncthreads();
+
+  // 4. conservative update with the non-conservative terms
+  for (int it = threadIdx.x; it < N4; it += NT) {
+    int p4, w;
+    SH::pos(it, TL, p4, w);
+    const int gi = a0 + p4;
+    if (w0 + w < ntw && gi < na) {
+      const int fl = SH::idx(p4, w, TL + 1), fr = SH::idx(p4 + 1, w, TL + 1);
+      const int ic = SH::idx(p4 + 2, w, TL + 4);
+      if (ok1[ic] != 1) continue;
+      R c[NF];
+      E e;
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, e);
+      const R* wc = r1 + ic * C1;
+      const R* ql = r3 + fl * C3;
+      const R* qr = r3 + fr * C3;
+      R uc[3], dF[3], nc[NF];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dF[j] = qr[NF + 1 + j] - ql[NF + 1 + j];
+      PH::template noncons<AX>(wc, uc, qr[NF] - ql[NF], dF, nc);
+#pragma unroll
+      for (int k = 0; k < NF; ++k) c[k] = c[k] + lam * ((ql[k] - qr[k]) + nc[k]);
+      e = e + E(lam) * (e3[fl] - e3[fr]);
+      store_cell<P, DIM, NMAT, NH>(a, idx, c, e);
+    }
+  }
+}
+
+// ------------------------------------------------------------- sources ----
+// Perturbation lookup phi(x) = phi0(X): multilinear, 1 outside the lattice.
+template <int DIM>
+__device__ __forceinline__ double lookup(const KArgs& a, const double X[3]) {
+  if (!a.phi0) return 1.0;
+  long long i0[3] = {0, 0, 0};
+  double w[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const double s = (X[k] - a.plo[k]) / a.ph[k];
+    if (!(s >= 0.0) || !(s <= double(a.pn[k] - 1))) return 1.0;
+    long long i = (long long)floor(s);
+    if (i > a.pn[k] - 2) i = a.pn[k] - 2;
+    i0[k] = i;
+    w[k] = s - double(i);
+  }
+  double v = 0.0;
+#pragma unroll
+  for (int c = 0; c < (1 << DIM); ++c) {
+    double wt = 1.0;
+    long long idx = 0, str = 1;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const int bit = (c >> k) & 1;
+      wt *= bit ? w[k] : 1.0 - w[k];
+      idx += (i0[k] + bit) * str;
+      str *= a.pn[k];
+    }
+    v += wt * double(__ldg(a.phi0 + idx));
+  }
+  return v;
+}
+
+// Mixture yield stress sum_l phi_l phi (1-D_l) sigma_Y,l (Johnson-Cook, rate
+// factor floored at 1, zero at critical damage) and its derivative in dl.
+template <int NMAT>
+__device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, const double* eps,
+                                            const double* D, double phihat, double dt, double dl,
+                                            double* dY) {
+  double Y = 0.0, dYs = 0.0;
+#pragma unroll
+  for (int l = 0; l < NMAT; ++l) {
+    const MatK& m = a.mat[l];
+    if (m.plasticity != 1) continue;
+    if (m.damage != 0 && D[l] >= m.D_crit) continue;
+    const double psi = m.damage != 0 ? 1.0 - D[l] : 1.0;
+    const double e = (eps[l] > 0.0 ? eps[l] : 0.0) + dl;
+    double hard = m.c1, dhard = 0.0;
+    if (m.c2 != 0.0) {
+      hard += m.c2 * pow(e, m.n_hard);
+      if (e > 0.0) dhard = m.c2 * m.n_hard * pow(e, m.n_hard - 1.0);
+    }
+    double Rr = 1.0, dR = 0.0;
+    if (m.c3 != 0.0 && dl > 0.0) {
+      const double r = 1.0 + m.c3 * log(dl / (dt * m.edot0));
+      if (r > 1.0) {
+        Rr = r;
+        dR = m.c3 / dl;
+      }
+    }
+    const double wgt = phi[l] * phihat * psi;
+    Y += wgt * hard * Rr;
+    dYs += wgt * (dhard * Rr + hard * dR);
+  }
+  if (dY) *dY = dYs;
+  return Y;
+}
+
+__device__ __forceinline__ double eps_thresh(double et, double ec, double n, double Rt) {
+  const double num = pow(ec, 2.0 * n) - pow(et, 2.0 * n);
+  const double den = pow(ec, 2.0 * n / Rt) - pow(et, 2.0 * n / Rt);
+  return pow(et, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));
+}
+
+__device__ __forceinline__ double dmg_rate(const MatK& m, double D, double eps, double ed,
+                                           double p, double Rt, double th) {
+  if (m.damage == 2) return m.Ddot0 * (1.0 - D) * ed;
+  if (!(p < 0.0) || !(eps > th)) return 0.0;
+  if (D >= m.D_crit) return 0.0;
+  const double aD = m.alpha_D, Dc = m.D_crit;
+  return aD * pow(Dc, 1.0 / aD) / log(m.eps_c / m.eps_t) * Rt * pow(Dc - D, (aD - 1.0) / aD) *
+         ed / eps;
+}
+
+__device__ __forceinline__ double damage_rk4(const MatK& m, double D, double eps0, double deps,
+                                             double dt, double p, double seq, double rho) {
+  if (m.damage == 0 || !(deps > 0.0)) return D;
+  double Rt = 1.0, th = 0.0;
+  if (m.damage == 1) {
+    if (!(seq > 0.0)) return D;
+    const double x = p / seq;
+    Rt = 2.0 / 3.0 * (1.0 + m.poisson) + 3.0 * (1.0 - 2.0 * m.poisson) * (m.rho0 / rho) * (x * x);
+    th = eps_thresh(m.eps_t, m.eps_c, m.n_hard, Rt);
+  }
+  const double ed = deps / dt;
+  const double k1 = dmg_rate(m, D, eps0, ed, p, Rt, th);
+  const double k2 = dmg_rate(m, D + 0.5 * dt * k1, eps0 + 0.5 * deps, ed, p, Rt, th);
+  const double k3 = dmg_rate(m, D + 0.5 * dt * k2, eps0 + 0.5 * deps, ed, p, Rt, th);
+  const double k4 = dmg_rate(m, D + dt * k3, eps0 + deps, ed, p, Rt, th);
+  double Dn = D + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+  if (Dn < 0.0) Dn = 0.0;
+  if (Dn > m.D_crit) Dn = m.D_crit;
+  return Dn;
+}
+
+// Per-cell sources after the sweeps (in place): renormalise det Fbar = 1,
+// radial return in Hencky space to the perturbed yield stress (Newton on
+// the plastic increment in FP64), then RK4 damage.
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(128) k_sources(KArgs a) {
+  typedef typename P::R R;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NF = L::NF;
+  const double dt = a.info->dt;
+  const long long step = a.info->steps;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    R c[NF], w[NF];
+    E e;
+    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    Aux<R> ax;
+    if (!PH::template u2w<0>(a, c, e, w, ax)) {
+      report(a.err, ST_ENONFINITE, cell, step);
+      continue;
+    }
+    double phi[NMAT], eps[NMAT], Dm[NMAT];
+    R rho[NMAT], Dr[NMAT], phir[NMAT];
+    {
+      R s = R(0);
+#pragma unroll
+      for (int l = 0; l < NMAT - 1; ++l) {
+        phir[l] = c[L::oPHI + l];
+        s += phir[l];
+      }
+      phir[NMAT - 1] = R(1) - s;
+    }
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      phi[l] = double(phir[l]);
+      rho[l] = w[L::oARHO + l];
+      eps[l] = 0.0;
+      Dm[l] = 0.0;
+#pragma unroll
+      for (int h = 0; h < NH; ++h)
+        if (a.hslot[l] == h) {
+          eps[l] = double(w[L::oH + 2 * h]);
+          Dm[l] = double(w[L::oH + 2 * h + 1]);
+        }
+      Dr[l] = R(Dm[l]);
+    }
+    double Xc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) Xc[k] = double(w[L::oX + k]);
+    const double phihat = lookup<DIM>(a, Xc);
+    // shear modulus of the mixture; whether the cell may yield
+    double Gm = 0.0;
+    bool can_yield = true;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      const MatK& m = a.mat[l];
+      R te, tp, tdp, tG;
+      thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
+      Gm += phi[l] * double(tG);
+      if (m.eos == 1 && m.G0 > 0.0 && m.plasticity != 1) can_yield = false;
+    }
+    // det Fbar = 1
+    R X[9];
+    PH::fullX(c, X);
+    if (P::aform) {
+      // A <- (I + A)/cbrt(det) - I with det - 1 expanded in A
+      const R ed = (X[0] + X[4] + X[8]) +
+                   (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
+                    X[5] * X[7]) +
+                   (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                    X[2] * (X[3] * X[7] - X[4] * X[6]));
+      const R cm1 = mexpm1(mlog1p(ed) / R(3));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) X[k] = (X[k] - ((k % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
+    } else {
+      const R det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                    X[2] * (X[3] * X[7] - X[4] * X[6]);
+      const R c3 = mcbrt(det);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) X[k] /= c3;
+    }
+    R devH[9], h[3], V[9];
+    if (!hencky<P::aform>(X, devH, h, V)) {
+      report(a.err, ST_ENONFINITE, cell, step);
+      continue;
+    }
+    double dl = 0.0;
+    if (can_yield && Gm > 0.0) {
+      const double J = sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
+                            double(h[2]) * double(h[2]));
+      const double str = sqrt(6.0) * Gm * J;
+      const double Y0 = yield_mix<NMAT>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
+      if (str > Y0) {
+        const double b0 = str / (3.0 * Gm);
+        double lo = 0.0, hi = b0, x = (str - Y0) / (3.0 * Gm);
+        bool conv = false;
+        for (int it = 0; it < 200; ++it) {
+          double dY;
+          const double Y = yield_mix<NMAT>(a, phi, eps, Dm, phihat, dt, x, &dY);
+          const double g = str - 3.0 * Gm * x - Y;
+          if (fabs(g) <= 8.0 * 2.220446049250313e-16 * str) {
+            conv = true;
+            break;
+          }
+          if (g > 0.0) lo = x; else hi = x;
+          double nx = x - g / (-3.0 * Gm - dY);
+          if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+          if (fabs(nx - x) <= 4.0 * 2.220446049250313e-16 * b0) {
+            x = nx;
+            conv = true;
+            break;
+          }
+          x = nx;
+        }
+        if (!conv) {
+          report(a.err, ST_ENOCONV, cell, step);
+          continue;
+        }
+        dl = x;
+        const R k = R((str - 3.0 * Gm * dl) / str);
+        // Fbar <- S Fbar, S = V diag(exp((k-1) h)) V^T (the rotation is kept);
+        // in A form A <- (S - I)(I + A) + A with S - I from expm1
+        R m1[3], Sm[9], Xn[9];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            Sm[3 * i + j] = V[3 * i + 0] * m1[0] * V[3 * j + 0] + V[3 * i + 1] * m1[1] * V[3 * j + 1] +
+                            V[3 * i + 2] * m1[2] * V[3 * j + 2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const R sx = Sm[3 * i + 0] * X[0 + j] + Sm[3 * i + 1] * X[3 + j] + Sm[3 * i + 2] * X[6 + j];
+            Xn[3 * i + j] = P::aform ? Sm[3 * i + j] + sx + X[3 * i + j] : sx;
+          }
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) X[k2] = Xn[k2];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = X[FC<DIM>::idx(k)];
+    if (dl > 0.0) {
+      R w2[NF];
+      Aux<R> as;
+      if (!PH::template u2w<0>(a, c, e, w2, as)) {
+        report(a.err, ST_ENONFINITE, cell, step);
+        continue;
+      }
+      typename PH::Mix mx;
+      PH::mixture(a, phir, rho, Dr, X, mx);
+      const double seq = sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2));
+#pragma unroll
+      for (int l = 0; l < NMAT; ++l) {
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh)
+          if (a.hslot[l] == hh) {
+            const R arho = c[L::oARHO + l];
+            const double Dn =
+                damage_rk4(a.mat[l], Dm[l], eps[l], dl, dt, double(w2[L::oE]), seq, double(rho[l]));
+            c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
+            c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
+          }
+      }
+    }
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, e);
+  }
+}
+
+// --------------------------------------------------------------- CFL ----
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_cfl(KArgs a) {
+  typedef typename P::R R;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  constexpr int NF = Lay<DIM, NMAT, NH>::NF;
+  const long long step = a.info->steps;
+  double smax = 0.0;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    R c[NF], w[NF];
+    E e;
+    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    Aux<R> ax;
+    if (!PH::template u2w<0>(a, c, e, w, ax)) {
+      report(a.err, ST_ENONFINITE, cell, step);
+      continue;
+    }
+    R v = R(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) v = fmax(v, mabs(ax.u[k]));
+    const double s = double(v + ax.cL);
+    smax = s > smax ? s : smax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+    atomicMax(&a.info->smax_bits, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// ------------------------------------------------------ init and read ----
+template <class P, int DIM, int NMAT, int NH>
+__global__ void k_init(KArgs a) {
+  typedef typename P::R R;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NF = L::NF;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    R w[NF], c[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double v = a.prim[(long long)f * a.ncell + cell];
+      if (P::aform && f >= L::oF && f < L::oF + L::NFC) {
+        const int ij = FC<DIM>::idx(f - L::oF);
+        if (ij % 4 == 0) v -= 1.0;
+      }
+      w[f] = R(v);
+    }
+    E e;
+    Aux<R> ax;
+    if (!PH::template w2u<0>(a, w, c, e, ax)) report(a.err, ST_ENONFINITE, cell, 0);
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, e);
+  }
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__global__ void k_read(KArgs a, int primitive) {
+  typedef typename P::R R;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NF = L::NF;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    R c[NF], w[NF];
+    E e;
+    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    const R* src = c;
+    if (primitive) {
+      Aux<R> ax;
+      if (!PH::template u2w<0>(a, c, e, w, ax)) report(a.err, ST_ENONFINITE, cell, 0);
+      src = w;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double v = double(src[f]);
+      if (f == L::oE && !primitive) v = e;
+      if (P::aform && f >= L::oF && f < L::oF + L::NFC) {
+        const int ij = FC<DIM>::idx(f - L::oF);
+        if (ij % 4 == 0) v += 1.0;
+      }
+      a.prim[(long long)f * a.ncell + cell] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ totals ----
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_totals(KArgs a) {
+  typedef typename P::R R;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NQ = NMAT + 4;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  typedef typename P::S S;
+  const S* U = (const S*)a.Uin;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) acc[l] += double(U[(long long)(L::oARHO + l) * a.ncell + cell]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+      acc[NMAT + k] += double(U[(long long)(L::oMOM + k) * a.ncell + cell]);
+    acc[NMAT + 3] += P::split ? a.Ein[cell] : double(U[(long long)L::oE * a.ncell + cell]);
+  }
+  __shared__ double red[8][NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i][threadIdx.x];
+    a.partial[(long long)blockIdx.x * NQ + threadIdx.x] = s;
+  }
+}
+
+}  // namespace mm

@@ -1,0 +1,589 @@
+// Device-side closures, mixture rule, fluxes and Riemann solver of the
+// diffuse-interface elastoplastic method (Wallis, Barton & Nikiforakis,
+// arXiv 2210.04037), templated on the precision policy:
+//   P64: every quantity in FP64; the deformation tensor is carried as Fbar
+//        and every closure is evaluated in the order of its definition, so
+//        the only differences from a plain FP64 evaluation are the last-ulp
+//        differences of the math library.
+//   P32: reconstruction, fluxes and closures in FP32; total energy, the
+//        energy recovery, the plastic-return iteration and all totals in
+//        FP64.  The deformation tensor is carried as A = Fbar - I so that the
+//        small elastic strains of metals keep their relative precision.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "mm_internal.h"
+
+namespace mm {
+
+typedef double E;  // energy scalar type in both precisions
+
+struct P64 {
+  typedef double R;
+  typedef double S;
+  static constexpr bool split = false;
+  static constexpr bool aform = false;
+};
+struct P32 {
+  typedef float R;
+  typedef float S;
+  static constexpr bool split = true;
+  static constexpr bool aform = true;
+};
+
+// ---------------------------------------------------------------- math ----
+__device__ __forceinline__ double mlog(double x) { return log(x); }
+__device__ __forceinline__ float mlog(float x) { return logf(x); }
+__device__ __forceinline__ double mlog1p(double x) { return log1p(x); }
+__device__ __forceinline__ float mlog1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double mexp(double x) { return exp(x); }
+__device__ __forceinline__ float mexp(float x) { return expf(x); }
+__device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
+__device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double mpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float mpow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double mcbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float mcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double mabs(double x) { return fabs(x); }
+__device__ __forceinline__ float mabs(float x) { return fabsf(x); }
+__device__ __forceinline__ bool mfinite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool mfinite(float x) { return isfinite(x); }
+
+template <class R> struct Eps;
+template <> struct Eps<double> { static constexpr double jacobi = 1e-32; };
+template <> struct Eps<float> { static constexpr float jacobi = 1e-14f; };
+
+// -------------------------------------------------------------- layout ----
+template <int DIM> struct FC;
+template <> struct FC<1> {
+  static constexpr int n = 3;
+  __host__ __device__ static constexpr int idx(int c) { return c == 0 ? 0 : (c == 1 ? 4 : 8); }
+};
+template <> struct FC<2> {
+  static constexpr int n = 5;
+  __host__ __device__ static constexpr int idx(int c) {
+    return c == 0 ? 0 : (c == 1 ? 1 : (c == 2 ? 3 : (c == 3 ? 4 : 8)));
+  }
+};
+template <> struct FC<3> {
+  static constexpr int n = 9;
+  __host__ __device__ static constexpr int idx(int c) { return c; }
+};
+
+template <int DIM, int NMAT, int NH>
+struct Lay {
+  static constexpr int NPHI = NMAT - 1;
+  static constexpr int NFC = FC<DIM>::n;
+  static constexpr int oPHI = 0;
+  static constexpr int oARHO = NPHI;
+  static constexpr int oMOM = oARHO + NMAT;
+  static constexpr int oE = oMOM + DIM;
+  static constexpr int oF = oE + 1;
+  static constexpr int oH = oF + NFC;
+  static constexpr int oX = oH + 2 * NH;
+  static constexpr int NF = oX + DIM;
+};
+
+// ------------------------------------------------- single-material EOS ----
+// Reference curve of material m at phasic density rho, damage factor psi and
+// shear invariant J2: e_ref = e_c + e_s, p_ref = rho^2 de_ref/drho,
+// dp_ref/drho and G.  Romenskii cold energy psi K0/(2 rho alpha^2)
+// (eta^alpha - 1)^2, G = psi G0 eta^(beta+1), e_s = G J2 / rho, so
+// p_c = psi K0/(2 alpha^2) (2 alpha q eta^alpha - q^2) with q = eta^alpha - 1
+// and p_s = beta G J2.  Ideal gas: all zero.
+template <class R>
+__device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, R& p,
+                                       R& dp, R& G) {
+  if (m.eos == 0) {
+    e = R(0); p = R(0); dp = R(0); G = R(0);
+    return;
+  }
+  const R a = R(m.alpha), rho0 = R(m.rho0), K0 = R(m.K0), bb = R(m.beta);
+  const R eta = rho / rho0;
+  const R ea = (m.alpha == 1.0) ? eta : mpow(eta, a);
+  const R q = ea - R(1);
+  const R ec = psi * K0 / (R(2) * rho * a * a) * (q * q);
+  const R pc = psi * K0 / (R(2) * a * a) * (R(2) * a * q * ea - q * q);
+  const R dpc = psi * K0 * mpow(eta, a - R(1)) * ((R(2) * a - R(1)) * ea + (R(1) - a)) / (a * rho0);
+  const R Gs = psi * R(m.G0) * mpow(eta, bb + R(1));
+  e = ec + Gs * J2 / rho;
+  p = pc + bb * Gs * J2;
+  dp = dpc + bb * (bb + R(1)) * Gs * J2 / rho;
+  G = Gs;
+}
+
+// ------------------------------------------- Hencky strain by Jacobi ----
+// One symmetric Schur rotation of the (P,Q) plane.
+template <int P, int Q, class R>
+__device__ __forceinline__ void jrot(R a[9], R V[9]) {
+  const R apq = a[3 * P + Q];
+  if (apq == R(0)) return;
+  const R app = a[3 * P + P], aqq = a[3 * Q + Q];
+  const R theta = (aqq - app) / (R(2) * apq);
+  R t = R(1) / (mabs(theta) + msqrt(theta * theta + R(1)));
+  if (theta < R(0)) t = -t;
+  const R c = R(1) / msqrt(t * t + R(1));
+  const R s = t * c;
+  constexpr int K = 3 - P - Q;
+  a[3 * P + P] = app - t * apq;
+  a[3 * Q + Q] = aqq + t * apq;
+  a[3 * P + Q] = R(0);
+  a[3 * Q + P] = R(0);
+  const R akp = a[3 * K + P], akq = a[3 * K + Q];
+  a[3 * K + P] = c * akp - s * akq;
+  a[3 * P + K] = a[3 * K + P];
+  a[3 * K + Q] = s * akp + c * akq;
+  a[3 * Q + K] = a[3 * K + Q];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const R vp = V[3 * r + P], vq = V[3 * r + Q];
+    V[3 * r + P] = c * vp - s * vq;
+    V[3 * r + Q] = s * vp + c * vq;
+  }
+}
+
+// Cyclic Jacobi on a symmetric 3x3 matrix (destroyed): eigenvalues mu and
+// eigenvectors in the columns of V.
+template <class R>
+__device__ __forceinline__ void jacobi(R a[9], R mu[3], R V[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) V[k] = (k % 4 == 0) ? R(1) : R(0);
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const R off = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+    const R dd = a[0] * a[0] + a[4] * a[4] + a[8] * a[8];
+    if (off <= Eps<R>::jacobi * dd) break;
+    jrot<0, 1>(a, V);
+    jrot<0, 2>(a, V);
+    jrot<1, 2>(a, V);
+  }
+  mu[0] = a[0];
+  mu[1] = a[4];
+  mu[2] = a[8];
+}
+
+// dev(H) = dev(1/2 ln b), b = Fbar Fbar^T, with its deviatoric eigenvalues h
+// and eigenvectors V.  X is Fbar (AF = false) or A = Fbar - I (AF = true,
+// where b - I = A + A^T + A A^T and ln(1 + mu) keeps small strains exact).
+// Returns false if b is not positive definite.
+template <bool AF, class R>
+__device__ __forceinline__ bool hencky(const R X[9], R devH[9], R h[3], R V[9]) {
+  R B[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      R s = X[3 * i + 0] * X[3 * j + 0] + X[3 * i + 1] * X[3 * j + 1] + X[3 * i + 2] * X[3 * j + 2];
+      if (AF) s = X[3 * i + j] + X[3 * j + i] + s;
+      B[3 * i + j] = s;
+      B[3 * j + i] = s;
+    }
+  R mu[3];
+  jacobi(B, mu, V);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (AF) {
+      if (!(mu[k] > R(-1)) || !mfinite(mu[k])) return false;
+      h[k] = R(0.5) * mlog1p(mu[k]);
+    } else {
+      if (!(mu[k] > R(0)) || !mfinite(mu[k])) return false;
+      h[k] = R(0.5) * mlog(mu[k]);
+    }
+  }
+  const R tr = (h[0] + h[1] + h[2]) / R(3);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) h[k] -= tr;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      devH[3 * i + j] = V[3 * i + 0] * h[0] * V[3 * j + 0] + V[3 * i + 1] * h[1] * V[3 * j + 1] +
+                        V[3 * i + 2] * h[2] * V[3 * j + 2];
+  return true;
+}
+
+// ------------------------------------------------------------ states ----
+// Derived quantities of one state: velocity, the stress column d (sigma_kd,
+// momentum flux and tangential tractions), the stress row d (sigma_dk, energy
+// flux), density, longitudinal sound speed, mixture shear modulus.
+template <class R>
+struct Aux {
+  R u[3];
+  R sd[3];
+  R sr[3];
+  R rho, cL, G;
+};
+
+template <class P, int DIM, int NMAT, int NH>
+struct Phys {
+  typedef typename P::R R;
+  typedef Lay<DIM, NMAT, NH> L;
+  static constexpr int NF = L::NF;
+  static constexpr bool AF = P::aform;
+
+  // Full 3x3 stored tensor (Fbar, or A = Fbar - I): inactive comps are 0 off
+  // the diagonal (and the diagonal is always stored).
+  __device__ static __forceinline__ void fullX(const R* c, R X[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) X[FC<DIM>::idx(k)] = c[L::oF + k];
+  }
+
+  // Value of Fbar_ij from a stored component.
+  __device__ static __forceinline__ R Fv(int i, int j, R s) {
+    return AF ? ((i == j ? R(1) : R(0)) + s) : s;
+  }
+
+  __device__ static __forceinline__ R damage_of(const KArgs& a, const R* w, int l) {
+    R D = R(0);
+#pragma unroll
+    for (int h = 0; h < NH; ++h)
+      if (h == a.hslot[l]) D = w[L::oH + 2 * h + 1];
+    return D;
+  }
+
+  // Mixture quantities of the isobaric Allaire closure with one deformation
+  // tensor: per-material e_ref, p_ref, dp_ref, and xi = sum phi_l/Gamma_l,
+  // G_mix = sum phi_l G_l.
+  struct Mix {
+    R e[NMAT], p[NMAT], dp[NMAT];
+    R xi, Gm, J2;
+    R devH[9];
+  };
+
+  __device__ static __forceinline__ bool mixture(const KArgs& a, const R phi[NMAT],
+                                                 const R rho[NMAT], const R D[NMAT],
+                                                 const R X[9], Mix& mx) {
+    R h[3], V[9];
+    if (!hencky<AF>(X, mx.devH, h, V)) return false;
+    mx.J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    mx.xi = R(0);
+    mx.Gm = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      const MatK& m = a.mat[l];
+      const R psi = m.damage != 0 ? R(1) - D[l] : R(1);
+      R G;
+      thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G);
+      mx.xi += phi[l] / R(m.Gamma);
+      mx.Gm += phi[l] * G;
+    }
+    return true;
+  }
+
+  // sigma = -p I + 2 G_mix dev(H); c_L^2 = c^2 + 4/3 G_mix/rho with the
+  // frozen mixture speed xi c^2 = sum y_l xi_l c_l^2,
+  // c_l^2 = dp_ref,l + (Gamma_l + 1)(p - p_ref,l)/rho_l.
+  template <int AX>
+  __device__ static __forceinline__ bool finish(const KArgs& a, R p, const R rho[NMAT],
+                                                const R arho[NMAT], const Mix& mx, Aux<R>& ax) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ax.sd[k] = (k == AX ? -p : R(0)) + R(2) * mx.Gm * mx.devH[3 * k + AX];
+      ax.sr[k] = (k == AX ? -p : R(0)) + R(2) * mx.Gm * mx.devH[3 * AX + k];
+    }
+    R s = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      const R Gam = R(a.mat[l].Gamma);
+      const R cl2 = mx.dp[l] + (Gam + R(1)) * (p - mx.p[l]) / rho[l];
+      s += (arho[l] / ax.rho) * (R(1) / Gam) * cl2;
+    }
+    const R c2 = s / mx.xi;
+    ax.G = mx.Gm;
+    const R cL2 = c2 + (R(4) / R(3)) * mx.Gm / ax.rho;
+    if (!(cL2 > R(0)) || !mfinite(cL2)) return false;
+    ax.cL = msqrt(cL2);
+    return true;
+  }
+
+  // primitive w -> conserved (c, rhoE).  w[oE] holds p.
+  template <int AX>
+  __device__ static bool w2u(const KArgs& a, const R* w, R* c, E& rhoE, Aux<R>& ax) {
+    R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
+    R s = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) {
+      phi[l] = w[L::oPHI + l];
+      s += phi[l];
+    }
+    phi[NMAT - 1] = R(1) - s;
+    ax.rho = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      if (!(phi[l] > R(0))) return false;
+      rho[l] = w[L::oARHO + l];
+      if (!(rho[l] > R(0))) return false;
+      arho[l] = phi[l] * rho[l];
+      ax.rho += arho[l];
+      D[l] = damage_of(a, w, l);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ax.u[k] = k < DIM ? w[L::oMOM + k] : R(0);
+    const R p = w[L::oE];
+    R X[9];
+    fullX(w, X);
+    Mix mx;
+    if (!mixture(a, phi, rho, D, X, mx)) return false;
+    E rhoe = 0.0;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l)
+      rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (E(p) - E(mx.p[l])) / E(a.mat[l].Gamma);
+    const E ke = 0.5 * E(ax.rho) *
+                 (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) c[L::oPHI + l] = phi[l];
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) c[L::oARHO + l] = arho[l];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) c[L::oMOM + k] = ax.rho * ax.u[k];
+    c[L::oE] = R(0);
+    rhoE = rhoe + ke;
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = w[L::oF + k];
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+#pragma unroll
+      for (int h = 0; h < NH; ++h)
+        if (a.hslot[l] == h) {
+          c[L::oH + 2 * h] = arho[l] * w[L::oH + 2 * h];
+          c[L::oH + 2 * h + 1] = arho[l] * w[L::oH + 2 * h + 1];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) c[L::oX + k] = w[L::oX + k];
+    return finish<AX>(a, p, rho, arho, mx, ax);
+  }
+
+  // conserved (c, rhoE) -> primitive w (w[oE] = p), with
+  // p = (rho e - sum_l phi_l rho_l e_ref,l + sum_l phi_l p_ref,l / Gamma_l) / xi.
+  template <int AX>
+  __device__ static bool u2w(const KArgs& a, const R* c, E rhoE, R* w, Aux<R>& ax) {
+    R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
+    R s = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) {
+      phi[l] = c[L::oPHI + l];
+      s += phi[l];
+    }
+    phi[NMAT - 1] = R(1) - s;
+    ax.rho = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      arho[l] = c[L::oARHO + l];
+      if (!(phi[l] > R(0)) || !(arho[l] > R(0))) return false;
+      rho[l] = arho[l] / phi[l];
+      ax.rho += arho[l];
+    }
+    bool ok = true;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      R ar = R(1);
+#pragma unroll
+      for (int l = 0; l < NMAT; ++l)
+        if (a.hslot[l] == h) ar = arho[l];
+      w[L::oH + 2 * h] = c[L::oH + 2 * h] / ar;
+      w[L::oH + 2 * h + 1] = c[L::oH + 2 * h + 1] / ar;
+    }
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) D[l] = damage_of(a, w, l);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ax.u[k] = k < DIM ? c[L::oMOM + k] / ax.rho : R(0);
+    R X[9];
+    fullX(c, X);
+    Mix mx;
+    if (!mixture(a, phi, rho, D, X, mx)) return false;
+    const E ke = 0.5 * E(ax.rho) *
+                 (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
+    E num = rhoE - ke;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l)
+      num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
+    const R p = R(num / E(mx.xi));
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) w[L::oPHI + l] = phi[l];
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) w[L::oARHO + l] = rho[l];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) w[L::oMOM + k] = ax.u[k];
+    w[L::oE] = p;
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) w[L::oF + k] = c[L::oF + k];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) w[L::oX + k] = c[L::oX + k];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) ok = ok && mfinite(w[k]) && mfinite(c[k]);
+    ok = ok && isfinite(rhoE);
+    if (!ok) return false;
+    return finish<AX>(a, p, rho, arho, mx, ax);
+  }
+
+  // Row AX of Fbar of a state vector.
+  template <int AX>
+  __device__ static __forceinline__ void frow(const R* c, R row[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R v = R(0);
+#pragma unroll
+      for (int q = 0; q < L::NFC; ++q)
+        if (FC<DIM>::idx(q) == 3 * AX + j) v = c[L::oF + q];
+      row[j] = Fv(AX, j, v);
+    }
+  }
+
+  // Physical flux along AX: q u_d for the advected densities, rho u_k u_d -
+  // sigma_kd, rho E u_d - sigma_dj u_j, Fbar_ij u_d - Fbar_dj u_i (zero for
+  // row d).
+  template <int AX>
+  __device__ static __forceinline__ void flux(const R* c, E rhoE, const Aux<R>& ax, R* f,
+                                              E& fe) {
+    const R ud = ax.u[AX];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) f[L::oPHI + l] = c[L::oPHI + l] * ud;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) f[L::oARHO + l] = c[L::oARHO + l] * ud;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) f[L::oMOM + k] = c[L::oMOM + k] * ud - ax.sd[k];
+    f[L::oE] = R(0);
+    fe = rhoE * E(ud) - (E(ax.sr[0]) * E(ax.u[0]) + E(ax.sr[1]) * E(ax.u[1]) +
+                         E(ax.sr[2]) * E(ax.u[2]));
+    R row[3];
+    frow<AX>(c, row);
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) {
+      const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+      f[L::oF + k] = (i == AX) ? R(0) : Fv(i, j, c[L::oF + k]) * ud - row[j] * ax.u[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NH; ++k) f[L::oH + k] = c[L::oH + k] * ud;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) f[L::oX + k] = c[L::oX + k] * ud;
+  }
+
+  // Non-conservative terms per unit 1/dx: phi and X take q_c du; the
+  // deformation tensor 2/3 Fbar_ij du - u_i dFbar_dj.
+  template <int AX>
+  __device__ static __forceinline__ void noncons(const R* wc, const R uc[3], R du,
+                                                 const R dFrow[3], R* nc) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) nc[k] = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) nc[L::oPHI + l] = wc[L::oPHI + l] * du;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) nc[L::oX + k] = wc[L::oX + k] * du;
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) {
+      const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+      nc[L::oF + k] = (R(2) / R(3)) * Fv(i, j, wc[L::oF + k]) * du - uc[i] * dFrow[j];
+    }
+  }
+
+  // HLLD-type Riemann solver for the elastic mixture: outer waves S_L, S_R
+  // (Davis), contact S*, shear waves S* -/+ c_s inside the star regions.
+  // Jumps from the Rankine-Hugoniot conditions of each wave; with G = 0 it
+  // is the HLLC solver.  Outputs the flux, the normal velocity at the face
+  // and the row d of Fbar on the upwind side of the contact.
+  template <int AX>
+  __device__ static void riemann(const R* cL_, E eL, const Aux<R>& aL, const R* cR_, E eR,
+                                 const Aux<R>& aR, R* fo, E& feo, R& uface, R frowo[3]) {
+    const R uL = aL.u[AX], uR = aR.u[AX];
+    const R a1 = uL - aL.cL, a2 = uR - aR.cL;
+    const R b1 = uL + aL.cL, b2 = uR + aR.cL;
+    const R SL = a1 < a2 ? a1 : a2;
+    const R SR = b1 > b2 ? b1 : b2;
+    const R sL = aL.sd[AX], sR = aR.sd[AX];
+    const R rL = aL.rho, rR = aR.rho;
+    const R Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+                 (rL * (SL - uL) - rR * (SR - uR));
+    if (SL >= R(0) || SR <= R(0)) {
+      const bool lft = SL >= R(0);
+      const Aux<R>& aK = lft ? aL : aR;
+      flux<AX>(lft ? cL_ : cR_, lft ? eL : eR, aK, fo, feo);
+      uface = aK.u[AX];
+      frow<AX>(lft ? cL_ : cR_, frowo);
+      return;
+    }
+    const bool lft = Ss >= R(0);
+    const R* cK = lft ? cL_ : cR_;
+    const E eK = lft ? eL : eR;
+    const Aux<R>& aK = lft ? aL : aR;
+    const R SK = lft ? SL : SR;
+    flux<AX>(cK, eK, aK, fo, feo);
+    frow<AX>(cK, frowo);
+    const R uK = aK.u[AX];
+    const R chi = (SK - uK) / (SK - Ss);
+    const R rK = aK.rho;
+    // star state U*_K; the flux is F_K + S_K (U*_K - U_K)
+    R us[NF];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) us[L::oPHI + l] = cK[L::oPHI + l] * chi;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) us[L::oARHO + l] = cK[L::oARHO + l] * chi;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) us[L::oMOM + k] = (k == AX) ? rK * chi * Ss : cK[L::oMOM + k] * chi;
+    us[L::oE] = R(0);
+    const E Es = E(chi) * (eK + E(rK) * E(Ss) * (E(Ss) - E(uK)) -
+                           E(aK.sd[AX]) * (E(Ss) - E(uK)) / (E(SK) - E(uK)));
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) {
+      const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+      // Fbar* = Fbar chi off row d; in A form A* = (delta_ij + A_ij) chi - delta_ij
+      if (i == AX)
+        us[L::oF + k] = cK[L::oF + k];
+      else
+        us[L::oF + k] = AF ? Fv(i, j, cK[L::oF + k]) * chi - (i == j ? R(1) : R(0))
+                           : cK[L::oF + k] * chi;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NH; ++k) us[L::oH + k] = cK[L::oH + k] * chi;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) us[L::oX + k] = cK[L::oX + k] * chi;
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+      if (k != L::oE) fo[k] = fo[k] + SK * (us[k] - cK[k]);
+    feo = feo + E(SK) * (Es - eK);
+    uface = uK + SK * (chi - R(1));
+    if (DIM == 1) return;
+    // shear waves in the star regions
+    const R rsL = rL * ((SL - uL) / (SL - Ss));
+    const R rsR = rR * ((SR - uR) / (SR - Ss));
+    R csL = msqrt(aL.G / rsL), csR = msqrt(aR.G / rsR);
+    if (csL > Ss - SL) csL = Ss - SL;
+    if (csR > SR - Ss) csR = SR - Ss;
+    const R ZL = rsL * csL, ZR = rsR * csR;
+    if (!(ZL + ZR > R(0))) return;
+    if (lft ? !(Ss - csL < R(0)) : !(Ss + csR > R(0))) return;
+    const R csK = lft ? csL : csR;
+    const R rsK = lft ? rsL : rsR;
+    const R sgn = lft ? R(1) : R(-1);
+    const R SSK = lft ? Ss - csL : Ss + csR;
+    E ess = Es;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == AX) continue;
+      const R uLt = aL.u[t], uRt = aR.u[t];
+      const R tauL = aL.sd[t], tauR = aR.sd[t];
+      const R uss = (tauR - tauL + ZL * uLt + ZR * uRt) / (ZL + ZR);
+      const R tss = tauL + ZL * (uss - uLt);
+      const R uKt = lft ? uLt : uRt, tauK = lft ? tauL : tauR;
+      const R du = uss - uKt;
+      fo[L::oMOM + t] = fo[L::oMOM + t] + SSK * (rsK * uss - us[L::oMOM + t]);
+#pragma unroll
+      for (int k = 0; k < L::NFC; ++k) {
+        const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+        if (i == t) {
+          const R uss_f = us[L::oF + k] + sgn * frowo[j] * du / csK;
+          fo[L::oF + k] = fo[L::oF + k] + SSK * (uss_f - us[L::oF + k]);
+        }
+      }
+      ess += E(sgn) * (E(tss) * E(uss) - E(tauK) * E(uKt)) / E(csK);
+    }
+    feo = feo + E(SSK) * (ess - Es);
+  }
+};
+
+}  // namespace mm

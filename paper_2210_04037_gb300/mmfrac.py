@@ -1,0 +1,245 @@
+"""Python binding of the mmfrac C ABI (include/mmfrac.h): argument
+marshalling only.  Every step of the method runs in the CUDA library; if the
+library cannot be loaded or no GPU is present, calls raise ``MMError``.
+
+The functions carry the C names without the ``mm_`` prefix
+(``create_grid``, ``set_materials``, ``step``, ``read_fields``,
+``conserved_totals``, ``destroy``, ``last_error``); ``Grid`` bundles them
+for a ``workloads.Case``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmmfrac.so")
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
+MM_ENONFINITE, MM_ENOCONV, MM_EDT, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7, -8
+STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA",
+                -4: "MM_ENONFINITE", -5: "MM_ENOCONV", -6: "MM_EDT", -7: "MM_ETIMEOUT",
+                -8: "MM_ESTATE"}
+FP64, FP32_SPLIT = W.FP64, W.FP32_SPLIT
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("bc", (ctypes.c_int * 2) * 3),
+                ("precision", ctypes.c_int), ("n_materials", ctypes.c_int)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("eos", ctypes.c_int), ("rho0", ctypes.c_double), ("K0", ctypes.c_double),
+                ("G0", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("Gamma0", ctypes.c_double), ("gamma_gas", ctypes.c_double),
+                ("plasticity", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("c3", ctypes.c_double), ("n_hard", ctypes.c_double), ("edot0", ctypes.c_double),
+                ("damage", ctypes.c_int), ("D_crit", ctypes.c_double), ("eps_t", ctypes.c_double),
+                ("eps_c", ctypes.c_double), ("alpha_D", ctypes.c_double),
+                ("poisson", ctypes.c_double), ("Ddot0", ctypes.c_double)]
+
+
+class Init(ctypes.Structure):
+    _fields_ = [("prim", ctypes.POINTER(ctypes.c_double)), ("phi0", ctypes.POINTER(ctypes.c_float)),
+                ("phi0_n", ctypes.c_int64 * 3), ("phi0_lo", ctypes.c_double * 3),
+                ("phi0_h", ctypes.c_double * 3)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("smax", ctypes.c_double),
+                ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
+
+
+EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
+           "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
+           "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read")
+KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmmfrac.so (built by ``paper_2210_04037_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise MMError(MM_ECUDA, f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        lib.mm_create_grid.argtypes = [P(GridDesc), vp, P(vp)]
+        lib.mm_set_materials.argtypes = [vp, P(Material), ctypes.c_int, P(Init)]
+        lib.mm_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(StepInfo)]
+        lib.mm_read_fields.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double),
+                                       ctypes.c_size_t]
+        lib.mm_conserved_totals.argtypes = [vp, P(ctypes.c_double), ctypes.c_size_t]
+        lib.mm_num_fields.argtypes = [vp]
+        lib.mm_num_cells.argtypes = [vp]
+        lib.mm_num_cells.restype = ctypes.c_int64
+        lib.mm_destroy.argtypes = [vp]
+        lib.mm_last_error.restype = ctypes.c_char_p
+        lib.mm_kernel_launches.argtypes = [vp]
+        lib.mm_kernel_launches.restype = ctypes.c_int64
+        lib.mm_profile_enable.argtypes = [vp, ctypes.c_int]
+        lib.mm_profile_enable.restype = ctypes.c_int
+        lib.mm_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), ctypes.c_int,
+                                        ctypes.c_int]
+        lib.mm_profile_read.restype = ctypes.c_int
+        for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
+                   "mm_conserved_totals", "mm_destroy"):
+            getattr(lib, fn).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().mm_last_error().decode()
+
+
+def _check(status: int) -> None:
+    if status != MM_OK:
+        raise MMError(status, last_error())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def material_struct(m) -> Material:
+    s = Material()
+    for name, typ in Material._fields_:
+        setattr(s, name, int(m[name]) if typ is ctypes.c_int else float(m[name]))
+    return s
+
+
+def create_grid(case, precision: int = FP64, stream=None) -> ctypes.c_void_p:
+    d = GridDesc()
+    d.dim = case.dim
+    for k in range(3):
+        d.n[k] = int(case.n[k]) if k < case.dim else 1
+        d.lo[k] = float(case.lo[k]) if k < case.dim else 0.0
+        d.hi[k] = float(case.hi[k]) if k < case.dim else 1.0
+        d.bc[k][0] = int(case.bc[2 * k]) if k < case.dim else 0
+        d.bc[k][1] = int(case.bc[2 * k + 1]) if k < case.dim else 0
+    d.precision = int(precision)
+    d.n_materials = len(case.materials)
+    h = ctypes.c_void_p()
+    _check(load().mm_create_grid(ctypes.byref(d), stream, ctypes.byref(h)))
+    return h
+
+
+def set_materials(grid, case, prim: np.ndarray | None = None) -> None:
+    mats = (Material * len(case.materials))(*[material_struct(m) for m in case.materials])
+    prim = np.ascontiguousarray(case.prim if prim is None else prim, dtype=np.float64)
+    init = Init()
+    init.prim = _dptr(prim)
+    keep = [prim]
+    if case.phi0 is not None:
+        phi0 = np.ascontiguousarray(case.phi0, dtype=np.float32)
+        keep.append(phi0)
+        init.phi0 = phi0.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        for k in range(3):
+            init.phi0_n[k] = int(case.pn[k])
+            init.phi0_lo[k] = float(case.plo[k])
+            init.phi0_h[k] = float(case.ph[k])
+    _check(load().mm_set_materials(grid, mats, len(case.materials), ctypes.byref(init)))
+
+
+def step(grid, n_steps: int, cfl: float) -> dict:
+    info = StepInfo()
+    _check(load().mm_step(grid, int(n_steps), float(cfl), ctypes.byref(info)))
+    return dict(t=info.t, dt_last=info.dt_last, smax=info.smax, steps=info.steps_done,
+                bad_cell=info.bad_cell)
+
+
+def read_fields(grid, primitive: bool = True, field_mask: int = (1 << 64) - 1,
+                out: np.ndarray | None = None) -> np.ndarray:
+    lib = load()
+    nf, nc = lib.mm_num_fields(grid), lib.mm_num_cells(grid)
+    nsel = sum(1 for f in range(nf) if field_mask >> f & 1)
+    if out is None:
+        out = np.empty((nsel, nc))
+    _check(lib.mm_read_fields(grid, ctypes.c_uint64(field_mask), 1 if primitive else 0, _dptr(out),
+                              out.size))
+    return out
+
+
+def conserved_totals(grid, nmat: int) -> np.ndarray:
+    out = np.zeros(nmat + 4)
+    _check(load().mm_conserved_totals(grid, _dptr(out), out.size))
+    return out
+
+
+def destroy(grid) -> None:
+    if grid:
+        _check(load().mm_destroy(grid))
+
+
+def kernel_launches(grid) -> int:
+    return int(load().mm_kernel_launches(grid))
+
+
+def profile_enable(grid, enable: bool = True) -> None:
+    _check(load().mm_profile_enable(grid, 1 if enable else 0))
+
+
+def profile_read(grid, reset: bool = True) -> dict:
+    n = len(KERNEL_KINDS)
+    ms = np.zeros(n)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(load().mm_profile_read(grid, _dptr(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  n, 1 if reset else 0))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+class Grid:
+    """A grid built from a ``workloads.Case`` on the current CUDA device."""
+
+    def __init__(self, case, precision: int = FP64, stream=None):
+        self.case = case
+        self.nmat = len(case.materials)
+        self.h = create_grid(case, precision, stream)
+        try:
+            set_materials(self.h, case)
+        except Exception:
+            destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, n_steps: int, cfl: float | None = None) -> dict:
+        return step(self.h, n_steps, self.case.cfl if cfl is None else cfl)
+
+    def read(self, primitive: bool = True, field_mask: int = (1 << 64) - 1, out=None) -> np.ndarray:
+        return read_fields(self.h, primitive, field_mask, out)
+
+    def totals(self) -> np.ndarray:
+        return conserved_totals(self.h, self.nmat)
+
+    def launches(self) -> int:
+        return kernel_launches(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

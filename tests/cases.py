@@ -101,3 +101,28 @@ def mirrored_x(case):
 
 def mirror_back_x(case, U):
     return _mirror_fields(case, U)
+
+
+def periodic_mix_3d(n, seed=6, shear=0.03, p0=5e8, dp=5e7, rho_gas=700.0, vel=5.0, bc=1,
+                    nz=None):
+    """3D version of the compressed periodic copper/air mixture: every
+    transport term, both tangential directions of the Riemann solver and
+    the plastic return are active; no dilute tensile phase."""
+    rng = np.random.default_rng(seed)
+    nz = n if nz is None else nz
+    mats = [W.cube("bonora"), W.air()]
+    L = 1e-3
+    c = W.Case("mix3d", 3, [n, n + 2, nz], [0, 0, 0], [L, L * (n + 2) / n, L * nz / n], [bc] * 6,
+               mats, None, cfl=0.5)
+    lay = c.layout
+    c.prim = W.blank_prim(lay, c.ncell)
+    x, y, z = c.centres()
+    k = 2 * np.pi / L
+    a = rng.uniform(0.5, 1.5, 6)
+    frac = 0.5 + 0.45 * np.sin(k * x + a[0]) * np.cos(k * y + a[1]) * np.cos(k * z * n / nz + a[4])
+    W.fill_two_phase(c, frac, 8370.0 * (1 + 0.002 * np.cos(k * y)), rho_gas,
+                     p0 + dp * np.sin(k * x + a[2]),
+                     [vel * np.sin(k * y + a[3]), vel * np.cos(k * x), vel * np.sin(k * x + a[5])])
+    c.prim[lay.F_index(0, 1)] = shear * np.sin(k * x)
+    c.prim[lay.F_index(2, 0)] = 0.5 * shear * np.cos(k * y)
+    return c
