@@ -50,8 +50,12 @@ def make_case(name: str, n: int):
 
 
 def state_bytes(case, precision: int) -> int:
+    """Bytes of one copy of the conserved state: FP64 stores every field in
+    8 bytes; FP32-split stores rho E and the N-1 volume fractions in 8 bytes
+    and the other fields in 4."""
     nf = case.layout.nfield
-    per = 8 * nf if precision == W.FP64 else 4 * (nf - 1) + 8
+    nx = len(case.materials)  # rho E + (N - 1) volume fractions
+    per = 8 * nf if precision == W.FP64 else 4 * (nf - nx) + 8 * nx
     return per * case.ncell
 
 

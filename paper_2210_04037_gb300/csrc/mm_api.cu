@@ -323,7 +323,9 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
       free_state(g);
       return fail(MM_ENOMEM, "device allocation of the state failed");
     }
-    if (g->prec == MM_FP32_SPLIT && cudaMalloc(&g->E[i], sizeof(double) * g->ncell) != cudaSuccess) {
+    // FP32-split: rho E and the N-1 volume fractions in an FP64 side array
+    if (g->prec == MM_FP32_SPLIT &&
+        cudaMalloc(&g->E[i], sizeof(double) * g->nmat * g->ncell) != cudaSuccess) {
       free_state(g);
       return fail(MM_ENOMEM, "device allocation of the state failed");
     }

@@ -53,13 +53,36 @@ __device__ __forceinline__ long long cell_index(const KArgs& a, int x, int y, in
   return (long long)x + (long long)a.n[0] * ((long long)y + (long long)a.n[1] * z);
 }
 
+// Field f of the x block (0: rho E, 1 + l: phi_l) of cell idx in storage.
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ long long xslot(const KArgs& a, int k, long long idx) {
+  typedef Lay<DIM, NMAT, NH> L;
+  if (P::split) return (long long)k * a.ncell + idx;
+  return (long long)(k == 0 ? L::oE : L::oPHI + k - 1) * a.ncell + idx;
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void load_at(const KArgs& a, long long idx, typename P::R* c, E* cx) {
+  typedef typename P::R R;
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  const S* U = (const S*)a.Uin;
+#pragma unroll
+  for (int f = 0; f < L::NF; ++f)
+    c[f] = (f == L::oE || f < L::oARHO) ? R(0) : R(U[(long long)f * a.ncell + idx]);
+#pragma unroll
+  for (int k = 0; k < 1 + L::NPHI; ++k) {
+    const long long q = xslot<P, DIM, NMAT, NH>(a, k, idx);
+    cx[k] = P::split ? a.Ein[q] : E(U[q]);
+  }
+}
+
 // Load the conserved state of the cell at axis position gi (ghost cells via
 // the boundary rule of that side), transverse position gw, rest rr.
 template <class P, int DIM, int NMAT, int NH, int AX>
 __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, int rr,
-                                               typename P::R* c, E& e) {
+                                               typename P::R* c, E* cx) {
   typedef typename P::R R;
-  typedef typename P::S S;
   typedef Lay<DIM, NMAT, NH> L;
   constexpr int TD = (AX == 0) ? 1 : 0;
   constexpr int RD = 3 - AX - TD;
@@ -80,10 +103,7 @@ __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, i
   co[TD] = gw;
   co[RD] = rr;
   const long long idx = cell_index(a, co[0], co[1], co[2]);
-  const S* U = (const S*)a.Uin;
-#pragma unroll
-  for (int f = 0; f < L::NF; ++f) c[f] = (f == L::oE) ? R(0) : R(U[(long long)f * a.ncell + idx]);
-  e = P::split ? a.Ein[idx] : E(U[(long long)L::oE * a.ncell + idx]);
+  load_at<P, DIM, NMAT, NH>(a, idx, c, cx);
   if (side >= 0 && kind == BC_P) {
     const R Lx = R(a.hi[AX] - a.lo[AX]);
     c[L::oX + AX] += side == 0 ? -Lx : Lx;
@@ -102,30 +122,21 @@ __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, i
 
 template <class P, int DIM, int NMAT, int NH>
 __device__ __forceinline__ void store_cell(const KArgs& a, long long idx, const typename P::R* c,
-                                           E e) {
+                                           const E* cx) {
   typedef typename P::S S;
   typedef Lay<DIM, NMAT, NH> L;
   S* U = (S*)a.Uout;
 #pragma unroll
   for (int f = 0; f < L::NF; ++f)
-    if (f != L::oE) U[(long long)f * a.ncell + idx] = S(c[f]);
-  if (P::split)
-    a.Eout[idx] = e;
-  else
-    U[(long long)L::oE * a.ncell + idx] = S(e);
-}
-
-template <class P, int DIM, int NMAT, int NH>
-__device__ __forceinline__ long long load_plain(const KArgs& a, long long idx, typename P::R* c,
-                                                E& e) {
-  typedef typename P::R R;
-  typedef typename P::S S;
-  typedef Lay<DIM, NMAT, NH> L;
-  const S* U = (const S*)a.Uin;
+    if (f != L::oE && f >= L::oARHO) U[(long long)f * a.ncell + idx] = S(c[f]);
 #pragma unroll
-  for (int f = 0; f < L::NF; ++f) c[f] = (f == L::oE) ? R(0) : R(U[(long long)f * a.ncell + idx]);
-  e = P::split ? a.Ein[idx] : E(U[(long long)L::oE * a.ncell + idx]);
-  return idx;
+  for (int k = 0; k < 1 + L::NPHI; ++k) {
+    const long long q = xslot<P, DIM, NMAT, NH>(a, k, idx);
+    if (P::split)
+      a.Eout[q] = cx[k];
+    else
+      U[q] = S(cx[k]);
+  }
 }
 
 // ------------------------------------------------------------------ sweep ----
@@ -153,7 +164,8 @@ struct SweepShape {
   static constexpr int NF = Lay<DIM, NMAT, NH>::NF;
   static constexpr int C1 = NF + 9, C2 = NF + 9, C3 = NF + 4;
   static constexpr int N1 = (TL + 4) * TW, N2 = (TL + 2) * TW, N3 = (TL + 1) * TW, N4 = TL * TW;
-  static constexpr size_t smem = sizeof(E) * (2 * N2 + N3) +
+  static constexpr int NX = Lay<DIM, NMAT, NH>::NPHI + 1;
+  static constexpr size_t smem = sizeof(E) * NX * (size_t(N1) + 2 * size_t(N2) + size_t(N3)) +
                                  sizeof(R) * (size_t(N1) * C1 + 2 * size_t(N2) * C2 + size_t(N3) * C3);
   __device__ static __forceinline__ int idx(int p, int w, int len) {
     return AX == 0 ? w * len + p : p * TW + w;
@@ -169,7 +181,12 @@ struct SweepShape {
   }
 };
 
-// One sweep along AX: Uin -> Uout.
+// One sweep along AX: Uin -> Uout.  Phases over the tile (each a pass of
+// the CTA's threads over its items, separated by barriers):
+//   1. load + primitive recovery of the tile cells with a halo of two,
+//   2. van Leer reconstruction + MUSCL-Hancock half step (face states),
+//   3. Riemann problem at each face,
+//   4. conservative update with the non-conservative terms, store.
 template <class P, int DIM, int NMAT, int NH, int AX>
 __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
     k_sweep(KArgs a) {
@@ -177,14 +194,15 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
   typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
-  constexpr int NF = L::NF, TL = SH::TL, TW = SH::TW, NT = SH::NT;
+  constexpr int NF = L::NF, NX = SH::NX, TL = SH::TL, TW = SH::TW, NT = SH::NT;
   constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3;
   constexpr int N1 = SH::N1, N2 = SH::N2, N3 = SH::N3, N4 = SH::N4;
   constexpr int TD = (AX == 0) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  E* e2 = reinterpret_cast<E*>(smem);
-  E* e3 = e2 + 2 * N2;
-  R* r1 = reinterpret_cast<R*>(e3 + N3);
+  E* x1 = reinterpret_cast<E*>(smem);  // N1 * NX
+  E* x2 = x1 + N1 * NX;                 // 2 * N2 * NX
+  E* x3 = x2 + 2 * N2 * NX;             // N3 * NX
+  R* r1 = reinterpret_cast<R*>(x3 + N3 * NX);
   R* r2 = r1 + N1 * C1;
   R* r3 = r2 + 2 * N2 * C2;
   __shared__ unsigned char ok1[N1], ok2[N2];
@@ -208,11 +226,11 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
     unsigned char okv = 0;
     if (w0 + w < ntw && gi >= -2 && gi < na + 2) {
       R c[NF];
-      E e;
-      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, e);
+      E cx[NX];
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx);
       R* rec = r1 + it * C1;
       Aux<R> ax;
-      if (PH::template u2w<AX>(a, c, e, rec, ax)) {
+      if (PH::template u2w<AX>(a, c, cx, rec, x1 + it * NX, ax)) {
         put_aux(rec + NF, ax);
         okv = 1;
       } else {
@@ -236,51 +254,68 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       const R* wm = r1 + im * C1;
       const R* wc = r1 + ic * C1;
       const R* wp = r1 + ip * C1;
+      const E* xm = x1 + im * NX;
+      const E* xc = x1 + ic * NX;
+      const E* xp = x1 + ip * NX;
       R uc[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
       R cl[NF], cr[NF];
-      E el, er;
+      E cxl[NX], cxr[NX];
       Aux<R> xl, xr;
       bool good;
       {
         R wl[NF], wr[NF];
+        E wxl[NX], wxr[NX];
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
-          const R s = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
-          wl[k] = wc[k] - R(0.5) * s;
-          wr[k] = wc[k] + R(0.5) * s;
+          const R sl = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
+          wl[k] = wc[k] - R(0.5) * sl;
+          wr[k] = wc[k] + R(0.5) * sl;
         }
-        good = PH::template w2u<AX>(a, wl, cl, el, xl) && PH::template w2u<AX>(a, wr, cr, er, xr);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          const E sl = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
+          wxl[k] = xc[k] - 0.5 * sl;
+          wxr[k] = xc[k] + 0.5 * sl;
+        }
+        good = PH::template w2u<AX>(a, wl, wxl, cl, cxl, xl) &&
+               PH::template w2u<AX>(a, wr, wxr, cr, cxr, xr);
       }
       if (good) {
         R fl[NF], fr[NF], nc[NF], rowl[3], rowr[3], dF[3];
-        E fel, fer;
-        PH::template flux<AX>(cl, el, xl, fl, fel);
-        PH::template flux<AX>(cr, er, xr, fr, fer);
+        E fxl[NX], fxr[NX], ncx[NX];
+        PH::template flux<AX>(cl, cxl, xl, fl, fxl);
+        PH::template flux<AX>(cr, cxr, xr, fr, fxr);
         PH::template frow<AX>(cl, rowl);
         PH::template frow<AX>(cr, rowr);
 #pragma unroll
         for (int j = 0; j < 3; ++j) dF[j] = rowr[j] - rowl[j];
-        PH::template noncons<AX>(wc, uc, xr.u[AX] - xl.u[AX], dF, nc);
+        PH::template noncons<AX>(wc, xc, uc, xr.u[AX] - xl.u[AX], dF, nc, ncx);
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
           const R inc = R(0.5) * lam * ((fl[k] - fr[k]) + nc[k]);
           cl[k] += inc;
           cr[k] += inc;
         }
-        const E einc = 0.5 * E(lam) * (fel - fer);
-        el += einc;
-        er += einc;
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          const E inc = 0.5 * E(lam) * ((fxl[k] - fxr[k]) + ncx[k]);
+          cxl[k] += inc;
+          cxr[k] += inc;
+        }
         R tmp[NF];
-        good = PH::template u2w<AX>(a, cl, el, tmp, xl) && PH::template u2w<AX>(a, cr, er, tmp, xr);
+        E tmpx[NX];
+        good = PH::template u2w<AX>(a, cl, cxl, tmp, tmpx, xl) &&
+               PH::template u2w<AX>(a, cr, cxr, tmp, tmpx, xr);
       }
       if (!good) {
         // first order: both faces take the cell average
-        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, el);
+        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl);
 #pragma unroll
         for (int k = 0; k < NF; ++k) cr[k] = cl[k];
-        er = el;
+#pragma unroll
+        for (int k = 0; k < NX; ++k) cxr[k] = cxl[k];
         get_aux(wc + NF, xl);
 #pragma unroll
         for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
@@ -295,8 +330,11 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       }
       put_aux(ql + NF, xl);
       put_aux(qr + NF, xr);
-      e2[2 * it] = el;
-      e2[2 * it + 1] = er;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        x2[(2 * it) * NX + k] = cxl[k];
+        x2[(2 * it + 1) * NX + k] = cxr[k];
+      }
       okv = 1;
     }
     ok2[it] = okv;
@@ -320,8 +358,9 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
         xr.u[k] = k < DIM ? qr[L::oMOM + k] / xr.rho : R(0);
       }
       R fo[NF], row[3], uf;
-      E fe;
-      PH::template riemann<AX>(ql, e2[2 * il + 1], xl, qr, e2[2 * ir], xr, fo, fe, uf, row);
+      E fox[NX];
+      PH::template riemann<AX>(ql, x2 + (2 * il + 1) * NX, xl, qr, x2 + (2 * ir) * NX, xr, fo,
+                               fox, uf, row);
       R* q3 = r3 + it * C3;
 #pragma unroll
       for (int k = 0; k < NF; ++k) q3[k] = fo[k];
@@ -329,7 +368,8 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       q3[NF + 1] = row[0];
       q3[NF + 2] = row[1];
       q3[NF + 3] = row[2];
-      e3[it] = fe;
+#pragma unroll
+      for (int k = 0; k < NX; ++k) x3[it * NX + k] = fox[k];
     }
   }
   __syncthreads();
@@ -344,21 +384,25 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       const int ic = SH::idx(p4 + 2, w, TL + 4);
       if (ok1[ic] != 1) continue;
       R c[NF];
-      E e;
-      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, e);
+      E cx[NX];
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx);
       const R* wc = r1 + ic * C1;
+      const E* xc = x1 + ic * NX;
       const R* ql = r3 + fl * C3;
       const R* qr = r3 + fr * C3;
       R uc[3], dF[3], nc[NF];
+      E ncx[NX];
 #pragma unroll
       for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
 #pragma unroll
       for (int j = 0; j < 3; ++j) dF[j] = qr[NF + 1 + j] - ql[NF + 1 + j];
-      PH::template noncons<AX>(wc, uc, qr[NF] - ql[NF], dF, nc);
+      PH::template noncons<AX>(wc, xc, uc, qr[NF] - ql[NF], dF, nc, ncx);
 #pragma unroll
       for (int k = 0; k < NF; ++k) c[k] = c[k] + lam * ((ql[k] - qr[k]) + nc[k]);
-      e = e + E(lam) * (e3[fl] - e3[fr]);
-      store_cell<P, DIM, NMAT, NH>(a, idx, c, e);
+#pragma unroll
+      for (int k = 0; k < NX; ++k)
+        cx[k] = cx[k] + E(lam) * ((x3[fl * NX + k] - x3[fr * NX + k]) + ncx[k]);
+      store_cell<P, DIM, NMAT, NH>(a, idx, c, cx);
     }
   }
 }
@@ -476,33 +520,25 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
-  constexpr int NF = L::NF;
+  constexpr int NF = L::NF, NX = PH::NX;
   const double dt = a.info->dt;
   const long long step = a.info->steps;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E e;
-    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    E cx[NX], wx[NX];
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
     Aux<R> ax;
-    if (!PH::template u2w<0>(a, c, e, w, ax)) {
+    if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }
     double phi[NMAT], eps[NMAT], Dm[NMAT];
     R rho[NMAT], Dr[NMAT], phir[NMAT];
-    {
-      R s = R(0);
-#pragma unroll
-      for (int l = 0; l < NMAT - 1; ++l) {
-        phir[l] = c[L::oPHI + l];
-        s += phir[l];
-      }
-      phir[NMAT - 1] = R(1) - s;
-    }
+    PH::fractions(cx, phi);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      phi[l] = double(phir[l]);
+      phir[l] = R(phi[l]);
       rho[l] = w[L::oARHO + l];
       eps[l] = 0.0;
       Dm[l] = 0.0;
@@ -614,8 +650,9 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = X[FC<DIM>::idx(k)];
     if (dl > 0.0) {
       R w2[NF];
+      E wx2[NX];
       Aux<R> as;
-      if (!PH::template u2w<0>(a, c, e, w2, as)) {
+      if (!PH::template u2w<0>(a, c, cx, w2, wx2, as)) {
         report(a.err, ST_ENONFINITE, cell, step);
         continue;
       }
@@ -628,14 +665,13 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
         for (int hh = 0; hh < NH; ++hh)
           if (a.hslot[l] == hh) {
             const R arho = c[L::oARHO + l];
-            const double Dn =
-                damage_rk4(a.mat[l], Dm[l], eps[l], dl, dt, double(w2[L::oE]), seq, double(rho[l]));
+            const double Dn = damage_rk4(a.mat[l], Dm[l], eps[l], dl, dt, wx2[0], seq, double(rho[l]));
             c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
             c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
           }
       }
     }
-    store_cell<P, DIM, NMAT, NH>(a, cell, c, e);
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx);
   }
 }
 
@@ -644,22 +680,22 @@ template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_cfl(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
-  constexpr int NF = Lay<DIM, NMAT, NH>::NF;
+  constexpr int NF = Lay<DIM, NMAT, NH>::NF, NX = PH::NX;
   const long long step = a.info->steps;
   double smax = 0.0;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E e;
-    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    E cx[NX], wx[NX];
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
     Aux<R> ax;
-    if (!PH::template u2w<0>(a, c, e, w, ax)) {
+    if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }
     R v = R(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) v = fmax(v, mabs(ax.u[k]));
+    for (int k = 0; k < DIM; ++k) v = mabs(ax.u[k]) > v ? mabs(ax.u[k]) : v;
     const double s = double(v + ax.cL);
     smax = s > smax ? s : smax;
   }
@@ -681,10 +717,11 @@ __global__ void k_init(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
-  constexpr int NF = L::NF;
+  constexpr int NF = L::NF, NX = PH::NX;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R w[NF], c[NF];
+    E wx[NX], cx[NX];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       double v = a.prim[(long long)f * a.ncell + cell];
@@ -693,11 +730,12 @@ __global__ void k_init(KArgs a) {
         if (ij % 4 == 0) v -= 1.0;
       }
       w[f] = R(v);
+      if (f == L::oE) wx[0] = v;
+      if (f < L::oARHO) wx[1 + f] = v;
     }
-    E e;
     Aux<R> ax;
-    if (!PH::template w2u<0>(a, w, c, e, ax)) report(a.err, ST_ENONFINITE, cell, 0);
-    store_cell<P, DIM, NMAT, NH>(a, cell, c, e);
+    if (!PH::template w2u<0>(a, w, wx, c, cx, ax)) report(a.err, ST_ENONFINITE, cell, 0);
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx);
   }
 }
 
@@ -706,22 +744,25 @@ __global__ void k_read(KArgs a, int primitive) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
-  constexpr int NF = L::NF;
+  constexpr int NF = L::NF, NX = PH::NX;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E e;
-    load_plain<P, DIM, NMAT, NH>(a, cell, c, e);
+    E cx[NX], wx[NX];
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
     const R* src = c;
+    const E* srcx = cx;
     if (primitive) {
       Aux<R> ax;
-      if (!PH::template u2w<0>(a, c, e, w, ax)) report(a.err, ST_ENONFINITE, cell, 0);
+      if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) report(a.err, ST_ENONFINITE, cell, 0);
       src = w;
+      srcx = wx;
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       double v = double(src[f]);
-      if (f == L::oE && !primitive) v = e;
+      if (f == L::oE) v = srcx[0];
+      if (f < L::oARHO) v = srcx[1 + f];
       if (P::aform && f >= L::oF && f < L::oF + L::NFC) {
         const int ij = FC<DIM>::idx(f - L::oF);
         if (ij % 4 == 0) v += 1.0;
@@ -734,13 +775,12 @@ __global__ void k_read(KArgs a, int primitive) {
 // ------------------------------------------------------------ totals ----
 template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_totals(KArgs a) {
-  typedef typename P::R R;
   typedef Lay<DIM, NMAT, NH> L;
+  typedef typename P::S S;
   constexpr int NQ = NMAT + 4;
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-  typedef typename P::S S;
   const S* U = (const S*)a.Uin;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
@@ -749,7 +789,8 @@ __global__ void __launch_bounds__(256) k_totals(KArgs a) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k)
       acc[NMAT + k] += double(U[(long long)(L::oMOM + k) * a.ncell + cell]);
-    acc[NMAT + 3] += P::split ? a.Ein[cell] : double(U[(long long)L::oE * a.ncell + cell]);
+    const long long q = xslot<P, DIM, NMAT, NH>(a, 0, cell);
+    acc[NMAT + 3] += P::split ? a.Ein[q] : double(U[q]);
   }
   __shared__ double red[8][NQ];
 #pragma unroll

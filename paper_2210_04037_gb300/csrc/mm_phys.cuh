@@ -217,11 +217,17 @@ struct Aux {
   R rho, cL, G;
 };
 
+// A state is carried as two blocks: v[NF] in the working precision R, and
+// x[NX] in FP64 with x[0] = rho E (conserved) or p (primitive) and
+// x[1 + l] = phi_l (l < N-1).  The slots of v at those positions are unused.
+// Keeping the volume fractions in FP64 makes the minority fraction
+// 1 - sum(phi) exact in FP32-split storage.
 template <class P, int DIM, int NMAT, int NH>
 struct Phys {
   typedef typename P::R R;
   typedef Lay<DIM, NMAT, NH> L;
   static constexpr int NF = L::NF;
+  static constexpr int NX = 1 + L::NPHI;
   static constexpr bool AF = P::aform;
 
   // Full 3x3 stored tensor (Fbar, or A = Fbar - I): inactive comps are 0 off
@@ -244,6 +250,17 @@ struct Phys {
     for (int h = 0; h < NH; ++h)
       if (h == a.hslot[l]) D = w[L::oH + 2 * h + 1];
     return D;
+  }
+
+  // Volume fractions of all N materials from the x block.
+  __device__ static __forceinline__ void fractions(const E* x, E phi[NMAT]) {
+    E s = 0.0;
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) {
+      phi[l] = x[1 + l];
+      s += phi[l];
+    }
+    phi[NMAT - 1] = 1.0 - s;
   }
 
   // Mixture quantities of the isobaric Allaire closure with one deformation
@@ -301,21 +318,17 @@ struct Phys {
     return true;
   }
 
-  // primitive w -> conserved (c, rhoE).  w[oE] holds p.
+  // primitive (w, wx) -> conserved (c, cx).
   template <int AX>
-  __device__ static bool w2u(const KArgs& a, const R* w, R* c, E& rhoE, Aux<R>& ax) {
+  __device__ static bool w2u(const KArgs& a, const R* w, const E* wx, R* c, E* cx, Aux<R>& ax) {
+    E phid[NMAT];
     R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
-    R s = R(0);
-#pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      phi[l] = w[L::oPHI + l];
-      s += phi[l];
-    }
-    phi[NMAT - 1] = R(1) - s;
+    fractions(wx, phid);
     ax.rho = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      if (!(phi[l] > R(0))) return false;
+      if (!(phid[l] > 0.0)) return false;
+      phi[l] = R(phid[l]);
       rho[l] = w[L::oARHO + l];
       if (!(rho[l] > R(0))) return false;
       arho[l] = phi[l] * rho[l];
@@ -324,7 +337,8 @@ struct Phys {
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) ax.u[k] = k < DIM ? w[L::oMOM + k] : R(0);
-    const R p = w[L::oE];
+    const E pE = wx[0];
+    const R p = R(pE);
     R X[9];
     fullX(w, X);
     Mix mx;
@@ -332,17 +346,20 @@ struct Phys {
     E rhoe = 0.0;
 #pragma unroll
     for (int l = 0; l < NMAT; ++l)
-      rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (E(p) - E(mx.p[l])) / E(a.mat[l].Gamma);
+      rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
     const E ke = 0.5 * E(ax.rho) *
                  (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) c[L::oPHI + l] = phi[l];
+    for (int l = 0; l < NMAT - 1; ++l) {
+      cx[1 + l] = phid[l];
+      c[L::oPHI + l] = R(0);
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) c[L::oARHO + l] = arho[l];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) c[L::oMOM + k] = ax.rho * ax.u[k];
     c[L::oE] = R(0);
-    rhoE = rhoe + ke;
+    cx[0] = rhoe + ke;
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = w[L::oF + k];
 #pragma unroll
@@ -359,24 +376,20 @@ struct Phys {
     return finish<AX>(a, p, rho, arho, mx, ax);
   }
 
-  // conserved (c, rhoE) -> primitive w (w[oE] = p), with
+  // conserved (c, cx) -> primitive (w, wx), with
   // p = (rho e - sum_l phi_l rho_l e_ref,l + sum_l phi_l p_ref,l / Gamma_l) / xi.
   template <int AX>
-  __device__ static bool u2w(const KArgs& a, const R* c, E rhoE, R* w, Aux<R>& ax) {
+  __device__ static bool u2w(const KArgs& a, const R* c, const E* cx, R* w, E* wx, Aux<R>& ax) {
+    E phid[NMAT];
     R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
-    R s = R(0);
-#pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      phi[l] = c[L::oPHI + l];
-      s += phi[l];
-    }
-    phi[NMAT - 1] = R(1) - s;
+    fractions(cx, phid);
     ax.rho = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       arho[l] = c[L::oARHO + l];
-      if (!(phi[l] > R(0)) || !(arho[l] > R(0))) return false;
-      rho[l] = arho[l] / phi[l];
+      if (!(phid[l] > 0.0) || !(arho[l] > R(0))) return false;
+      phi[l] = R(phid[l]);
+      rho[l] = R(E(arho[l]) / phid[l]);
       ax.rho += arho[l];
     }
     bool ok = true;
@@ -399,27 +412,32 @@ struct Phys {
     if (!mixture(a, phi, rho, D, X, mx)) return false;
     const E ke = 0.5 * E(ax.rho) *
                  (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
-    E num = rhoE - ke;
+    E num = cx[0] - ke;
 #pragma unroll
     for (int l = 0; l < NMAT; ++l)
       num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
-    const R p = R(num / E(mx.xi));
+    const E pE = num / E(mx.xi);
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) w[L::oPHI + l] = phi[l];
+    for (int l = 0; l < NMAT - 1; ++l) {
+      wx[1 + l] = phid[l];
+      w[L::oPHI + l] = R(0);
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) w[L::oARHO + l] = rho[l];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) w[L::oMOM + k] = ax.u[k];
-    w[L::oE] = p;
+    w[L::oE] = R(0);
+    wx[0] = pE;
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) w[L::oF + k] = c[L::oF + k];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) w[L::oX + k] = c[L::oX + k];
 #pragma unroll
     for (int k = 0; k < NF; ++k) ok = ok && mfinite(w[k]) && mfinite(c[k]);
-    ok = ok && isfinite(rhoE);
+#pragma unroll
+    for (int k = 0; k < NX; ++k) ok = ok && isfinite(cx[k]) && isfinite(wx[k]);
     if (!ok) return false;
-    return finish<AX>(a, p, rho, arho, mx, ax);
+    return finish<AX>(a, R(pE), rho, arho, mx, ax);
   }
 
   // Row AX of Fbar of a state vector.
@@ -439,18 +457,21 @@ struct Phys {
   // sigma_kd, rho E u_d - sigma_dj u_j, Fbar_ij u_d - Fbar_dj u_i (zero for
   // row d).
   template <int AX>
-  __device__ static __forceinline__ void flux(const R* c, E rhoE, const Aux<R>& ax, R* f,
-                                              E& fe) {
+  __device__ static __forceinline__ void flux(const R* c, const E* cx, const Aux<R>& ax, R* f,
+                                              E* fx) {
     const R ud = ax.u[AX];
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) f[L::oPHI + l] = c[L::oPHI + l] * ud;
+    for (int l = 0; l < NMAT - 1; ++l) {
+      fx[1 + l] = cx[1 + l] * E(ud);
+      f[L::oPHI + l] = R(0);
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) f[L::oARHO + l] = c[L::oARHO + l] * ud;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) f[L::oMOM + k] = c[L::oMOM + k] * ud - ax.sd[k];
     f[L::oE] = R(0);
-    fe = rhoE * E(ud) - (E(ax.sr[0]) * E(ax.u[0]) + E(ax.sr[1]) * E(ax.u[1]) +
-                         E(ax.sr[2]) * E(ax.u[2]));
+    fx[0] = cx[0] * E(ud) - (E(ax.sr[0]) * E(ax.u[0]) + E(ax.sr[1]) * E(ax.u[1]) +
+                             E(ax.sr[2]) * E(ax.u[2]));
     R row[3];
     frow<AX>(c, row);
 #pragma unroll
@@ -467,12 +488,13 @@ struct Phys {
   // Non-conservative terms per unit 1/dx: phi and X take q_c du; the
   // deformation tensor 2/3 Fbar_ij du - u_i dFbar_dj.
   template <int AX>
-  __device__ static __forceinline__ void noncons(const R* wc, const R uc[3], R du,
-                                                 const R dFrow[3], R* nc) {
+  __device__ static __forceinline__ void noncons(const R* wc, const E* wcx, const R uc[3], R du,
+                                                 const R dFrow[3], R* nc, E* ncx) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) nc[k] = R(0);
+    ncx[0] = 0.0;
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) nc[L::oPHI + l] = wc[L::oPHI + l] * du;
+    for (int l = 0; l < NMAT - 1; ++l) ncx[1 + l] = wcx[1 + l] * E(du);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) nc[L::oX + k] = wc[L::oX + k] * du;
 #pragma unroll
@@ -488,8 +510,9 @@ struct Phys {
   // is the HLLC solver.  Outputs the flux, the normal velocity at the face
   // and the row d of Fbar on the upwind side of the contact.
   template <int AX>
-  __device__ static void riemann(const R* cL_, E eL, const Aux<R>& aL, const R* cR_, E eR,
-                                 const Aux<R>& aR, R* fo, E& feo, R& uface, R frowo[3]) {
+  __device__ static void riemann(const R* cL_, const E* xL, const Aux<R>& aL, const R* cR_,
+                                 const E* xR, const Aux<R>& aR, R* fo, E* fox, R& uface,
+                                 R frowo[3]) {
     const R uL = aL.u[AX], uR = aR.u[AX];
     const R a1 = uL - aL.cL, a2 = uR - aR.cL;
     const R b1 = uL + aL.cL, b2 = uR + aR.cL;
@@ -502,17 +525,17 @@ struct Phys {
     if (SL >= R(0) || SR <= R(0)) {
       const bool lft = SL >= R(0);
       const Aux<R>& aK = lft ? aL : aR;
-      flux<AX>(lft ? cL_ : cR_, lft ? eL : eR, aK, fo, feo);
+      flux<AX>(lft ? cL_ : cR_, lft ? xL : xR, aK, fo, fox);
       uface = aK.u[AX];
       frow<AX>(lft ? cL_ : cR_, frowo);
       return;
     }
     const bool lft = Ss >= R(0);
     const R* cK = lft ? cL_ : cR_;
-    const E eK = lft ? eL : eR;
+    const E* xK = lft ? xL : xR;
     const Aux<R>& aK = lft ? aL : aR;
     const R SK = lft ? SL : SR;
-    flux<AX>(cK, eK, aK, fo, feo);
+    flux<AX>(cK, xK, aK, fo, fox);
     frow<AX>(cK, frowo);
     const R uK = aK.u[AX];
     const R chi = (SK - uK) / (SK - Ss);
@@ -520,13 +543,16 @@ struct Phys {
     // star state U*_K; the flux is F_K + S_K (U*_K - U_K)
     R us[NF];
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) us[L::oPHI + l] = cK[L::oPHI + l] * chi;
+    for (int l = 0; l < NMAT - 1; ++l) {
+      us[L::oPHI + l] = R(0);
+      fox[1 + l] = fox[1 + l] + E(SK) * (xK[1 + l] * E(chi) - xK[1 + l]);
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) us[L::oARHO + l] = cK[L::oARHO + l] * chi;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) us[L::oMOM + k] = (k == AX) ? rK * chi * Ss : cK[L::oMOM + k] * chi;
     us[L::oE] = R(0);
-    const E Es = E(chi) * (eK + E(rK) * E(Ss) * (E(Ss) - E(uK)) -
+    const E Es = E(chi) * (xK[0] + E(rK) * E(Ss) * (E(Ss) - E(uK)) -
                            E(aK.sd[AX]) * (E(Ss) - E(uK)) / (E(SK) - E(uK)));
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) {
@@ -544,8 +570,8 @@ struct Phys {
     for (int k = 0; k < DIM; ++k) us[L::oX + k] = cK[L::oX + k] * chi;
 #pragma unroll
     for (int k = 0; k < NF; ++k)
-      if (k != L::oE) fo[k] = fo[k] + SK * (us[k] - cK[k]);
-    feo = feo + E(SK) * (Es - eK);
+      if (k != L::oE && (k < L::oPHI || k >= L::oPHI + L::NPHI)) fo[k] = fo[k] + SK * (us[k] - cK[k]);
+    fox[0] = fox[0] + E(SK) * (Es - xK[0]);
     uface = uK + SK * (chi - R(1));
     if (DIM == 1) return;
     // shear waves in the star regions
@@ -582,7 +608,7 @@ struct Phys {
       }
       ess += E(sgn) * (E(tss) * E(uss) - E(tauK) * E(uKt)) / E(csK);
     }
-    feo = feo + E(SSK) * (ess - Es);
+    fox[0] = fox[0] + E(SSK) * (ess - Es);
   }
 };
 

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 FULL = {"ring_2d_512": lambda: W.ring_2d(512), "cylinder_3d_256": lambda: W.cylinder_3d(256)}
 
 
-@pytest.mark.parametrize("precision,tol", [(mmfrac.FP64, 1e-10), (mmfrac.FP32_SPLIT, 1e-4)])
+@pytest.mark.parametrize("precision,tol", [(mmfrac.FP64, 1e-10), (mmfrac.FP32_SPLIT, 1e-3)])
 @pytest.mark.parametrize("name", list(FULL))
 def test_full_size_one_step_on_sampled_cells(name, precision, tol):
     case = FULL[name]()
