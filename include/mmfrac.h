@@ -133,6 +133,34 @@ mm_status mm_read_fields(mm_grid* g, uint64_t field_mask, int primitive,
  * FP64.  out_len >= N + 4.  Errors: MM_EINVAL. */
 mm_status mm_conserved_totals(mm_grid* g, double* out, size_t out_len);
 
+/* Conserved totals of a state the caller holds in device memory, computed
+ * without allocating anything (the paper has no counterpart; this is an
+ * interface for callers that cannot allocate).  Some callers cannot call
+ * cudaMalloc: a serving loop that owns a fixed pool of device memory and
+ * must not let a library allocate (cudaMalloc can synchronise the device and
+ * fragments the pool), or a runtime whose allocator is off limits at the
+ * point of the call.  They pass the state and the output; the block partial
+ * sums go to one file-scope device array of 1024 x (MM_MAXMAT + 4) doubles
+ * (48 KiB) that every GPU which loads the library keeps until the process
+ * exits.
+ *   d_cons   device pointer, FP64 conserved fields [nfield][ncell] in the
+ *            field order above (mm_read_fields(..., primitive = 0) layout);
+ *   dim, ncell, n_materials (1..MM_MAXMAT), n_plastic (materials with a
+ *            plasticity model): the layout of d_cons;
+ *   dx       host array, cell size per axis (dV = product over dim);
+ *   d_out    device pointer to N + 4 doubles (as mm_conserved_totals);
+ *   cuda_stream  stream to order the two kernels on (NULL: default stream).
+ * The call is asynchronous on the stream.  The first call on a device (with
+ * that device current) resolves the scratch array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call on a device shares the one array and overwrites every entry it
+ * reads, so nothing carries over, but calls that overlap on the GPU (other
+ * streams, other threads) race on it: order them.  More materials than the
+ * scratch holds: MM_EINVAL.  Other errors: MM_EINVAL, MM_ECUDA. */
+mm_status mm_conserved_totals_noalloc(const double* d_cons, int dim, int64_t ncell,
+                                      int n_materials, int n_plastic, const double dx[3],
+                                      double* d_out, void* cuda_stream);
+
 /* Number of fields and cells of the grid (for sizing buffers). */
 int mm_num_fields(const mm_grid* g);
 int64_t mm_num_cells(const mm_grid* g);

@@ -19,7 +19,7 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmfrac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"mm_api.cu": []}
+UNITS = {"mm_api.cu": [], "mm_noalloc.cu": []}
 for _d in (1, 2, 3):
     UNITS[f"mm_fp64_d{_d}.cu"] = ["--fmad=false"]
     UNITS[f"mm_fp32_d{_d}.cu"] = []

@@ -51,6 +51,8 @@ __global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin) {
 
 }  // namespace
 
+void mm_internal_set_error(const char* msg) { g_error = msg; }
+
 namespace mm {
 // Sum of the per-block partial totals, one warp per quantity, scaled by dV.
 __global__ void k_totals_final(const double* partial, int nblocks, int nq, double dV,

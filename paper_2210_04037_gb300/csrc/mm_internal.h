@@ -57,6 +57,9 @@ struct KArgs {
   int tiles[3];        // tiles along the sweep axis, the transverse axis, the rest
 };
 
+// Sets the message mm_last_error() returns on the calling thread.
+void mm_internal_set_error(const char* msg);
+
 // Launchers implemented in the precision x dimension translation units
 // (mm_fp64_d{1,2,3}.cu, mm_fp32_d{1,2,3}.cu).  what: 0 init, 1 read
 // (flag = primitive), 2 CFL reduction, 3 sweep along axis, 4 sources,

@@ -64,7 +64,8 @@ class StepInfo(ctypes.Structure):
 
 EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
-           "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read")
+           "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
+           "mm_conserved_totals_noalloc")
 KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources")
 
 _lock = threading.Lock()
@@ -100,6 +101,9 @@ def load(path: str = LIB_PATH):
         lib.mm_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64), ctypes.c_int,
                                         ctypes.c_int]
         lib.mm_profile_read.restype = ctypes.c_int
+        lib.mm_conserved_totals_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                                    ctypes.c_int, P(ctypes.c_double), vp, vp]
+        lib.mm_conserved_totals_noalloc.restype = ctypes.c_int
         for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
                    "mm_conserved_totals", "mm_destroy"):
             getattr(lib, fn).restype = ctypes.c_int
@@ -205,6 +209,20 @@ def profile_read(grid, reset: bool = True) -> dict:
     _check(load().mm_profile_read(grid, _dptr(ms), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   n, 1 if reset else 0))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def conserved_totals_noalloc(d_cons: int, dim: int, ncell: int, n_materials: int,
+                             n_plastic: int, dx, d_out: int, stream=None) -> None:
+    """Totals of a conserved state held in the caller's device memory
+    (``d_cons``: device address of [nfield][ncell] FP64 conserved fields),
+    written to the caller's device buffer ``d_out`` (N + 4 doubles), with no
+    allocation inside the library: for callers that manage all device memory
+    themselves and cannot let a library call cudaMalloc.  Asynchronous on
+    ``stream``."""
+    dxa = (ctypes.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    _check(load().mm_conserved_totals_noalloc(ctypes.c_void_p(d_cons), int(dim), int(ncell),
+                                              int(n_materials), int(n_plastic), dxa,
+                                              ctypes.c_void_p(d_out), stream))
 
 
 class Grid:
