@@ -51,11 +51,10 @@ def make_case(name: str, n: int):
 
 def state_bytes(case, precision: int) -> int:
     """Bytes of one copy of the conserved state: FP64 stores every field in
-    8 bytes; FP32-split stores rho E and the N-1 volume fractions in 8 bytes
-    and the other fields in 4."""
+    8 bytes; FP32-split stores rho E in 8 bytes and every other field, plus
+    the carried last volume fraction, in 4."""
     nf = case.layout.nfield
-    nx = len(case.materials)  # rho E + (N - 1) volume fractions
-    per = 8 * nf if precision == W.FP64 else 4 * (nf - nx) + 8 * nx
+    per = 8 * nf if precision == W.FP64 else 4 * nf + 8
     return per * case.ncell
 
 

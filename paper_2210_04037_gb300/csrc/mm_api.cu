@@ -306,6 +306,11 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     k.Ddot0 = m.Ddot0;
     k.Gamma = m.eos == MM_EOS_IDEAL_GAS ? m.gamma_gas - 1.0 : m.Gamma0;
     k.xi = 1.0 / k.Gamma;
+    if (m.damage == MM_DMG_BONORA) {
+      k.bon_k = m.alpha_D * pow(m.D_crit, 1.0 / m.alpha_D) / log(m.eps_c / m.eps_t);
+      k.bon_ec2n = pow(m.eps_c, 2.0 * m.n_hard);
+      k.bon_et2n = pow(m.eps_t, 2.0 * m.n_hard);
+    }
     if (m.plasticity == MM_PL_JOHNSON_COOK) hslot[l] = nhist++;
   }
   if (nhist > 1) return fail(MM_EINVAL, "at most one plastic material is supported");
@@ -320,14 +325,16 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   g->nhist = nhist;
   g->nfield = nfield;
   const size_t es = elem_size(g);
+  // FP32-split: one more float field (the last volume fraction is carried,
+  // not formed as 1 - sum) and rho E in an FP64 side array
+  const size_t nstore = g->prec == MM_FP32_SPLIT ? nfield + 1 : nfield;
   for (int i = 0; i < 2; ++i) {
-    if (cudaMalloc(&g->U[i], es * nfield * g->ncell) != cudaSuccess) {
+    if (cudaMalloc(&g->U[i], es * nstore * g->ncell) != cudaSuccess) {
       free_state(g);
       return fail(MM_ENOMEM, "device allocation of the state failed");
     }
-    // FP32-split: rho E and the N-1 volume fractions in an FP64 side array
     if (g->prec == MM_FP32_SPLIT &&
-        cudaMalloc(&g->E[i], sizeof(double) * g->nmat * g->ncell) != cudaSuccess) {
+        cudaMalloc(&g->E[i], sizeof(double) * g->ncell) != cudaSuccess) {
       free_state(g);
       return fail(MM_ENOMEM, "device allocation of the state failed");
     }

@@ -16,6 +16,9 @@ struct MatK {
   double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
   double xi;     // 1 / Grueneisen coefficient (ideal gas: 1/(gamma-1))
   double Gamma;  // Grueneisen coefficient (ideal gas: gamma - 1)
+  // Bonora constants: alpha_D D_c^(1/alpha_D) / ln(eps_c/eps_t), and
+  // eps_c^(2n), eps_t^(2n) of the threshold law (n the hardening exponent)
+  double bon_k, bon_ec2n, bon_et2n;
 };
 
 // First failure seen on the device (sticky until the host clears it).

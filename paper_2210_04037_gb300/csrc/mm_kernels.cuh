@@ -19,29 +19,39 @@ __device__ __forceinline__ void report(DevErr* e, int code, long long cell, long
   }
 }
 
-// Derived quantities of a state kept beside it in shared memory (9 values).
-template <class R>
+// Derived quantities of a state kept beside it in shared memory: the stress
+// column and row (the FP64 path keeps both, which differ in the last ulp;
+// the split path keeps the column of the symmetric stress only), density,
+// c_L and G.  NAUX values.
+template <class P>
+struct AuxRec {
+  static constexpr int N = P::split ? 6 : 9;
+};
+
+template <class P, class R>
 __device__ __forceinline__ void put_aux(R* q, const Aux<R>& ax) {
+  constexpr int o = P::split ? 3 : 6;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     q[k] = ax.sd[k];
-    q[3 + k] = ax.sr[k];
+    if (!P::split) q[3 + k] = ax.sr[k];
   }
-  q[6] = ax.rho;
-  q[7] = ax.cL;
-  q[8] = ax.G;
+  q[o] = ax.rho;
+  q[o + 1] = ax.cL;
+  q[o + 2] = ax.G;
 }
 
-template <class R>
+template <class P, class R>
 __device__ __forceinline__ void get_aux(const R* q, Aux<R>& ax) {
+  constexpr int o = P::split ? 3 : 6;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     ax.sd[k] = q[k];
-    ax.sr[k] = q[3 + k];
+    ax.sr[k] = P::split ? q[k] : q[3 + k];
   }
-  ax.rho = q[6];
-  ax.cL = q[7];
-  ax.G = q[8];
+  ax.rho = q[o];
+  ax.cL = q[o + 1];
+  ax.G = q[o + 2];
 }
 
 template <class R>
@@ -53,35 +63,40 @@ __device__ __forceinline__ long long cell_index(const KArgs& a, int x, int y, in
   return (long long)x + (long long)a.n[0] * ((long long)y + (long long)a.n[1] * z);
 }
 
-// Field f of the x block (0: rho E, 1 + l: phi_l) of cell idx in storage.
+// Storage of the second block.  FP64: rho E and phi_0..phi_{N-2} in their
+// slots of the field array.  FP32-split: rho E in the FP64 side array, the N
+// volume fractions as floats in the phi slots plus one extra slot NF.
 template <class P, int DIM, int NMAT, int NH>
-__device__ __forceinline__ long long xslot(const KArgs& a, int k, long long idx) {
+__device__ __forceinline__ long long phislot(const KArgs& a, int l, long long idx) {
   typedef Lay<DIM, NMAT, NH> L;
-  if (P::split) return (long long)k * a.ncell + idx;
-  return (long long)(k == 0 ? L::oE : L::oPHI + k - 1) * a.ncell + idx;
+  return (long long)(l < L::NPHI ? L::oPHI + l : L::NF) * a.ncell + idx;
 }
 
 template <class P, int DIM, int NMAT, int NH>
-__device__ __forceinline__ void load_at(const KArgs& a, long long idx, typename P::R* c, E* cx) {
+__device__ __forceinline__ void load_at(const KArgs& a, long long idx, typename P::R* c,
+                                        typename P::X* cx, double* rhoE) {
   typedef typename P::R R;
   typedef typename P::S S;
+  typedef typename P::X XT;
   typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NPX = Phys<P, DIM, NMAT, NH>::NPX;
   const S* U = (const S*)a.Uin;
 #pragma unroll
   for (int f = 0; f < L::NF; ++f)
     c[f] = (f == L::oE || f < L::oARHO) ? R(0) : R(U[(long long)f * a.ncell + idx]);
 #pragma unroll
-  for (int k = 0; k < 1 + L::NPHI; ++k) {
-    const long long q = xslot<P, DIM, NMAT, NH>(a, k, idx);
-    cx[k] = P::split ? a.Ein[q] : E(U[q]);
-  }
+  for (int l = 0; l < NPX; ++l) cx[1 + l] = XT(U[phislot<P, DIM, NMAT, NH>(a, l, idx)]);
+  const double e = P::split ? a.Ein[idx] : double(U[(long long)L::oE * a.ncell + idx]);
+  cx[0] = XT(e);
+  *rhoE = e;
 }
 
 // Load the conserved state of the cell at axis position gi (ghost cells via
 // the boundary rule of that side), transverse position gw, rest rr.
 template <class P, int DIM, int NMAT, int NH, int AX>
 __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, int rr,
-                                               typename P::R* c, E* cx) {
+                                               typename P::R* c, typename P::X* cx,
+                                               double* rhoE) {
   typedef typename P::R R;
   typedef Lay<DIM, NMAT, NH> L;
   constexpr int TD = (AX == 0) ? 1 : 0;
@@ -103,7 +118,7 @@ __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, i
   co[TD] = gw;
   co[RD] = rr;
   const long long idx = cell_index(a, co[0], co[1], co[2]);
-  load_at<P, DIM, NMAT, NH>(a, idx, c, cx);
+  load_at<P, DIM, NMAT, NH>(a, idx, c, cx, rhoE);
   if (side >= 0 && kind == BC_P) {
     const R Lx = R(a.hi[AX] - a.lo[AX]);
     c[L::oX + AX] += side == 0 ? -Lx : Lx;
@@ -122,39 +137,40 @@ __device__ __forceinline__ long long load_cell(const KArgs& a, int gi, int gw, i
 
 template <class P, int DIM, int NMAT, int NH>
 __device__ __forceinline__ void store_cell(const KArgs& a, long long idx, const typename P::R* c,
-                                           const E* cx) {
+                                           const typename P::X* cx, double rhoE) {
   typedef typename P::S S;
   typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NPX = Phys<P, DIM, NMAT, NH>::NPX;
   S* U = (S*)a.Uout;
 #pragma unroll
   for (int f = 0; f < L::NF; ++f)
     if (f != L::oE && f >= L::oARHO) U[(long long)f * a.ncell + idx] = S(c[f]);
 #pragma unroll
-  for (int k = 0; k < 1 + L::NPHI; ++k) {
-    const long long q = xslot<P, DIM, NMAT, NH>(a, k, idx);
-    if (P::split)
-      a.Eout[q] = cx[k];
-    else
-      U[q] = S(cx[k]);
-  }
+  for (int l = 0; l < NPX; ++l) U[phislot<P, DIM, NMAT, NH>(a, l, idx)] = S(cx[1 + l]);
+  if (P::split)
+    a.Eout[idx] = rhoE;
+  else
+    U[(long long)L::oE * a.ncell + idx] = S(rhoE);
 }
 
 // ------------------------------------------------------------------ sweep ----
 template <class P, int DIM, int AX> struct Tile;
-// FP64 (compute bound on GB300's FP64 rate): small tiles.
-template <> struct Tile<P64, 1, 0> { static constexpr int TL = 64, TW = 1, NT = 64; };
-template <> struct Tile<P64, 2, 0> { static constexpr int TL = 32, TW = 2, NT = 64; };
-template <> struct Tile<P64, 2, 1> { static constexpr int TL = 16, TW = 4, NT = 64; };
-template <> struct Tile<P64, 3, 0> { static constexpr int TL = 32, TW = 2, NT = 64; };
-template <> struct Tile<P64, 3, 1> { static constexpr int TL = 16, TW = 4, NT = 64; };
-template <> struct Tile<P64, 3, 2> { static constexpr int TL = 16, TW = 4, NT = 64; };
-// FP32-split
-template <> struct Tile<P32, 1, 0> { static constexpr int TL = 128, TW = 1, NT = 128; };
-template <> struct Tile<P32, 2, 0> { static constexpr int TL = 32, TW = 4, NT = 128; };
-template <> struct Tile<P32, 2, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
-template <> struct Tile<P32, 3, 0> { static constexpr int TL = 32, TW = 4, NT = 128; };
-template <> struct Tile<P32, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
-template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
+// The halo-extended tile (TL + 4) x TW equals the CTA, so each phase is one
+// pass of the threads (phases 2-4 have 2, 3 and 4 fewer rows of items).
+// FP64 (compute bound on GB300's FP64 rate): 64-thread CTAs.
+template <> struct Tile<P64, 1, 0> { static constexpr int TL = 60, TW = 1, NT = 64; };
+template <> struct Tile<P64, 2, 0> { static constexpr int TL = 28, TW = 2, NT = 64; };
+template <> struct Tile<P64, 2, 1> { static constexpr int TL = 12, TW = 4, NT = 64; };
+template <> struct Tile<P64, 3, 0> { static constexpr int TL = 28, TW = 2, NT = 64; };
+template <> struct Tile<P64, 3, 1> { static constexpr int TL = 12, TW = 4, NT = 64; };
+template <> struct Tile<P64, 3, 2> { static constexpr int TL = 12, TW = 4, NT = 64; };
+// FP32-split: 128-thread CTAs, transverse width 8 (32-byte sectors of x).
+template <> struct Tile<P32, 1, 0> { static constexpr int TL = 124, TW = 1, NT = 128; };
+template <> struct Tile<P32, 2, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
+template <> struct Tile<P32, 2, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
+template <> struct Tile<P32, 3, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 2> { static constexpr int TL = 12, TW = 8, NT = 128; };
 
 template <class P, int DIM, int NMAT, int NH, int AX>
 struct SweepShape {
@@ -162,10 +178,10 @@ struct SweepShape {
   static constexpr int TL = Tile<P, DIM, AX>::TL, TW = Tile<P, DIM, AX>::TW;
   static constexpr int NT = Tile<P, DIM, AX>::NT;
   static constexpr int NF = Lay<DIM, NMAT, NH>::NF;
-  static constexpr int C1 = NF + 9, C2 = NF + 9, C3 = NF + 4;
+  static constexpr int C1 = NF + AuxRec<P>::N, C2 = NF + AuxRec<P>::N, C3 = NF + 4;
   static constexpr int N1 = (TL + 4) * TW, N2 = (TL + 2) * TW, N3 = (TL + 1) * TW, N4 = TL * TW;
-  static constexpr int NX = Lay<DIM, NMAT, NH>::NPHI + 1;
-  static constexpr size_t smem = sizeof(E) * NX * (size_t(N1) + 2 * size_t(N2) + size_t(N3)) +
+  static constexpr int NX = Phys<P, DIM, NMAT, NH>::NX;
+  static constexpr size_t smem = sizeof(typename P::X) * NX * (size_t(N1) + 2 * size_t(N2) + size_t(N3)) +
                                  sizeof(R) * (size_t(N1) * C1 + 2 * size_t(N2) * C2 + size_t(N3) * C3);
   __device__ static __forceinline__ int idx(int p, int w, int len) {
     return AX == 0 ? w * len + p : p * TW + w;
@@ -194,14 +210,15 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
   typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
+  typedef typename P::X XT;
   constexpr int NF = L::NF, NX = SH::NX, TL = SH::TL, TW = SH::TW, NT = SH::NT;
   constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3;
   constexpr int N1 = SH::N1, N2 = SH::N2, N3 = SH::N3, N4 = SH::N4;
   constexpr int TD = (AX == 0) ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  E* x1 = reinterpret_cast<E*>(smem);  // N1 * NX
-  E* x2 = x1 + N1 * NX;                 // 2 * N2 * NX
-  E* x3 = x2 + 2 * N2 * NX;             // N3 * NX
+  XT* x1 = reinterpret_cast<XT*>(smem);  // N1 * NX
+  XT* x2 = x1 + N1 * NX;                  // 2 * N2 * NX
+  XT* x3 = x2 + 2 * N2 * NX;              // N3 * NX
   R* r1 = reinterpret_cast<R*>(x3 + N3 * NX);
   R* r2 = r1 + N1 * C1;
   R* r3 = r2 + 2 * N2 * C2;
@@ -226,12 +243,13 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
     unsigned char okv = 0;
     if (w0 + w < ntw && gi >= -2 && gi < na + 2) {
       R c[NF];
-      E cx[NX];
-      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx);
+      XT cx[NX];
+      double eE;
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
       R* rec = r1 + it * C1;
       Aux<R> ax;
-      if (PH::template u2w<AX>(a, c, cx, rec, x1 + it * NX, ax)) {
-        put_aux(rec + NF, ax);
+      if (PH::template u2w<AX>(a, c, cx, rec, x1 + it * NX, ax, &eE)) {
+        put_aux<P>(rec + NF, ax);
         okv = 1;
       } else {
         report(a.err, ST_ENONFINITE, idx, step);
@@ -254,19 +272,19 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       const R* wm = r1 + im * C1;
       const R* wc = r1 + ic * C1;
       const R* wp = r1 + ip * C1;
-      const E* xm = x1 + im * NX;
-      const E* xc = x1 + ic * NX;
-      const E* xp = x1 + ip * NX;
+      const XT* xm = x1 + im * NX;
+      const XT* xc = x1 + ic * NX;
+      const XT* xp = x1 + ip * NX;
       R uc[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
       R cl[NF], cr[NF];
-      E cxl[NX], cxr[NX];
+      XT cxl[NX], cxr[NX];
       Aux<R> xl, xr;
       bool good;
       {
         R wl[NF], wr[NF];
-        E wxl[NX], wxr[NX];
+        XT wxl[NX], wxr[NX];
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
           const R sl = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
@@ -275,16 +293,16 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
         }
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
-          const E sl = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
-          wxl[k] = xc[k] - 0.5 * sl;
-          wxr[k] = xc[k] + 0.5 * sl;
+          const XT sl = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
+          wxl[k] = xc[k] - XT(0.5) * sl;
+          wxr[k] = xc[k] + XT(0.5) * sl;
         }
         good = PH::template w2u<AX>(a, wl, wxl, cl, cxl, xl) &&
                PH::template w2u<AX>(a, wr, wxr, cr, cxr, xr);
       }
       if (good) {
         R fl[NF], fr[NF], nc[NF], rowl[3], rowr[3], dF[3];
-        E fxl[NX], fxr[NX], ncx[NX];
+        XT fxl[NX], fxr[NX], ncx[NX];
         PH::template flux<AX>(cl, cxl, xl, fl, fxl);
         PH::template flux<AX>(cr, cxr, xr, fr, fxr);
         PH::template frow<AX>(cl, rowl);
@@ -300,23 +318,24 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
         }
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
-          const E inc = 0.5 * E(lam) * ((fxl[k] - fxr[k]) + ncx[k]);
+          const XT inc = XT(0.5) * XT(lam) * ((fxl[k] - fxr[k]) + ncx[k]);
           cxl[k] += inc;
           cxr[k] += inc;
         }
         R tmp[NF];
-        E tmpx[NX];
+        XT tmpx[NX];
         good = PH::template u2w<AX>(a, cl, cxl, tmp, tmpx, xl) &&
                PH::template u2w<AX>(a, cr, cxr, tmp, tmpx, xr);
       }
       if (!good) {
         // first order: both faces take the cell average
-        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl);
+        double eE;
+        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl, &eE);
 #pragma unroll
         for (int k = 0; k < NF; ++k) cr[k] = cl[k];
 #pragma unroll
         for (int k = 0; k < NX; ++k) cxr[k] = cxl[k];
-        get_aux(wc + NF, xl);
+        get_aux<P>(wc + NF, xl);
 #pragma unroll
         for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
         xr = xl;
@@ -328,8 +347,8 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
         ql[k] = cl[k];
         qr[k] = cr[k];
       }
-      put_aux(ql + NF, xl);
-      put_aux(qr + NF, xr);
+      put_aux<P>(ql + NF, xl);
+      put_aux<P>(qr + NF, xr);
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
         x2[(2 * it) * NX + k] = cxl[k];
@@ -350,15 +369,15 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       const R* ql = r2 + (2 * il + 1) * C2;  // right face state of the left cell
       const R* qr = r2 + (2 * ir) * C2;      // left face state of the right cell
       Aux<R> xl, xr;
-      get_aux(ql + NF, xl);
-      get_aux(qr + NF, xr);
+      get_aux<P>(ql + NF, xl);
+      get_aux<P>(qr + NF, xr);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         xl.u[k] = k < DIM ? ql[L::oMOM + k] / xl.rho : R(0);
         xr.u[k] = k < DIM ? qr[L::oMOM + k] / xr.rho : R(0);
       }
       R fo[NF], row[3], uf;
-      E fox[NX];
+      XT fox[NX];
       PH::template riemann<AX>(ql, x2 + (2 * il + 1) * NX, xl, qr, x2 + (2 * ir) * NX, xr, fo,
                                fox, uf, row);
       R* q3 = r3 + it * C3;
@@ -384,14 +403,15 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       const int ic = SH::idx(p4 + 2, w, TL + 4);
       if (ok1[ic] != 1) continue;
       R c[NF];
-      E cx[NX];
-      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx);
+      XT cx[NX];
+      double eE;
+      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
       const R* wc = r1 + ic * C1;
-      const E* xc = x1 + ic * NX;
+      const XT* xc = x1 + ic * NX;
       const R* ql = r3 + fl * C3;
       const R* qr = r3 + fr * C3;
       R uc[3], dF[3], nc[NF];
-      E ncx[NX];
+      XT ncx[NX];
 #pragma unroll
       for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
 #pragma unroll
@@ -400,49 +420,54 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
 #pragma unroll
       for (int k = 0; k < NF; ++k) c[k] = c[k] + lam * ((ql[k] - qr[k]) + nc[k]);
 #pragma unroll
-      for (int k = 0; k < NX; ++k)
-        cx[k] = cx[k] + E(lam) * ((x3[fl * NX + k] - x3[fr * NX + k]) + ncx[k]);
-      store_cell<P, DIM, NMAT, NH>(a, idx, c, cx);
+      for (int k = 1; k < NX; ++k)
+        cx[k] = cx[k] + XT(lam) * ((x3[fl * NX + k] - x3[fr * NX + k]) + ncx[k]);
+      // total energy updated in FP64 (the stored state)
+      eE = eE + double(lam) * ((double(x3[fl * NX]) - double(x3[fr * NX])) + double(ncx[0]));
+      store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
     }
   }
 }
 
 // ------------------------------------------------------------- sources ----
 // Perturbation lookup phi(x) = phi0(X): multilinear, 1 outside the lattice.
-template <int DIM>
-__device__ __forceinline__ double lookup(const KArgs& a, const double X[3]) {
-  if (!a.phi0) return 1.0;
+// T = double (FP64 path) or float (FP32-split).
+template <int DIM, class T>
+__device__ __forceinline__ T lookup(const KArgs& a, const T X[3]) {
+  if (!a.phi0) return T(1);
   long long i0[3] = {0, 0, 0};
-  double w[3] = {0.0, 0.0, 0.0};
+  T w[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    const double s = (X[k] - a.plo[k]) / a.ph[k];
-    if (!(s >= 0.0) || !(s <= double(a.pn[k] - 1))) return 1.0;
+    const T s = (X[k] - T(a.plo[k])) / T(a.ph[k]);
+    if (!(s >= T(0)) || !(s <= T(a.pn[k] - 1))) return T(1);
     long long i = (long long)floor(s);
     if (i > a.pn[k] - 2) i = a.pn[k] - 2;
     i0[k] = i;
-    w[k] = s - double(i);
+    w[k] = s - T(i);
   }
-  double v = 0.0;
+  T v = T(0);
 #pragma unroll
   for (int c = 0; c < (1 << DIM); ++c) {
-    double wt = 1.0;
+    T wt = T(1);
     long long idx = 0, str = 1;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       const int bit = (c >> k) & 1;
-      wt *= bit ? w[k] : 1.0 - w[k];
+      wt *= bit ? w[k] : T(1) - w[k];
       idx += (i0[k] + bit) * str;
       str *= a.pn[k];
     }
-    v += wt * double(__ldg(a.phi0 + idx));
+    v += wt * T(__ldg(a.phi0 + idx));
   }
   return v;
 }
 
 // Mixture yield stress sum_l phi_l phi (1-D_l) sigma_Y,l (Johnson-Cook, rate
 // factor floored at 1, zero at critical damage) and its derivative in dl.
-template <int NMAT>
+// The Johnson-Cook powers and logarithm are evaluated in T (FP64 on the FP64
+// path, FP32 on the split path); the sums are FP64.
+template <int NMAT, class T>
 __device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, const double* eps,
                                             const double* D, double phihat, double dt, double dl,
                                             double* dY) {
@@ -456,12 +481,12 @@ __device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, c
     const double e = (eps[l] > 0.0 ? eps[l] : 0.0) + dl;
     double hard = m.c1, dhard = 0.0;
     if (m.c2 != 0.0) {
-      hard += m.c2 * pow(e, m.n_hard);
-      if (e > 0.0) dhard = m.c2 * m.n_hard * pow(e, m.n_hard - 1.0);
+      hard += m.c2 * double(mpow(T(e), T(m.n_hard)));
+      if (e > 0.0) dhard = m.c2 * m.n_hard * double(mpow(T(e), T(m.n_hard - 1.0)));
     }
     double Rr = 1.0, dR = 0.0;
     if (m.c3 != 0.0 && dl > 0.0) {
-      const double r = 1.0 + m.c3 * log(dl / (dt * m.edot0));
+      const double r = 1.0 + m.c3 * double(mlog(T(dl / (dt * m.edot0))));
       if (r > 1.0) {
         Rr = r;
         dR = m.c3 / dl;
@@ -475,40 +500,49 @@ __device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, c
   return Y;
 }
 
-__device__ __forceinline__ double eps_thresh(double et, double ec, double n, double Rt) {
-  const double num = pow(ec, 2.0 * n) - pow(et, 2.0 * n);
-  const double den = pow(ec, 2.0 * n / Rt) - pow(et, 2.0 * n / Rt);
-  return pow(et, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));
+// Triaxiality-dependent threshold strain; eps_c^(2n), eps_t^(2n) precomputed.
+template <class T>
+__device__ __forceinline__ T eps_thresh(const MatK& m, T Rt) {
+  const T n = T(m.n_hard), et = T(m.eps_t), ec = T(m.eps_c);
+  const T num = T(m.bon_ec2n) - T(m.bon_et2n);
+  const T den = mpow(ec, T(2) * n / Rt) - mpow(et, T(2) * n / Rt);
+  return mpow(et, T(1) / Rt) / mpow(Rt, T(1) / n) * mpow(num / den, T(1) / (T(2) * n));
 }
 
-__device__ __forceinline__ double dmg_rate(const MatK& m, double D, double eps, double ed,
-                                           double p, double Rt, double th) {
-  if (m.damage == 2) return m.Ddot0 * (1.0 - D) * ed;
-  if (!(p < 0.0) || !(eps > th)) return 0.0;
-  if (D >= m.D_crit) return 0.0;
-  const double aD = m.alpha_D, Dc = m.D_crit;
-  return aD * pow(Dc, 1.0 / aD) / log(m.eps_c / m.eps_t) * Rt * pow(Dc - D, (aD - 1.0) / aD) *
-         ed / eps;
+template <class T>
+__device__ __forceinline__ T dmg_rate(const MatK& m, T D, T eps, T ed, T Rt, T th, bool tension) {
+  if (m.damage == 2) return T(m.Ddot0) * (T(1) - D) * ed;
+  if (!tension || !(eps > th)) return T(0);
+  if (D >= T(m.D_crit)) return T(0);
+  const T aD = T(m.alpha_D), Dc = T(m.D_crit);
+  return T(m.bon_k) * Rt * mpow(Dc - D, (aD - T(1)) / aD) * ed / eps;
 }
 
-__device__ __forceinline__ double damage_rk4(const MatK& m, double D, double eps0, double deps,
-                                             double dt, double p, double seq, double rho) {
-  if (m.damage == 0 || !(deps > 0.0)) return D;
-  double Rt = 1.0, th = 0.0;
+// RK4 over the step of the damage rate with eps_p(t) linear in t (the
+// plastic increment deps over dt), p and sigma_eq held at the returned
+// state; clamped to [0, D_crit].  Bonora: zero unless p < 0 (checked first).
+template <class T>
+__device__ __forceinline__ T damage_rk4(const MatK& m, T D, T eps0, T deps, T dt, T p, T seq,
+                                        T rho) {
+  if (m.damage == 0 || !(deps > T(0))) return D;
+  T Rt = T(1), th = T(0);
+  const bool tension = p < T(0);
   if (m.damage == 1) {
-    if (!(seq > 0.0)) return D;
-    const double x = p / seq;
-    Rt = 2.0 / 3.0 * (1.0 + m.poisson) + 3.0 * (1.0 - 2.0 * m.poisson) * (m.rho0 / rho) * (x * x);
-    th = eps_thresh(m.eps_t, m.eps_c, m.n_hard, Rt);
+    if (!(seq > T(0))) return D;
+    if (!tension) return D < T(0) ? T(0) : (D > T(m.D_crit) ? T(m.D_crit) : D);
+    const T x = p / seq;
+    Rt = T(2) / T(3) * (T(1) + T(m.poisson)) +
+         T(3) * (T(1) - T(2) * T(m.poisson)) * (T(m.rho0) / rho) * (x * x);
+    th = eps_thresh<T>(m, Rt);
   }
-  const double ed = deps / dt;
-  const double k1 = dmg_rate(m, D, eps0, ed, p, Rt, th);
-  const double k2 = dmg_rate(m, D + 0.5 * dt * k1, eps0 + 0.5 * deps, ed, p, Rt, th);
-  const double k3 = dmg_rate(m, D + 0.5 * dt * k2, eps0 + 0.5 * deps, ed, p, Rt, th);
-  const double k4 = dmg_rate(m, D + dt * k3, eps0 + deps, ed, p, Rt, th);
-  double Dn = D + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
-  if (Dn < 0.0) Dn = 0.0;
-  if (Dn > m.D_crit) Dn = m.D_crit;
+  const T ed = deps / dt;
+  const T k1 = dmg_rate<T>(m, D, eps0, ed, Rt, th, tension);
+  const T k2 = dmg_rate<T>(m, D + T(0.5) * dt * k1, eps0 + T(0.5) * deps, ed, Rt, th, tension);
+  const T k3 = dmg_rate<T>(m, D + T(0.5) * dt * k2, eps0 + T(0.5) * deps, ed, Rt, th, tension);
+  const T k4 = dmg_rate<T>(m, D + dt * k3, eps0 + deps, ed, Rt, th, tension);
+  T Dn = D + dt / T(6) * (k1 + T(2) * k2 + T(2) * k3 + k4);
+  if (Dn < T(0)) Dn = T(0);
+  if (Dn > T(m.D_crit)) Dn = T(m.D_crit);
   return Dn;
 }
 
@@ -520,22 +554,30 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
+  typedef typename P::X XT;
   constexpr int NF = L::NF, NX = PH::NX;
   const double dt = a.info->dt;
   const long long step = a.info->steps;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E cx[NX], wx[NX];
-    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
+    XT cx[NX], wx[NX];
+    double eE;
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
     Aux<R> ax;
-    if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) {
+    typename PH::Mix mx0;
+    if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }
     double phi[NMAT], eps[NMAT], Dm[NMAT];
     R rho[NMAT], Dr[NMAT], phir[NMAT];
-    PH::fractions(cx, phi);
+    {
+      XT phx[NMAT];
+      PH::fractions(cx, phx);
+#pragma unroll
+      for (int l = 0; l < NMAT; ++l) phi[l] = double(phx[l]);
+    }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       phir[l] = R(phi[l]);
@@ -550,21 +592,25 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
         }
       Dr[l] = R(Dm[l]);
     }
-    double Xc[3] = {0.0, 0.0, 0.0};
+    R Xc[3] = {R(0), R(0), R(0)};
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) Xc[k] = double(w[L::oX + k]);
-    const double phihat = lookup<DIM>(a, Xc);
+    for (int k = 0; k < DIM; ++k) Xc[k] = w[L::oX + k];
+    const double phihat = double(lookup<DIM, R>(a, Xc));
     // shear modulus of the mixture; whether the cell may yield
     double Gm = 0.0;
     bool can_yield = true;
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       const MatK& m = a.mat[l];
-      R te, tp, tdp, tG;
-      thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
-      Gm += phi[l] * double(tG);
       if (m.eos == 1 && m.G0 > 0.0 && m.plasticity != 1) can_yield = false;
+      if constexpr (!P::split) {
+        R te, tp, tdp, tG;
+        thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
+        Gm += phi[l] * double(tG);
+      }
     }
+    // split path: G_mix of the recovery (G does not depend on J2)
+    if constexpr (P::split) Gm = double(mx0.Gm);
     // det Fbar = 1
     R X[9];
     PH::fullX(c, X);
@@ -585,33 +631,55 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) X[k] /= c3;
     }
+    // dev(H), |dev(H)|, and (for the return) either eigen-pairs or the
+    // series form of exp((k-1) dev(H)) - I
     R devH[9], h[3], V[9];
-    if (!hencky<P::aform>(X, devH, h, V)) {
-      report(a.err, ST_ENONFINITE, cell, step);
-      continue;
+    R J2 = R(0);
+    bool series = false;
+    if constexpr (P::split) {
+      // the recovery's dev(H): scaling Fbar by det^(-1/3) leaves dev(H)
+      // unchanged; the series form of the return applies while the stretch
+      // is small (|dev(H)|_F <= 0.05), else the eigen-pairs are taken below
+      if (mx0.J2 <= R(2.5e-3)) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) devH[q] = mx0.devH[q];
+        J2 = mx0.J2;
+        series = true;
+      }
+    }
+    if (!series) {
+      if (!hencky<P::aform>(X, devH, h, V)) {
+        report(a.err, ST_ENONFINITE, cell, step);
+        continue;
+      }
+      J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
     }
     double dl = 0.0;
     if (can_yield && Gm > 0.0) {
-      const double J = sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
-                            double(h[2]) * double(h[2]));
+      const double J = series ? sqrt(double(J2))
+                              : sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
+                                     double(h[2]) * double(h[2]));
       const double str = sqrt(6.0) * Gm * J;
-      const double Y0 = yield_mix<NMAT>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
+      const double Y0 = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
       if (str > Y0) {
+        // stopping rule at the accuracy of the yield-stress evaluation
+        const double gtol = P::split ? 1e-6 : 8.0 * 2.220446049250313e-16;
+        const double xtol = P::split ? 1e-7 : 4.0 * 2.220446049250313e-16;
         const double b0 = str / (3.0 * Gm);
         double lo = 0.0, hi = b0, x = (str - Y0) / (3.0 * Gm);
         bool conv = false;
         for (int it = 0; it < 200; ++it) {
           double dY;
-          const double Y = yield_mix<NMAT>(a, phi, eps, Dm, phihat, dt, x, &dY);
+          const double Y = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, x, &dY);
           const double g = str - 3.0 * Gm * x - Y;
-          if (fabs(g) <= 8.0 * 2.220446049250313e-16 * str) {
+          if (fabs(g) <= gtol * str) {
             conv = true;
             break;
           }
           if (g > 0.0) lo = x; else hi = x;
           double nx = x - g / (-3.0 * Gm - dY);
           if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-          if (fabs(nx - x) <= 4.0 * 2.220446049250313e-16 * b0) {
+          if (fabs(nx - x) <= xtol * b0) {
             x = nx;
             conv = true;
             break;
@@ -624,17 +692,25 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
         }
         dl = x;
         const R k = R((str - 3.0 * Gm * dl) / str);
-        // Fbar <- S Fbar, S = V diag(exp((k-1) h)) V^T (the rotation is kept);
-        // in A form A <- (S - I)(I + A) + A with S - I from expm1
-        R m1[3], Sm[9], Xn[9];
+        // Fbar <- S Fbar, S = exp((k-1) dev(H)) (the rotation is kept); in A
+        // form A <- (S - I)(I + A) + A
+        R Sm[9], Xn[9];
+        if (series) {
+          R Y[9];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
+          for (int q = 0; q < 9; ++q) Y[q] = (k - R(1)) * devH[q];
+          expm1_series(Y, Sm);
+        } else {
+          R m1[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+          for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
-            Sm[3 * i + j] = V[3 * i + 0] * m1[0] * V[3 * j + 0] + V[3 * i + 1] * m1[1] * V[3 * j + 1] +
-                            V[3 * i + 2] * m1[2] * V[3 * j + 2];
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              Sm[3 * i + j] = V[3 * i + 0] * m1[0] * V[3 * j + 0] + V[3 * i + 1] * m1[1] * V[3 * j + 1] +
+                              V[3 * i + 2] * m1[2] * V[3 * j + 2];
+        }
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -650,9 +726,9 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = X[FC<DIM>::idx(k)];
     if (dl > 0.0) {
       R w2[NF];
-      E wx2[NX];
+      XT wx2[NX];
       Aux<R> as;
-      if (!PH::template u2w<0>(a, c, cx, w2, wx2, as)) {
+      if (!PH::template u2w<0>(a, c, cx, w2, wx2, as, &eE)) {
         report(a.err, ST_ENONFINITE, cell, step);
         continue;
       }
@@ -665,13 +741,14 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
         for (int hh = 0; hh < NH; ++hh)
           if (a.hslot[l] == hh) {
             const R arho = c[L::oARHO + l];
-            const double Dn = damage_rk4(a.mat[l], Dm[l], eps[l], dl, dt, wx2[0], seq, double(rho[l]));
+            const double Dn = double(damage_rk4<R>(a.mat[l], R(Dm[l]), R(eps[l]), R(dl), R(dt),
+                                                   R(wx2[0]), R(seq), rho[l]));
             c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
             c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
           }
       }
     }
-    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx);
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx, eE);
   }
 }
 
@@ -680,16 +757,19 @@ template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_cfl(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef typename P::X XT;
   constexpr int NF = Lay<DIM, NMAT, NH>::NF, NX = PH::NX;
   const long long step = a.info->steps;
   double smax = 0.0;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E cx[NX], wx[NX];
-    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
+    XT cx[NX], wx[NX];
+    double eE;
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
     Aux<R> ax;
-    if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) {
+    typename PH::Mix mx0;
+    if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }
@@ -717,11 +797,13 @@ __global__ void k_init(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
+  typedef typename P::X XT;
   constexpr int NF = L::NF, NX = PH::NX;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R w[NF], c[NF];
-    E wx[NX], cx[NX];
+    XT wx[NX], cx[NX];
+    double phisum = 0.0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       double v = a.prim[(long long)f * a.ncell + cell];
@@ -730,12 +812,18 @@ __global__ void k_init(KArgs a) {
         if (ij % 4 == 0) v -= 1.0;
       }
       w[f] = R(v);
-      if (f == L::oE) wx[0] = v;
-      if (f < L::oARHO) wx[1 + f] = v;
+      if (f == L::oE) wx[0] = XT(v);
+      if (f < L::oARHO) {
+        wx[1 + f] = XT(v);
+        phisum += v;
+      }
     }
+    // all N fractions carried: the last one formed once, here, in FP64
+    if (P::allphi) wx[NX - 1] = XT(1.0 - phisum);
     Aux<R> ax;
-    if (!PH::template w2u<0>(a, w, wx, c, cx, ax)) report(a.err, ST_ENONFINITE, cell, 0);
-    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx);
+    double eE = 0.0;
+    if (!PH::template w2u<0>(a, w, wx, c, cx, ax, &eE)) report(a.err, ST_ENONFINITE, cell, 0);
+    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx, eE);
   }
 }
 
@@ -744,25 +832,27 @@ __global__ void k_read(KArgs a, int primitive) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
+  typedef typename P::X XT;
   constexpr int NF = L::NF, NX = PH::NX;
   for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
        cell += (long long)gridDim.x * blockDim.x) {
     R c[NF], w[NF];
-    E cx[NX], wx[NX];
-    load_at<P, DIM, NMAT, NH>(a, cell, c, cx);
+    XT cx[NX], wx[NX];
+    double eE;
+    load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
     const R* src = c;
-    const E* srcx = cx;
+    const XT* srcx = cx;
     if (primitive) {
       Aux<R> ax;
-      if (!PH::template u2w<0>(a, c, cx, w, wx, ax)) report(a.err, ST_ENONFINITE, cell, 0);
+      if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE)) report(a.err, ST_ENONFINITE, cell, 0);
       src = w;
       srcx = wx;
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       double v = double(src[f]);
-      if (f == L::oE) v = srcx[0];
-      if (f < L::oARHO) v = srcx[1 + f];
+      if (f == L::oE) v = primitive ? double(srcx[0]) : eE;
+      if (f < L::oARHO) v = double(srcx[1 + f]);
       if (P::aform && f >= L::oF && f < L::oF + L::NFC) {
         const int ij = FC<DIM>::idx(f - L::oF);
         if (ij % 4 == 0) v += 1.0;
@@ -789,8 +879,7 @@ __global__ void __launch_bounds__(256) k_totals(KArgs a) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k)
       acc[NMAT + k] += double(U[(long long)(L::oMOM + k) * a.ncell + cell]);
-    const long long q = xslot<P, DIM, NMAT, NH>(a, 0, cell);
-    acc[NMAT + 3] += P::split ? a.Ein[q] : double(U[q]);
+    acc[NMAT + 3] += P::split ? a.Ein[cell] : double(U[(long long)L::oE * a.ncell + cell]);
   }
   __shared__ double red[8][NQ];
 #pragma unroll

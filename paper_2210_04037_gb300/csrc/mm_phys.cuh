@@ -20,17 +20,25 @@ namespace mm {
 
 typedef double E;  // energy scalar type in both precisions
 
+// R: working precision; S: storage of the R fields; X: the second block
+// (rho E / p and the volume fractions); allphi: all N volume fractions are
+// carried (each its own advected field) instead of N-1 with the last one
+// 1 - sum, so no fraction is ever formed by cancellation.
 struct P64 {
   typedef double R;
   typedef double S;
+  typedef double X;
   static constexpr bool split = false;
   static constexpr bool aform = false;
+  static constexpr bool allphi = false;
 };
 struct P32 {
   typedef float R;
   typedef float S;
+  typedef float X;
   static constexpr bool split = true;
   static constexpr bool aform = true;
+  static constexpr bool allphi = true;
 };
 
 // ---------------------------------------------------------------- math ----
@@ -45,7 +53,9 @@ __device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double mpow(double x, double y) { return pow(x, y); }
-__device__ __forceinline__ float mpow(float x, float y) { return powf(x, y); }
+// FP32 power by exp2(y log2 x) on the special-function unit (x > 0): the
+// closures' powers of compression ratios need relative, not last-ulp, accuracy
+__device__ __forceinline__ float mpow(float x, float y) { return exp2f(y * __log2f(x)); }
 __device__ __forceinline__ double mcbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float mcbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double mabs(double x) { return fabs(x); }
@@ -205,6 +215,104 @@ __device__ __forceinline__ bool hencky(const R X[9], R devH[9], R h[3], R V[9]) 
   return true;
 }
 
+// ln(I + B) of a symmetric B with small norm by its power series
+// sum_k (-1)^(k+1) B^k / k in Horner form; returns false (leaving L unset)
+// when |B|_F is too large for the chosen number of terms, in which case the
+// caller takes the eigen-decomposition.  Truncation error <= |B|^(K+1)/(K+1)
+// relative to |B| < 1e-8 for the thresholds below.
+template <class R>
+__device__ __forceinline__ bool log_series(const R B[9], R L[9]) {
+  const R n2 = B[0] * B[0] + B[4] * B[4] + B[8] * B[8] + R(2) * (B[1] * B[1] + B[2] * B[2] + B[5] * B[5]);
+  int K;
+  if (n2 <= R(4e-4)) K = 5;          // |B| <= 0.02
+  else if (n2 <= R(1e-2)) K = 9;     // |B| <= 0.1
+  else return false;
+  // M <- I/K; then M <- I/k - B M for k = K-1 .. 1; L = B M
+  R M[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) M[q] = (q % 4 == 0) ? R(1) / R(K) : R(0);
+  for (int k = K - 1; k >= 1; --k) {
+    R T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        T[3 * i + j] = (i == j ? R(1) / R(k) : R(0)) -
+                       (B[3 * i + 0] * M[0 + j] + B[3 * i + 1] * M[3 + j] + B[3 * i + 2] * M[6 + j]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) M[q] = T[q];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      L[3 * i + j] = B[3 * i + 0] * M[0 + j] + B[3 * i + 1] * M[3 + j] + B[3 * i + 2] * M[6 + j];
+  return true;
+}
+
+// Large-strain fallback of hencky_fast: one out-of-line copy, so the rarely
+// taken eigen-decomposition does not bloat every inlined call site.
+static __device__ __noinline__ bool hencky_jacobi_f32(const float* A, float* devH) {
+  float h[3], V[9];
+  return hencky<true>(A, devH, h, V);
+}
+
+// dev(H) and J2 = tr(dev(H)^2) of A = Fbar - I, by the series when the
+// elastic stretch is small (every metal state and the diffuse zone kept near
+// the yield surface), else by the eigen-decomposition.
+template <class R>
+__device__ __forceinline__ bool hencky_fast(const R A[9], R devH[9], R& J2) {
+  R B[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const R s = A[3 * i + j] + A[3 * j + i] +
+                  (A[3 * i + 0] * A[3 * j + 0] + A[3 * i + 1] * A[3 * j + 1] + A[3 * i + 2] * A[3 * j + 2]);
+      B[3 * i + j] = s;
+      B[3 * j + i] = s;
+    }
+  R L[9];
+  if (log_series(B, L)) {
+    const R tr = (L[0] + L[4] + L[8]) / R(3);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) devH[q] = R(0.5) * (L[q] - ((q % 4 == 0) ? tr : R(0)));
+  } else {
+    if (!hencky_jacobi_f32(A, devH)) return false;
+  }
+  J2 = R(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) J2 += devH[q] * devH[q];
+  return mfinite(J2);
+}
+
+// exp(X) - I of a symmetric X with |X|_F <= 0.06 by its power series
+// (truncation below 1e-10 relative).
+template <class R>
+__device__ __forceinline__ void expm1_series(const R X[9], R M[9]) {
+  constexpr int K = 6;
+  // Horner: E = X (I + X/2 (I + X/3 (I + X/4 (I + X/5 (I + X/6)))))
+  R P[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) P[q] = (q % 4 == 0) ? R(1) : R(0);
+#pragma unroll
+  for (int k = K; k >= 1; --k) {
+    R Q[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Q[3 * i + j] = (X[3 * i + 0] * P[0 + j] + X[3 * i + 1] * P[3 + j] + X[3 * i + 2] * P[6 + j]) / R(k);
+    if (k > 1) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) P[q] = Q[q] + ((q % 4 == 0) ? R(1) : R(0));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) M[q] = Q[q];
+    }
+  }
+}
+
 // ------------------------------------------------------------ states ----
 // Derived quantities of one state: velocity, the stress column d (sigma_kd,
 // momentum flux and tangential tractions), the stress row d (sigma_dk, energy
@@ -225,9 +333,11 @@ struct Aux {
 template <class P, int DIM, int NMAT, int NH>
 struct Phys {
   typedef typename P::R R;
+  typedef typename P::X XT;
   typedef Lay<DIM, NMAT, NH> L;
   static constexpr int NF = L::NF;
-  static constexpr int NX = 1 + L::NPHI;
+  static constexpr int NPX = P::allphi ? NMAT : L::NPHI;  // fractions in the X block
+  static constexpr int NX = 1 + NPX;
   static constexpr bool AF = P::aform;
 
   // Full 3x3 stored tensor (Fbar, or A = Fbar - I): inactive comps are 0 off
@@ -252,15 +362,20 @@ struct Phys {
     return D;
   }
 
-  // Volume fractions of all N materials from the x block.
-  __device__ static __forceinline__ void fractions(const E* x, E phi[NMAT]) {
-    E s = 0.0;
+  // Volume fractions of all N materials from the X block.
+  __device__ static __forceinline__ void fractions(const XT* x, XT phi[NMAT]) {
+    if constexpr (P::allphi) {
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      phi[l] = x[1 + l];
-      s += phi[l];
+      for (int l = 0; l < NMAT; ++l) phi[l] = x[1 + l];
+    } else {
+      XT s = XT(0);
+#pragma unroll
+      for (int l = 0; l < NMAT - 1; ++l) {
+        phi[l] = x[1 + l];
+        s += phi[l];
+      }
+      phi[NMAT - 1] = XT(1) - s;
     }
-    phi[NMAT - 1] = 1.0 - s;
   }
 
   // Mixture quantities of the isobaric Allaire closure with one deformation
@@ -275,9 +390,13 @@ struct Phys {
   __device__ static __forceinline__ bool mixture(const KArgs& a, const R phi[NMAT],
                                                  const R rho[NMAT], const R D[NMAT],
                                                  const R X[9], Mix& mx) {
-    R h[3], V[9];
-    if (!hencky<AF>(X, mx.devH, h, V)) return false;
-    mx.J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    if constexpr (P::split) {
+      if (!hencky_fast(X, mx.devH, mx.J2)) return false;
+    } else {
+      R h[3], V[9];
+      if (!hencky<AF>(X, mx.devH, h, V)) return false;
+      mx.J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    }
     mx.xi = R(0);
     mx.Gm = R(0);
 #pragma unroll
@@ -286,7 +405,10 @@ struct Phys {
       const R psi = m.damage != 0 ? R(1) - D[l] : R(1);
       R G;
       thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G);
-      mx.xi += phi[l] / R(m.Gamma);
+      if constexpr (P::split)
+        mx.xi += phi[l] * R(m.xi);
+      else
+        mx.xi += phi[l] / R(m.Gamma);
       mx.Gm += phi[l] * G;
     }
     return true;
@@ -318,16 +440,18 @@ struct Phys {
     return true;
   }
 
-  // primitive (w, wx) -> conserved (c, cx).
+  // primitive (w, wx) -> conserved (c, cx); the total energy is also
+  // returned in FP64 (rhoE_out, may be null) for storage.
   template <int AX>
-  __device__ static bool w2u(const KArgs& a, const R* w, const E* wx, R* c, E* cx, Aux<R>& ax) {
-    E phid[NMAT];
+  __device__ static bool w2u(const KArgs& a, const R* w, const XT* wx, R* c, XT* cx, Aux<R>& ax,
+                             double* rhoE_out = nullptr) {
+    XT phid[NMAT];
     R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
     fractions(wx, phid);
     ax.rho = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      if (!(phid[l] > 0.0)) return false;
+      if (!(phid[l] > XT(0))) return false;
       phi[l] = R(phid[l]);
       rho[l] = w[L::oARHO + l];
       if (!(rho[l] > R(0))) return false;
@@ -337,29 +461,38 @@ struct Phys {
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) ax.u[k] = k < DIM ? w[L::oMOM + k] : R(0);
-    const E pE = wx[0];
-    const R p = R(pE);
+    const E pE = E(wx[0]);
+    const R p = R(wx[0]);
     R X[9];
     fullX(w, X);
     Mix mx;
     if (!mixture(a, phi, rho, D, X, mx)) return false;
-    E rhoe = 0.0;
+    E rhoe = 0.0, ke = 0.0;
+    if constexpr (P::split) {
+      // FP32: the face states need float accuracy only
+      R re = R(0);
 #pragma unroll
-    for (int l = 0; l < NMAT; ++l)
-      rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
-    const E ke = 0.5 * E(ax.rho) *
-                 (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
+      for (int l = 0; l < NMAT; ++l) re += arho[l] * mx.e[l] + phi[l] * R(a.mat[l].xi) * (p - mx.p[l]);
+      rhoe = E(re);
+      ke = E(R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]));
+    } else {
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      cx[1 + l] = phid[l];
-      c[L::oPHI + l] = R(0);
+      for (int l = 0; l < NMAT; ++l)
+        rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
+      ke = 0.5 * E(ax.rho) *
+           (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
     }
+#pragma unroll
+    for (int l = 0; l < NPX; ++l) cx[1 + l] = phid[l];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) c[L::oPHI + l] = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) c[L::oARHO + l] = arho[l];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) c[L::oMOM + k] = ax.rho * ax.u[k];
     c[L::oE] = R(0);
-    cx[0] = rhoe + ke;
+    cx[0] = XT(rhoe + ke);
+    if (rhoE_out) *rhoE_out = rhoe + ke;
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = w[L::oF + k];
 #pragma unroll
@@ -378,18 +511,24 @@ struct Phys {
 
   // conserved (c, cx) -> primitive (w, wx), with
   // p = (rho e - sum_l phi_l rho_l e_ref,l + sum_l phi_l p_ref,l / Gamma_l) / xi.
+  // rhoE_d (may be null): the cell's total energy in FP64 (stored state);
+  // face states pass null and use cx[0].
   template <int AX>
-  __device__ static bool u2w(const KArgs& a, const R* c, const E* cx, R* w, E* wx, Aux<R>& ax) {
-    E phid[NMAT];
+  __device__ static bool u2w(const KArgs& a, const R* c, const XT* cx, R* w, XT* wx, Aux<R>& ax,
+                             const double* rhoE_d = nullptr, Mix* mxo = nullptr) {
+    XT phid[NMAT];
     R phi[NMAT], rho[NMAT], arho[NMAT], D[NMAT];
     fractions(cx, phid);
     ax.rho = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       arho[l] = c[L::oARHO + l];
-      if (!(phid[l] > 0.0) || !(arho[l] > R(0))) return false;
+      if (!(phid[l] > XT(0)) || !(arho[l] > R(0))) return false;
       phi[l] = R(phid[l]);
-      rho[l] = R(E(arho[l]) / phid[l]);
+      if constexpr (P::split)
+        rho[l] = arho[l] / phi[l];
+      else
+        rho[l] = R(E(arho[l]) / phid[l]);
       ax.rho += arho[l];
     }
     bool ok = true;
@@ -410,24 +549,34 @@ struct Phys {
     fullX(c, X);
     Mix mx;
     if (!mixture(a, phi, rho, D, X, mx)) return false;
-    const E ke = 0.5 * E(ax.rho) *
-                 (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
-    E num = cx[0] - ke;
+    E pE;
+    if constexpr (P::split) {
+      // rho e = rho E - rho |u|^2/2 with the one subtraction in FP64 (rho E
+      // is kept in FP64 so its updates do not accumulate FP32 rounding)
+      const R ke = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
+      R num = rhoE_d ? R(*rhoE_d - E(ke)) : R(cx[0]) - ke;
 #pragma unroll
-    for (int l = 0; l < NMAT; ++l)
-      num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
-    const E pE = num / E(mx.xi);
+      for (int l = 0; l < NMAT; ++l) num += -arho[l] * mx.e[l] + phi[l] * R(a.mat[l].xi) * mx.p[l];
+      pE = E(num / mx.xi);
+    } else {
+      const E ke = 0.5 * E(ax.rho) *
+                   (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
+      E num = (rhoE_d ? *rhoE_d : E(cx[0])) - ke;
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      wx[1 + l] = phid[l];
-      w[L::oPHI + l] = R(0);
+      for (int l = 0; l < NMAT; ++l)
+        num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
+      pE = num / E(mx.xi);
     }
+#pragma unroll
+    for (int l = 0; l < NPX; ++l) wx[1 + l] = phid[l];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) w[L::oPHI + l] = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) w[L::oARHO + l] = rho[l];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) w[L::oMOM + k] = ax.u[k];
     w[L::oE] = R(0);
-    wx[0] = pE;
+    wx[0] = XT(pE);
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) w[L::oF + k] = c[L::oF + k];
 #pragma unroll
@@ -435,8 +584,9 @@ struct Phys {
 #pragma unroll
     for (int k = 0; k < NF; ++k) ok = ok && mfinite(w[k]) && mfinite(c[k]);
 #pragma unroll
-    for (int k = 0; k < NX; ++k) ok = ok && isfinite(cx[k]) && isfinite(wx[k]);
+    for (int k = 0; k < NX; ++k) ok = ok && mfinite(cx[k]) && mfinite(wx[k]);
     if (!ok) return false;
+    if (mxo) *mxo = mx;
     return finish<AX>(a, R(pE), rho, arho, mx, ax);
   }
 
@@ -457,21 +607,23 @@ struct Phys {
   // sigma_kd, rho E u_d - sigma_dj u_j, Fbar_ij u_d - Fbar_dj u_i (zero for
   // row d).
   template <int AX>
-  __device__ static __forceinline__ void flux(const R* c, const E* cx, const Aux<R>& ax, R* f,
-                                              E* fx) {
+  __device__ static __forceinline__ void flux(const R* c, const XT* cx, const Aux<R>& ax, R* f,
+                                              XT* fx) {
     const R ud = ax.u[AX];
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      fx[1 + l] = cx[1 + l] * E(ud);
-      f[L::oPHI + l] = R(0);
-    }
+    for (int l = 0; l < NPX; ++l) fx[1 + l] = cx[1 + l] * XT(ud);
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) f[L::oPHI + l] = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) f[L::oARHO + l] = c[L::oARHO + l] * ud;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) f[L::oMOM + k] = c[L::oMOM + k] * ud - ax.sd[k];
     f[L::oE] = R(0);
-    fx[0] = cx[0] * E(ud) - (E(ax.sr[0]) * E(ax.u[0]) + E(ax.sr[1]) * E(ax.u[1]) +
-                             E(ax.sr[2]) * E(ax.u[2]));
+    if constexpr (P::split)
+      fx[0] = XT(R(cx[0]) * ud - (ax.sr[0] * ax.u[0] + ax.sr[1] * ax.u[1] + ax.sr[2] * ax.u[2]));
+    else
+      fx[0] = cx[0] * E(ud) - (E(ax.sr[0]) * E(ax.u[0]) + E(ax.sr[1]) * E(ax.u[1]) +
+                               E(ax.sr[2]) * E(ax.u[2]));
     R row[3];
     frow<AX>(c, row);
 #pragma unroll
@@ -488,13 +640,13 @@ struct Phys {
   // Non-conservative terms per unit 1/dx: phi and X take q_c du; the
   // deformation tensor 2/3 Fbar_ij du - u_i dFbar_dj.
   template <int AX>
-  __device__ static __forceinline__ void noncons(const R* wc, const E* wcx, const R uc[3], R du,
-                                                 const R dFrow[3], R* nc, E* ncx) {
+  __device__ static __forceinline__ void noncons(const R* wc, const XT* wcx, const R uc[3], R du,
+                                                 const R dFrow[3], R* nc, XT* ncx) {
 #pragma unroll
     for (int k = 0; k < NF; ++k) nc[k] = R(0);
-    ncx[0] = 0.0;
+    ncx[0] = XT(0);
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) ncx[1 + l] = wcx[1 + l] * E(du);
+    for (int l = 0; l < NPX; ++l) ncx[1 + l] = wcx[1 + l] * XT(du);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) nc[L::oX + k] = wc[L::oX + k] * du;
 #pragma unroll
@@ -510,8 +662,8 @@ struct Phys {
   // is the HLLC solver.  Outputs the flux, the normal velocity at the face
   // and the row d of Fbar on the upwind side of the contact.
   template <int AX>
-  __device__ static void riemann(const R* cL_, const E* xL, const Aux<R>& aL, const R* cR_,
-                                 const E* xR, const Aux<R>& aR, R* fo, E* fox, R& uface,
+  __device__ static void riemann(const R* cL_, const XT* xL, const Aux<R>& aL, const R* cR_,
+                                 const XT* xR, const Aux<R>& aR, R* fo, XT* fox, R& uface,
                                  R frowo[3]) {
     const R uL = aL.u[AX], uR = aR.u[AX];
     const R a1 = uL - aL.cL, a2 = uR - aR.cL;
@@ -532,7 +684,7 @@ struct Phys {
     }
     const bool lft = Ss >= R(0);
     const R* cK = lft ? cL_ : cR_;
-    const E* xK = lft ? xL : xR;
+    const XT* xK = lft ? xL : xR;
     const Aux<R>& aK = lft ? aL : aR;
     const R SK = lft ? SL : SR;
     flux<AX>(cK, xK, aK, fo, fox);
@@ -543,17 +695,16 @@ struct Phys {
     // star state U*_K; the flux is F_K + S_K (U*_K - U_K)
     R us[NF];
 #pragma unroll
-    for (int l = 0; l < NMAT - 1; ++l) {
-      us[L::oPHI + l] = R(0);
-      fox[1 + l] = fox[1 + l] + E(SK) * (xK[1 + l] * E(chi) - xK[1 + l]);
-    }
+    for (int l = 0; l < NMAT - 1; ++l) us[L::oPHI + l] = R(0);
+#pragma unroll
+    for (int l = 0; l < NPX; ++l) fox[1 + l] = fox[1 + l] + XT(SK) * (xK[1 + l] * XT(chi) - xK[1 + l]);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) us[L::oARHO + l] = cK[L::oARHO + l] * chi;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) us[L::oMOM + k] = (k == AX) ? rK * chi * Ss : cK[L::oMOM + k] * chi;
     us[L::oE] = R(0);
-    const E Es = E(chi) * (xK[0] + E(rK) * E(Ss) * (E(Ss) - E(uK)) -
-                           E(aK.sd[AX]) * (E(Ss) - E(uK)) / (E(SK) - E(uK)));
+    const XT Es = XT(chi) * (xK[0] + XT(rK) * XT(Ss) * (XT(Ss) - XT(uK)) -
+                             XT(aK.sd[AX]) * (XT(Ss) - XT(uK)) / (XT(SK) - XT(uK)));
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) {
       const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
@@ -571,7 +722,7 @@ struct Phys {
 #pragma unroll
     for (int k = 0; k < NF; ++k)
       if (k != L::oE && (k < L::oPHI || k >= L::oPHI + L::NPHI)) fo[k] = fo[k] + SK * (us[k] - cK[k]);
-    fox[0] = fox[0] + E(SK) * (Es - xK[0]);
+    fox[0] = fox[0] + XT(SK) * (Es - xK[0]);
     uface = uK + SK * (chi - R(1));
     if (DIM == 1) return;
     // shear waves in the star regions
@@ -587,7 +738,7 @@ struct Phys {
     const R rsK = lft ? rsL : rsR;
     const R sgn = lft ? R(1) : R(-1);
     const R SSK = lft ? Ss - csL : Ss + csR;
-    E ess = Es;
+    XT ess = Es;
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
       if (t == AX) continue;
@@ -606,9 +757,9 @@ struct Phys {
           fo[L::oF + k] = fo[L::oF + k] + SSK * (uss_f - us[L::oF + k]);
         }
       }
-      ess += E(sgn) * (E(tss) * E(uss) - E(tauK) * E(uKt)) / E(csK);
+      ess += XT(sgn) * (XT(tss) * XT(uss) - XT(tauK) * XT(uKt)) / XT(csK);
     }
-    fox[0] = fox[0] + E(SSK) * (ess - Es);
+    fox[0] = fox[0] + XT(SSK) * (ess - Es);
   }
 };
 
