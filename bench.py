@@ -49,6 +49,22 @@ def make_case(name: str, n: int):
     return W.WORKLOADS[name](n)
 
 
+def max_over_ranks(value: float, dist=None, device: str = "cuda") -> float:
+    """Largest value over the ranks of the process group (the timing rule:
+    the slowest replica sets the time); the value itself on one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(cells_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job cell-updates/s: every rank advances its own replica."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3)
+
+
 def state_bytes(case, precision: int) -> int:
     """Bytes of one copy of the conserved state: FP64 stores every field in
     8 bytes; FP32-split stores rho E in 8 bytes and every other field, plus
@@ -224,11 +240,8 @@ def run_gpu(args, rank: int, world: int):
     with ClockSampler(local) as clk:
         g, ms, prof, launches = time_device(case, prec, args.steps, args.warmup, stream, flush)
         torch.cuda.synchronize()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * case.ncell * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist)
+    value = aggregate_rate(case.ncell, args.steps, ms, world)
     # dominant kernel and its roofline (algorithmic bytes: one read and one
     # write of the state per launch for the sweeps and the sources)
     peak, peak_kind = read_peaks()
@@ -272,10 +285,7 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     mmfrac.destroy(h)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     h2d = (case.prim.nbytes + (case.phi0.nbytes if case.phi0 is not None else 0)) / args.steps
     d2h = (len(case.materials) + 4) * 8 + out_pinned.numel() * 8 / args.steps
     line = {
