@@ -153,6 +153,22 @@ __device__ __forceinline__ void store_cell(const KArgs& a, long long idx, const 
     U[(long long)L::oE * a.ncell + idx] = S(rhoE);
 }
 
+// In-place store of the deformation tensor (and optionally the history) of
+// one cell: the fields the source step changes.
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void store_sources(const KArgs& a, long long idx,
+                                              const typename P::R* c, bool hist) {
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  S* U = (S*)a.Uout;
+#pragma unroll
+  for (int k = 0; k < L::NFC; ++k) U[(long long)(L::oF + k) * a.ncell + idx] = S(c[L::oF + k]);
+  if (hist) {
+#pragma unroll
+    for (int k = 0; k < 2 * NH; ++k) U[(long long)(L::oH + k) * a.ncell + idx] = S(c[L::oH + k]);
+  }
+}
+
 // ------------------------------------------------------------------ sweep ----
 template <class P, int DIM, int AX> struct Tile;
 // The halo-extended tile (TL + 4) x TW equals the CTA, so each phase is one
@@ -281,24 +297,49 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       R cl[NF], cr[NF];
       XT cxl[NX], cxr[NX];
       Aux<R> xl, xr;
-      bool good;
+      bool good, flat = true;
       {
         R wl[NF], wr[NF];
         XT wxl[NX], wxr[NX];
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
           const R sl = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
+          if (k < L::oX) flat = flat && sl == R(0);
           wl[k] = wc[k] - R(0.5) * sl;
           wr[k] = wc[k] + R(0.5) * sl;
         }
 #pragma unroll
         for (int k = 0; k < NX; ++k) {
           const XT sl = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
+          flat = flat && sl == XT(0);
           wxl[k] = xc[k] - XT(0.5) * sl;
           wxr[k] = xc[k] + XT(0.5) * sl;
         }
-        good = PH::template w2u<AX>(a, wl, wxl, cl, cxl, xl) &&
-               PH::template w2u<AX>(a, wr, wxr, cr, cxr, xr);
+        // Split path: with every slope but those of X zero, both face states
+        // equal the cell state except in X, and the half step changes only X
+        // (X enters no closure): X_L,R += lam/2 (X_L - X_R) u_d.
+        if (P::split && flat) {
+          double eE;
+          load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl, &eE);
+#pragma unroll
+          for (int k = 0; k < NF; ++k) cr[k] = cl[k];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) cxr[k] = cxl[k];
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) {
+            const R inc = R(0.5) * lam * (wl[L::oX + k] - wr[L::oX + k]) * uc[AX];
+            cl[L::oX + k] = wl[L::oX + k] + inc;
+            cr[L::oX + k] = wr[L::oX + k] + inc;
+          }
+          get_aux<P>(wc + NF, xl);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
+          xr = xl;
+          good = false;
+        } else {
+          good = PH::template w2u<AX>(a, wl, wxl, cl, cxl, xl) &&
+                 PH::template w2u<AX>(a, wr, wxr, cr, cxr, xr);
+        }
       }
       if (good) {
         R fl[NF], fr[NF], nc[NF], rowl[3], rowr[3], dF[3];
@@ -327,7 +368,7 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
         good = PH::template u2w<AX>(a, cl, cxl, tmp, tmpx, xl) &&
                PH::template u2w<AX>(a, cr, cxr, tmp, tmpx, xr);
       }
-      if (!good) {
+      if (!good && !(P::split && flat)) {
         // first order: both faces take the cell average
         double eE;
         load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl, &eE);
@@ -500,6 +541,43 @@ __device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, c
   return Y;
 }
 
+// The same yield stress and derivative evaluated wholly in FP32 (split
+// path): the Newton iterate and residual stay FP64, the function values and
+// the step quotient are FP32.
+template <int NMAT>
+__device__ __forceinline__ float yield_mix_f32(const KArgs& a, const float* phi, const float* eps,
+                                               const float* D, float phihat, float inv_dt,
+                                               float dl, float* dY) {
+  float Y = 0.f, dYs = 0.f;
+#pragma unroll
+  for (int l = 0; l < NMAT; ++l) {
+    const MatK& m = a.mat[l];
+    if (m.plasticity != 1) continue;
+    if (m.damage != 0 && D[l] >= float(m.D_crit)) continue;
+    const float psi = m.damage != 0 ? 1.f - D[l] : 1.f;
+    const float e = (eps[l] > 0.f ? eps[l] : 0.f) + dl;
+    float hard = float(m.c1), dhard = 0.f;
+    if (m.c2 != 0.0) {
+      const float en = mpow(e, float(m.n_hard));
+      hard += float(m.c2) * en;
+      if (e > 0.f) dhard = float(m.c2 * m.n_hard) * en / e;
+    }
+    float Rr = 1.f, dR = 0.f;
+    if (m.c3 != 0.0 && dl > 0.f) {
+      const float r = 1.f + float(m.c3) * __logf(dl * inv_dt / float(m.edot0));
+      if (r > 1.f) {
+        Rr = r;
+        dR = float(m.c3) / dl;
+      }
+    }
+    const float wgt = phi[l] * phihat * psi;
+    Y += wgt * hard * Rr;
+    dYs += wgt * (dhard * Rr + hard * dR);
+  }
+  *dY = dYs;
+  return Y;
+}
+
 // Triaxiality-dependent threshold strain; eps_c^(2n), eps_t^(2n) precomputed.
 template <class T>
 __device__ __forceinline__ T eps_thresh(const MatK& m, T Rt) {
@@ -544,6 +622,181 @@ __device__ __forceinline__ T damage_rk4(const MatK& m, T D, T eps0, T deps, T dt
   if (Dn < T(0)) Dn = T(0);
   if (Dn > T(m.D_crit)) Dn = T(m.D_crit);
   return Dn;
+}
+
+// The full source step of one cell: det Fbar = 1, the radial return to the
+// perturbed yield stress (FP64 Newton) and RK4 damage, then the in-place
+// store.  Out of line: in the split path only cells at or above yield come
+// here, so the common elastic path of k_sources stays compact.
+template <class P, int DIM, int NMAT, int NH>
+__device__ __noinline__ void source_full(const KArgs& a, long long cell, typename P::R* c,
+                                         const typename P::X* cx, double eE, const double* phi,
+                                         const double* eps, const double* Dm,
+                                         const typename P::R* rho, const typename P::R* Dr,
+                                         const typename P::R* phir, double phihat, double Gm,
+                                         bool can_yield, double dt, long long step) {
+  typedef typename P::R R;
+  typedef typename P::X XT;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NF = L::NF, NX = PH::NX;
+  (void)NX;
+  // det Fbar = 1
+  R X[9];
+  PH::fullX(c, X);
+  if (P::aform) {
+    // A <- (I + A)/cbrt(det) - I with det - 1 expanded in A
+    const R ed = (X[0] + X[4] + X[8]) +
+                 (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
+                  X[5] * X[7]) +
+                 (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                  X[2] * (X[3] * X[7] - X[4] * X[6]));
+    const R cm1 = mexpm1(mlog1p(ed) / R(3));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = (X[k] - ((k % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
+  } else {
+    const R det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                  X[2] * (X[3] * X[7] - X[4] * X[6]);
+    const R c3 = mcbrt(det);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] /= c3;
+  }
+  // dev(H), |dev(H)|, and (for the return) either eigen-pairs or the
+  // series form of exp((k-1) dev(H)) - I
+  R devH[9], h[3], V[9];
+  R J2 = R(0);
+  bool series = false;
+  if constexpr (P::split) {
+    // series form while the stretch is small (|dev(H)|_F <= 0.05), else
+    // the eigen-pairs are taken below
+    R dH[9], j2;
+    if (hencky_fast(X, dH, j2) && j2 <= R(2.5e-3)) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) devH[q] = dH[q];
+      J2 = j2;
+      series = true;
+    }
+  }
+  if (!series) {
+    if (!hencky<P::aform>(X, devH, h, V)) {
+      report(a.err, ST_ENONFINITE, cell, step);
+      return;
+    }
+    J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+  }
+  double dl = 0.0;
+  if (can_yield && Gm > 0.0) {
+    const double J = series ? sqrt(double(J2))
+                            : sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
+                                   double(h[2]) * double(h[2]));
+    const double str = sqrt(6.0) * Gm * J;
+    float phf[NMAT], epf[NMAT], Dmf[NMAT];
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      phf[l] = float(phi[l]);
+      epf[l] = float(eps[l]);
+      Dmf[l] = float(Dm[l]);
+    }
+    const float inv_dt = float(1.0 / dt);
+    float dYf0;
+    const double Y0 =
+        P::split ? double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat), inv_dt, 0.f, &dYf0))
+                 : yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
+    if (str > Y0) {
+      // stopping rule at the accuracy of the yield-stress evaluation
+      const double gtol = P::split ? 1e-6 : 8.0 * 2.220446049250313e-16;
+      const double xtol = P::split ? 1e-7 : 4.0 * 2.220446049250313e-16;
+      const double b0 = str / (3.0 * Gm);
+      double lo = 0.0, hi = b0, x = (str - Y0) / (3.0 * Gm);
+      bool conv = false;
+      for (int it = 0; it < 200; ++it) {
+        double dY, Y;
+        if (P::split) {
+          float dYf;
+          Y = double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat), inv_dt, float(x), &dYf));
+          dY = double(dYf);
+        } else {
+          Y = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, x, &dY);
+        }
+        const double g = str - 3.0 * Gm * x - Y;
+        if (fabs(g) <= gtol * str) {
+          conv = true;
+          break;
+        }
+        if (g > 0.0) lo = x; else hi = x;
+        double nx = P::split ? x - double(float(g) / float(-3.0 * Gm - dY))
+                             : x - g / (-3.0 * Gm - dY);
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (fabs(nx - x) <= xtol * b0) {
+          x = nx;
+          conv = true;
+          break;
+        }
+        x = nx;
+      }
+      if (!conv) {
+        report(a.err, ST_ENOCONV, cell, step);
+        return;
+      }
+      dl = x;
+      const R k = R((str - 3.0 * Gm * dl) / str);
+      // Fbar <- S Fbar, S = exp((k-1) dev(H)) (the rotation is kept); in A
+      // form A <- (S - I)(I + A) + A
+      R Sm[9], Xn[9];
+      if (series) {
+        R Y[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Y[q] = (k - R(1)) * devH[q];
+        expm1_series(Y, Sm);
+      } else {
+        R m1[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            Sm[3 * i + j] = V[3 * i + 0] * m1[0] * V[3 * j + 0] + V[3 * i + 1] * m1[1] * V[3 * j + 1] +
+                            V[3 * i + 2] * m1[2] * V[3 * j + 2];
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const R sx = Sm[3 * i + 0] * X[0 + j] + Sm[3 * i + 1] * X[3 + j] + Sm[3 * i + 2] * X[6 + j];
+          Xn[3 * i + j] = P::aform ? Sm[3 * i + j] + sx + X[3 * i + j] : sx;
+        }
+#pragma unroll
+      for (int k2 = 0; k2 < 9; ++k2) X[k2] = Xn[k2];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = X[FC<DIM>::idx(k)];
+  if (dl > 0.0) {
+    R w2[NF];
+    XT wx2[NX];
+    Aux<R> as;
+    if (!PH::template u2w<0>(a, c, cx, w2, wx2, as, &eE)) {
+      report(a.err, ST_ENONFINITE, cell, step);
+      return;
+    }
+    typename PH::Mix mx;
+    PH::mixture(a, phir, rho, Dr, X, mx);
+    const double seq = sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2));
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+#pragma unroll
+      for (int hh = 0; hh < NH; ++hh)
+        if (a.hslot[l] == hh) {
+          const R arho = c[L::oARHO + l];
+          const double Dn = double(damage_rk4<R>(a.mat[l], R(Dm[l]), R(eps[l]), R(dl), R(dt),
+                                                 R(wx2[0]), R(seq), rho[l]));
+          c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
+          c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
+        }
+    }
+  }
+  store_sources<P, DIM, NMAT, NH>(a, cell, c, dl > 0.0);
 }
 
 // Per-cell sources after the sweeps (in place): renormalise det Fbar = 1,
@@ -611,144 +864,43 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
     }
     // split path: G_mix of the recovery (G does not depend on J2)
     if constexpr (P::split) Gm = double(mx0.Gm);
-    // det Fbar = 1
-    R X[9];
-    PH::fullX(c, X);
-    if (P::aform) {
-      // A <- (I + A)/cbrt(det) - I with det - 1 expanded in A
-      const R ed = (X[0] + X[4] + X[8]) +
-                   (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
-                    X[5] * X[7]) +
-                   (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                    X[2] * (X[3] * X[7] - X[4] * X[6]));
-      const R cm1 = mexpm1(mlog1p(ed) / R(3));
-#pragma unroll
-      for (int k = 0; k < 9; ++k) X[k] = (X[k] - ((k % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
-    } else {
-      const R det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                    X[2] * (X[3] * X[7] - X[4] * X[6]);
-      const R c3 = mcbrt(det);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) X[k] /= c3;
-    }
-    // dev(H), |dev(H)|, and (for the return) either eigen-pairs or the
-    // series form of exp((k-1) dev(H)) - I
-    R devH[9], h[3], V[9];
-    R J2 = R(0);
-    bool series = false;
     if constexpr (P::split) {
-      // the recovery's dev(H): scaling Fbar by det^(-1/3) leaves dev(H)
-      // unchanged; the series form of the return applies while the stretch
-      // is small (|dev(H)|_F <= 0.05), else the eigen-pairs are taken below
-      if (mx0.J2 <= R(2.5e-3)) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) devH[q] = mx0.devH[q];
-        J2 = mx0.J2;
-        series = true;
-      }
-    }
-    if (!series) {
-      if (!hencky<P::aform>(X, devH, h, V)) {
-        report(a.err, ST_ENONFINITE, cell, step);
-        continue;
-      }
-      J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
-    }
-    double dl = 0.0;
-    if (can_yield && Gm > 0.0) {
-      const double J = series ? sqrt(double(J2))
-                              : sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
-                                     double(h[2]) * double(h[2]));
-      const double str = sqrt(6.0) * Gm * J;
-      const double Y0 = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
-      if (str > Y0) {
-        // stopping rule at the accuracy of the yield-stress evaluation
-        const double gtol = P::split ? 1e-6 : 8.0 * 2.220446049250313e-16;
-        const double xtol = P::split ? 1e-7 : 4.0 * 2.220446049250313e-16;
-        const double b0 = str / (3.0 * Gm);
-        double lo = 0.0, hi = b0, x = (str - Y0) / (3.0 * Gm);
-        bool conv = false;
-        for (int it = 0; it < 200; ++it) {
-          double dY;
-          const double Y = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, x, &dY);
-          const double g = str - 3.0 * Gm * x - Y;
-          if (fabs(g) <= gtol * str) {
-            conv = true;
-            break;
-          }
-          if (g > 0.0) lo = x; else hi = x;
-          double nx = x - g / (-3.0 * Gm - dY);
-          if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
-          if (fabs(nx - x) <= xtol * b0) {
-            x = nx;
-            conv = true;
-            break;
-          }
-          x = nx;
-        }
-        if (!conv) {
-          report(a.err, ST_ENOCONV, cell, step);
-          continue;
-        }
-        dl = x;
-        const R k = R((str - 3.0 * Gm * dl) / str);
-        // Fbar <- S Fbar, S = exp((k-1) dev(H)) (the rotation is kept); in A
-        // form A <- (S - I)(I + A) + A
-        R Sm[9], Xn[9];
-        if (series) {
-          R Y[9];
-#pragma unroll
-          for (int q = 0; q < 9; ++q) Y[q] = (k - R(1)) * devH[q];
-          expm1_series(Y, Sm);
-        } else {
-          R m1[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-              Sm[3 * i + j] = V[3 * i + 0] * m1[0] * V[3 * j + 0] + V[3 * i + 1] * m1[1] * V[3 * j + 1] +
-                              V[3 * i + 2] * m1[2] * V[3 * j + 2];
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            const R sx = Sm[3 * i + 0] * X[0 + j] + Sm[3 * i + 1] * X[3 + j] + Sm[3 * i + 2] * X[6 + j];
-            Xn[3 * i + j] = P::aform ? Sm[3 * i + j] + sx + X[3 * i + j] : sx;
-          }
-#pragma unroll
-        for (int k2 = 0; k2 < 9; ++k2) X[k2] = Xn[k2];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = X[FC<DIM>::idx(k)];
-    if (dl > 0.0) {
-      R w2[NF];
-      XT wx2[NX];
-      Aux<R> as;
-      if (!PH::template u2w<0>(a, c, cx, w2, wx2, as, &eE)) {
-        report(a.err, ST_ENONFINITE, cell, step);
-        continue;
-      }
-      typename PH::Mix mx;
-      PH::mixture(a, phir, rho, Dr, X, mx);
-      const double seq = sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2));
+      // FP32 yield test against the rate-free yield stress; cells clearly
+      // inside the yield surface only get det Fbar = 1 (and nothing is
+      // written when that leaves Fbar as it is)
+      R y0 = R(0);
 #pragma unroll
       for (int l = 0; l < NMAT; ++l) {
+        const MatK& m = a.mat[l];
+        if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_crit))) continue;
+        const R e = eps[l] > 0.0 ? R(eps[l]) : R(0);
+        R hard = R(m.c1);
+        if (m.c2 != 0.0) hard += R(m.c2) * mpow(e, R(m.n_hard));
+        y0 += phir[l] * R(phihat) * (m.damage != 0 ? R(1) - Dr[l] : R(1)) * hard;
+      }
+      const R strf = R(2.449489743f) * mx0.Gm * msqrt(mx0.J2);
+      if (!can_yield || !(mx0.Gm > R(0)) || !(strf > y0 * R(0.9999))) {
+        R X[9];
+        PH::fullX(c, X);
+        const R ed = (X[0] + X[4] + X[8]) +
+                     (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
+                      X[5] * X[7]) +
+                     (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                      X[2] * (X[3] * X[7] - X[4] * X[6]));
+        if (ed != R(0)) {
+          const R cm1 = mexpm1(mlog1p(ed) / R(3));
 #pragma unroll
-        for (int hh = 0; hh < NH; ++hh)
-          if (a.hslot[l] == hh) {
-            const R arho = c[L::oARHO + l];
-            const double Dn = double(damage_rk4<R>(a.mat[l], R(Dm[l]), R(eps[l]), R(dl), R(dt),
-                                                   R(wx2[0]), R(seq), rho[l]));
-            c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
-            c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
+          for (int k = 0; k < L::NFC; ++k) {
+            const int q = FC<DIM>::idx(k);
+            c[L::oF + k] = (X[q] - ((q % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
           }
+          store_sources<P, DIM, NMAT, NH>(a, cell, c, false);
+        }
+        continue;
       }
     }
-    store_cell<P, DIM, NMAT, NH>(a, cell, c, cx, eE);
+    source_full<P, DIM, NMAT, NH>(a, cell, c, cx, eE, phi, eps, Dm, rho, Dr, phir, phihat, Gm,
+                                  can_yield, dt, step);
   }
 }
 
@@ -768,8 +920,7 @@ __global__ void __launch_bounds__(256) k_cfl(KArgs a) {
     double eE;
     load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
     Aux<R> ax;
-    typename PH::Mix mx0;
-    if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {
+    if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE)) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }

@@ -18,7 +18,8 @@ import numpy as np
 from . import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmmfrac.so")
+# MMFRAC_LIB selects another build of the library (e.g. a variant under test)
+LIB_PATH = os.environ.get("MMFRAC_LIB") or os.path.join(HERE, "libmmfrac.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
 MM_ENONFINITE, MM_ENOCONV, MM_EDT, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7, -8
