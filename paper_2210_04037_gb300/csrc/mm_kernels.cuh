@@ -294,106 +294,141 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       R uc[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) uc[k] = k < DIM ? wc[L::oMOM + k] : R(0);
-      R cl[NF], cr[NF];
-      XT cxl[NX], cxr[NX];
-      Aux<R> xl, xr;
-      bool good, flat = true;
-      {
-        R wl[NF], wr[NF];
-        XT wxl[NX], wxr[NX];
+      R sl[NF];
+      XT slx[NX];
+      bool flat = true;
 #pragma unroll
-        for (int k = 0; k < NF; ++k) {
-          const R sl = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
-          if (k < L::oX) flat = flat && sl == R(0);
-          wl[k] = wc[k] - R(0.5) * sl;
-          wr[k] = wc[k] + R(0.5) * sl;
-        }
+      for (int k = 0; k < NF; ++k) {
+        sl[k] = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
+        if (k < L::oX) flat = flat && sl[k] == R(0);
+      }
 #pragma unroll
-        for (int k = 0; k < NX; ++k) {
-          const XT sl = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
-          flat = flat && sl == XT(0);
-          wxl[k] = xc[k] - XT(0.5) * sl;
-          wxr[k] = xc[k] + XT(0.5) * sl;
-        }
+      for (int k = 0; k < NX; ++k) {
+        slx[k] = van_leer(xc[k] - xm[k], xp[k] - xc[k]);
+        flat = flat && slx[k] == XT(0);
+      }
+      // face states: slot 2 it is the left face (w - slope/2), 2 it + 1 the right
+      R* const q0 = r2 + (2 * it) * C2;
+      XT* const qx0 = x2 + (2 * it) * NX;
+      bool done = false;
+      if (P::split && flat) {
         // Split path: with every slope but those of X zero, both face states
         // equal the cell state except in X, and the half step changes only X
         // (X enters no closure): X_L,R += lam/2 (X_L - X_R) u_d.
-        if (P::split && flat) {
-          double eE;
-          load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl, &eE);
+        R c[NF];
+        XT cx[NX];
+        double eE;
+        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
+        Aux<R> xa;
+        get_aux<P>(wc + NF, xa);
 #pragma unroll
-          for (int k = 0; k < NF; ++k) cr[k] = cl[k];
+        for (int k = 0; k < 3; ++k) xa.u[k] = uc[k];
 #pragma unroll
-          for (int k = 0; k < NX; ++k) cxr[k] = cxl[k];
+        for (int s = 0; s < 2; ++s) {
+          R* q = q0 + s * C2;
+#pragma unroll
+          for (int k = 0; k < NF; ++k) q[k] = c[k];
 #pragma unroll
           for (int k = 0; k < DIM; ++k) {
-            const R inc = R(0.5) * lam * (wl[L::oX + k] - wr[L::oX + k]) * uc[AX];
-            cl[L::oX + k] = wl[L::oX + k] + inc;
-            cr[L::oX + k] = wr[L::oX + k] + inc;
+            const R inc = R(0.5) * lam * ((wc[L::oX + k] - R(0.5) * sl[L::oX + k]) -
+                                          (wc[L::oX + k] + R(0.5) * sl[L::oX + k])) * uc[AX];
+            q[L::oX + k] = (s == 0 ? wc[L::oX + k] - R(0.5) * sl[L::oX + k]
+                                   : wc[L::oX + k] + R(0.5) * sl[L::oX + k]) + inc;
           }
-          get_aux<P>(wc + NF, xl);
+          put_aux<P>(q + NF, xa);
 #pragma unroll
-          for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
-          xr = xl;
-          good = false;
-        } else {
-          good = PH::template w2u<AX>(a, wl, wxl, cl, cxl, xl) &&
-                 PH::template w2u<AX>(a, wr, wxr, cr, cxr, xr);
+          for (int k = 0; k < NX; ++k) qx0[s * NX + k] = cx[k];
         }
+        done = true;
+      } else {
+        // MUSCL-Hancock: one pass per face state (one code site for the
+        // state conversions), accumulating F_L - F_R and the jumps the
+        // non-conservative terms need; the half-step states go to shared memory.
+        bool good = true;
+        R dfl[NF], dF[3], du = R(0);
+        XT dfx[NX];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) dfl[k] = R(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) dfx[k] = XT(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dF[j] = R(0);
+#pragma unroll 1
+        for (int s = 0; s < 2; ++s) {
+          const R hs = s == 0 ? R(-0.5) : R(0.5);
+          const R sg = s == 0 ? R(1) : R(-1);
+          R wv[NF], cs[NF], f[NF], row[3];
+          XT wxv[NX], cxs[NX], fx[NX];
+#pragma unroll
+          for (int k = 0; k < NF; ++k) wv[k] = wc[k] + hs * sl[k];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) wxv[k] = xc[k] + XT(hs) * slx[k];
+          Aux<R> xs;
+          if (!PH::template w2u<AX>(a, wv, wxv, cs, cxs, xs)) {
+            good = false;
+            break;
+          }
+          PH::template flux<AX>(cs, cxs, xs, f, fx);
+          PH::template frow<AX>(cs, row);
+#pragma unroll
+          for (int k = 0; k < NF; ++k) dfl[k] += sg * f[k];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) dfx[k] += XT(sg) * fx[k];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dF[j] -= sg * row[j];
+          du -= sg * xs.u[AX];
+          R* q = q0 + s * C2;
+#pragma unroll
+          for (int k = 0; k < NF; ++k) q[k] = cs[k];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) qx0[s * NX + k] = cxs[k];
+        }
+        if (good) {
+          R nc[NF];
+          XT ncx[NX];
+          PH::template noncons<AX>(wc, xc, uc, du, dF, nc, ncx);
+#pragma unroll 1
+          for (int s = 0; s < 2; ++s) {
+            R* q = q0 + s * C2;
+            XT* qx = qx0 + s * NX;
+            R cs[NF], tmp[NF];
+            XT cxs[NX], tmpx[NX];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) cs[k] = q[k] + R(0.5) * lam * (dfl[k] + nc[k]);
+#pragma unroll
+            for (int k = 0; k < NX; ++k) cxs[k] = qx[k] + XT(0.5) * XT(lam) * (dfx[k] + ncx[k]);
+            Aux<R> xs;
+            if (!PH::template u2w<AX>(a, cs, cxs, tmp, tmpx, xs)) {
+              good = false;
+              break;
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) q[k] = cs[k];
+#pragma unroll
+            for (int k = 0; k < NX; ++k) qx[k] = cxs[k];
+            put_aux<P>(q + NF, xs);
+          }
+        }
+        done = good;
       }
-      if (good) {
-        R fl[NF], fr[NF], nc[NF], rowl[3], rowr[3], dF[3];
-        XT fxl[NX], fxr[NX], ncx[NX];
-        PH::template flux<AX>(cl, cxl, xl, fl, fxl);
-        PH::template flux<AX>(cr, cxr, xr, fr, fxr);
-        PH::template frow<AX>(cl, rowl);
-        PH::template frow<AX>(cr, rowr);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dF[j] = rowr[j] - rowl[j];
-        PH::template noncons<AX>(wc, xc, uc, xr.u[AX] - xl.u[AX], dF, nc, ncx);
-#pragma unroll
-        for (int k = 0; k < NF; ++k) {
-          const R inc = R(0.5) * lam * ((fl[k] - fr[k]) + nc[k]);
-          cl[k] += inc;
-          cr[k] += inc;
-        }
-#pragma unroll
-        for (int k = 0; k < NX; ++k) {
-          const XT inc = XT(0.5) * XT(lam) * ((fxl[k] - fxr[k]) + ncx[k]);
-          cxl[k] += inc;
-          cxr[k] += inc;
-        }
-        R tmp[NF];
-        XT tmpx[NX];
-        good = PH::template u2w<AX>(a, cl, cxl, tmp, tmpx, xl) &&
-               PH::template u2w<AX>(a, cr, cxr, tmp, tmpx, xr);
-      }
-      if (!good && !(P::split && flat)) {
+      if (!done) {
         // first order: both faces take the cell average
+        R c[NF];
+        XT cx[NX];
         double eE;
-        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, cl, cxl, &eE);
+        load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
+        Aux<R> xa;
+        get_aux<P>(wc + NF, xa);
 #pragma unroll
-        for (int k = 0; k < NF; ++k) cr[k] = cl[k];
+        for (int k = 0; k < 3; ++k) xa.u[k] = uc[k];
 #pragma unroll
-        for (int k = 0; k < NX; ++k) cxr[k] = cxl[k];
-        get_aux<P>(wc + NF, xl);
+        for (int s = 0; s < 2; ++s) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) xl.u[k] = uc[k];
-        xr = xl;
-      }
-      R* ql = r2 + (2 * it) * C2;
-      R* qr = r2 + (2 * it + 1) * C2;
+          for (int k = 0; k < NF; ++k) q0[s * C2 + k] = c[k];
+          put_aux<P>(q0 + s * C2 + NF, xa);
 #pragma unroll
-      for (int k = 0; k < NF; ++k) {
-        ql[k] = cl[k];
-        qr[k] = cr[k];
-      }
-      put_aux<P>(ql + NF, xl);
-      put_aux<P>(qr + NF, xr);
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        x2[(2 * it) * NX + k] = cxl[k];
-        x2[(2 * it + 1) * NX + k] = cxr[k];
+          for (int k = 0; k < NX; ++k) qx0[s * NX + k] = cx[k];
+        }
       }
       okv = 1;
     }

@@ -674,22 +674,21 @@ struct Phys {
     const R rL = aL.rho, rR = aR.rho;
     const R Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
                  (rL * (SL - uL) - rR * (SR - uR));
-    if (SL >= R(0) || SR <= R(0)) {
-      const bool lft = SL >= R(0);
-      const Aux<R>& aK = lft ? aL : aR;
-      flux<AX>(lft ? cL_ : cR_, lft ? xL : xR, aK, fo, fox);
-      uface = aK.u[AX];
-      frow<AX>(lft ? cL_ : cR_, frowo);
-      return;
-    }
-    const bool lft = Ss >= R(0);
+    // one upwind state: supersonic -> the state on the upwind side of both
+    // waves, subsonic -> the state on the side of the contact holding the face
+    const bool sup = SL >= R(0) || SR <= R(0);
+    const bool lft = sup ? SL >= R(0) : Ss >= R(0);
     const R* cK = lft ? cL_ : cR_;
     const XT* xK = lft ? xL : xR;
     const Aux<R>& aK = lft ? aL : aR;
-    const R SK = lft ? SL : SR;
     flux<AX>(cK, xK, aK, fo, fox);
     frow<AX>(cK, frowo);
     const R uK = aK.u[AX];
+    if (sup) {
+      uface = uK;
+      return;
+    }
+    const R SK = lft ? SL : SR;
     const R chi = (SK - uK) / (SK - Ss);
     const R rK = aK.rho;
     // star state U*_K; the flux is F_K + S_K (U*_K - U_K)
