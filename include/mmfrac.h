@@ -87,7 +87,8 @@ typedef struct {
  * (host, copied).  phi0 = perturbation lattice of phi0_n points per axis
  * (x fastest) with origin phi0_lo and spacing phi0_h (host, copied), or NULL
  * for phi = 1 everywhere (Sec. 3.2.2: phi(x) = phi0(X(x)), multilinear,
- * 1 outside the lattice). */
+ * 1 outside the lattice).  At least 2 points per axis and at most 2^31 - 1
+ * points in all (else MM_EINVAL). */
 typedef struct {
   const double* prim;
   const float* phi0;

@@ -317,9 +317,14 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   const int nF = g->dim == 1 ? 3 : (g->dim == 2 ? 5 : 9);
   const int nfield = (g->nmat - 1) + g->nmat + g->dim + 1 + nF + 2 * nhist + g->dim;
   if (init->phi0) {
-    for (int k = 0; k < g->dim; ++k)
+    long long np = 1;
+    for (int k = 0; k < g->dim; ++k) {
       if (init->phi0_n[k] < 2 || !(init->phi0_h[k] > 0))
         return fail(MM_EINVAL, "perturbation lattice needs >= 2 points and h > 0 per axis");
+      if (init->phi0_n[k] > 0x7fffffffLL / np)
+        return fail(MM_EINVAL, "perturbation lattice exceeds 2^31 - 1 points");
+      np *= init->phi0_n[k];
+    }
   }
   free_state(g);
   g->nhist = nhist;
@@ -347,8 +352,41 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   a.nhist = nhist;
   a.nfield = nfield;
   for (int l = 0; l < MM_MAXMAT; ++l) {
-    a.mat[l] = mk[l];
+    const MatK& k = mk[l];
+    a.mat[l] = k;
     a.hslot[l] = hslot[l];
+    MatKf& f = a.matf[l];
+    f.eos = k.eos;
+    f.plasticity = k.plasticity;
+    f.damage = k.damage;
+    f.alpha_one = k.alpha == 1.0;
+    f.rho0 = float(k.rho0);
+    f.K0 = float(k.K0);
+    f.G0 = float(k.G0);
+    f.alpha = float(k.alpha);
+    f.beta = float(k.beta);
+    f.Gamma0 = float(k.Gamma0);
+    f.gamma_gas = float(k.gamma_gas);
+    f.c1 = float(k.c1);
+    f.c2 = float(k.c2);
+    f.c3 = float(k.c3);
+    f.n_hard = float(k.n_hard);
+    f.edot0 = float(k.edot0);
+    f.D_crit = float(k.D_crit);
+    f.eps_t = float(k.eps_t);
+    f.eps_c = float(k.eps_c);
+    f.alpha_D = float(k.alpha_D);
+    f.poisson = float(k.poisson);
+    f.Ddot0 = float(k.Ddot0);
+    f.xi = float(k.xi);
+    f.Gamma = float(k.Gamma);
+    f.bon_k = float(k.bon_k);
+    f.bon_ec2n = float(k.bon_ec2n);
+    f.bon_et2n = float(k.bon_et2n);
+    f.inv_rho0 = k.rho0 > 0 ? float(1.0 / k.rho0) : 0.f;
+    f.K0_2a2 = k.alpha > 0 ? float(k.K0 / (2.0 * k.alpha * k.alpha)) : 0.f;
+    f.K0_arho0 = k.alpha > 0 && k.rho0 > 0 ? float(k.K0 / (k.alpha * k.rho0)) : 0.f;
+    f.c2n = float(k.c2 * k.n_hard);
   }
   a.prim = g->prim;
   a.phi0 = nullptr;
@@ -358,6 +396,8 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
       a.pn[k] = (int)init->phi0_n[k];
       a.plo[k] = init->phi0_lo[k];
       a.ph[k] = init->phi0_h[k];
+      a.plof[k] = float(init->phi0_lo[k]);
+      a.phf[k] = float(init->phi0_h[k]);
       np *= init->phi0_n[k];
     }
     if (cudaMalloc(&g->phi0, sizeof(float) * np) != cudaSuccess) {

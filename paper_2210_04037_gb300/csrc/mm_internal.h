@@ -21,6 +21,22 @@ struct MatK {
   double bon_k, bon_ec2n, bon_et2n;
 };
 
+// The same constants in FP32 for the FP32-split kernels, which read them as
+// operands straight from the parameter bank (a double constant would cost a
+// conversion on the FP64 pipe at every use), plus ratios the FP32 closure
+// uses in place of divisions.
+struct MatKf {
+  int eos, plasticity, damage, alpha_one;  // alpha_one: alpha == 1
+  float rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
+  float c1, c2, c3, n_hard, edot0;
+  float D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+  float xi, Gamma, bon_k, bon_ec2n, bon_et2n;
+  float inv_rho0;  // 1 / rho0
+  float K0_2a2;    // K0 / (2 alpha^2)
+  float K0_arho0;  // K0 / (alpha rho0)
+  float c2n;       // c2 n_hard
+};
+
 // First failure seen on the device (sticky until the host clears it).
 struct DevErr {
   int code;       // 0 or an mm_status
@@ -45,6 +61,7 @@ struct KArgs {
   int bc[3][2];
   int hslot[MM_MAXMAT];
   MatK mat[MM_MAXMAT];
+  MatKf matf[MM_MAXMAT];
   const void* Uin;     // conserved fields [nfield][ncell] (double or float)
   void* Uout;
   const double* Ein;   // rho E [ncell] (FP32-split storage only)
@@ -52,6 +69,7 @@ struct KArgs {
   const float* phi0;
   int pn[3];
   double plo[3], ph[3];
+  float plof[3], phf[3];  // plo, ph in FP32
   DevInfo* info;
   DevErr* err;
   double cfl, dxmin;

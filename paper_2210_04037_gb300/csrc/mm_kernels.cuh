@@ -499,6 +499,8 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       for (int k = 1; k < NX; ++k)
         cx[k] = cx[k] + XT(lam) * ((x3[fl * NX + k] - x3[fr * NX + k]) + ncx[k]);
       // total energy updated in FP64 (the stored state)
+      // (the face fluxes differenced in FP64 telescope exactly over the
+      // cells, which keeps the total energy conserved to FP64 rounding)
       eE = eE + double(lam) * ((double(x3[fl * NX]) - double(x3[fr * NX])) + double(ncx[0]));
       store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
     }
@@ -511,13 +513,16 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
 template <int DIM, class T>
 __device__ __forceinline__ T lookup(const KArgs& a, const T X[3]) {
   if (!a.phi0) return T(1);
-  long long i0[3] = {0, 0, 0};
+  // lattice of at most 2^31 - 1 points (checked on the host): int indices
+  int i0[3] = {0, 0, 0};
   T w[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    const T s = (X[k] - T(a.plo[k])) / T(a.ph[k]);
+    const T lo = sizeof(T) == 4 ? T(a.plof[k]) : T(a.plo[k]);
+    const T h = sizeof(T) == 4 ? T(a.phf[k]) : T(a.ph[k]);
+    const T s = (X[k] - lo) / h;
     if (!(s >= T(0)) || !(s <= T(a.pn[k] - 1))) return T(1);
-    long long i = (long long)floor(s);
+    int i = int(floor(s));
     if (i > a.pn[k] - 2) i = a.pn[k] - 2;
     i0[k] = i;
     w[k] = s - T(i);
@@ -526,7 +531,7 @@ __device__ __forceinline__ T lookup(const KArgs& a, const T X[3]) {
 #pragma unroll
   for (int c = 0; c < (1 << DIM); ++c) {
     T wt = T(1);
-    long long idx = 0, str = 1;
+    int idx = 0, str = 1;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       const int bit = (c >> k) & 1;
@@ -586,23 +591,23 @@ __device__ __forceinline__ float yield_mix_f32(const KArgs& a, const float* phi,
   float Y = 0.f, dYs = 0.f;
 #pragma unroll
   for (int l = 0; l < NMAT; ++l) {
-    const MatK& m = a.mat[l];
+    const MatKf& m = a.matf[l];
     if (m.plasticity != 1) continue;
-    if (m.damage != 0 && D[l] >= float(m.D_crit)) continue;
+    if (m.damage != 0 && D[l] >= m.D_crit) continue;
     const float psi = m.damage != 0 ? 1.f - D[l] : 1.f;
     const float e = (eps[l] > 0.f ? eps[l] : 0.f) + dl;
-    float hard = float(m.c1), dhard = 0.f;
-    if (m.c2 != 0.0) {
-      const float en = mpow(e, float(m.n_hard));
-      hard += float(m.c2) * en;
-      if (e > 0.f) dhard = float(m.c2 * m.n_hard) * en / e;
+    float hard = m.c1, dhard = 0.f;
+    if (m.c2 != 0.f) {
+      const float en = mpow(e, m.n_hard);
+      hard += m.c2 * en;
+      if (e > 0.f) dhard = m.c2n * en / e;
     }
     float Rr = 1.f, dR = 0.f;
-    if (m.c3 != 0.0 && dl > 0.f) {
-      const float r = 1.f + float(m.c3) * __logf(dl * inv_dt / float(m.edot0));
+    if (m.c3 != 0.f && dl > 0.f) {
+      const float r = 1.f + m.c3 * __logf(dl * inv_dt / m.edot0);
       if (r > 1.f) {
         Rr = r;
-        dR = float(m.c3) / dl;
+        dR = m.c3 / dl;
       }
     }
     const float wgt = phi[l] * phihat * psi;
@@ -614,16 +619,16 @@ __device__ __forceinline__ float yield_mix_f32(const KArgs& a, const float* phi,
 }
 
 // Triaxiality-dependent threshold strain; eps_c^(2n), eps_t^(2n) precomputed.
-template <class T>
-__device__ __forceinline__ T eps_thresh(const MatK& m, T Rt) {
+template <class T, class M>
+__device__ __forceinline__ T eps_thresh(const M& m, T Rt) {
   const T n = T(m.n_hard), et = T(m.eps_t), ec = T(m.eps_c);
   const T num = T(m.bon_ec2n) - T(m.bon_et2n);
   const T den = mpow(ec, T(2) * n / Rt) - mpow(et, T(2) * n / Rt);
   return mpow(et, T(1) / Rt) / mpow(Rt, T(1) / n) * mpow(num / den, T(1) / (T(2) * n));
 }
 
-template <class T>
-__device__ __forceinline__ T dmg_rate(const MatK& m, T D, T eps, T ed, T Rt, T th, bool tension) {
+template <class T, class M>
+__device__ __forceinline__ T dmg_rate(const M& m, T D, T eps, T ed, T Rt, T th, bool tension) {
   if (m.damage == 2) return T(m.Ddot0) * (T(1) - D) * ed;
   if (!tension || !(eps > th)) return T(0);
   if (D >= T(m.D_crit)) return T(0);
@@ -634,8 +639,8 @@ __device__ __forceinline__ T dmg_rate(const MatK& m, T D, T eps, T ed, T Rt, T t
 // RK4 over the step of the damage rate with eps_p(t) linear in t (the
 // plastic increment deps over dt), p and sigma_eq held at the returned
 // state; clamped to [0, D_crit].  Bonora: zero unless p < 0 (checked first).
-template <class T>
-__device__ __forceinline__ T damage_rk4(const MatK& m, T D, T eps0, T deps, T dt, T p, T seq,
+template <class T, class M>
+__device__ __forceinline__ T damage_rk4(const M& m, T D, T eps0, T deps, T dt, T p, T seq,
                                         T rho) {
   if (m.damage == 0 || !(deps > T(0))) return D;
   T Rt = T(1), th = T(0);
@@ -646,13 +651,13 @@ __device__ __forceinline__ T damage_rk4(const MatK& m, T D, T eps0, T deps, T dt
     const T x = p / seq;
     Rt = T(2) / T(3) * (T(1) + T(m.poisson)) +
          T(3) * (T(1) - T(2) * T(m.poisson)) * (T(m.rho0) / rho) * (x * x);
-    th = eps_thresh<T>(m, Rt);
+    th = eps_thresh<T, M>(m, Rt);
   }
   const T ed = deps / dt;
-  const T k1 = dmg_rate<T>(m, D, eps0, ed, Rt, th, tension);
-  const T k2 = dmg_rate<T>(m, D + T(0.5) * dt * k1, eps0 + T(0.5) * deps, ed, Rt, th, tension);
-  const T k3 = dmg_rate<T>(m, D + T(0.5) * dt * k2, eps0 + T(0.5) * deps, ed, Rt, th, tension);
-  const T k4 = dmg_rate<T>(m, D + dt * k3, eps0 + deps, ed, Rt, th, tension);
+  const T k1 = dmg_rate<T, M>(m, D, eps0, ed, Rt, th, tension);
+  const T k2 = dmg_rate<T, M>(m, D + T(0.5) * dt * k1, eps0 + T(0.5) * deps, ed, Rt, th, tension);
+  const T k3 = dmg_rate<T, M>(m, D + T(0.5) * dt * k2, eps0 + T(0.5) * deps, ed, Rt, th, tension);
+  const T k4 = dmg_rate<T, M>(m, D + dt * k3, eps0 + deps, ed, Rt, th, tension);
   T Dn = D + dt / T(6) * (k1 + T(2) * k2 + T(2) * k3 + k4);
   if (Dn < T(0)) Dn = T(0);
   if (Dn > T(m.D_crit)) Dn = T(m.D_crit);
@@ -665,10 +670,10 @@ __device__ __forceinline__ T damage_rk4(const MatK& m, T D, T eps0, T deps, T dt
 // here, so the common elastic path of k_sources stays compact.
 template <class P, int DIM, int NMAT, int NH>
 __device__ __noinline__ void source_full(const KArgs& a, long long cell, typename P::R* c,
-                                         const typename P::X* cx, double eE, const double* phi,
-                                         const double* eps, const double* Dm,
+                                         const typename P::X* cx, double eE,
                                          const typename P::R* rho, const typename P::R* Dr,
-                                         const typename P::R* phir, double phihat, double Gm,
+                                         const typename P::R* phir, const typename P::R* Er,
+                                         typename P::R phihat_r, typename P::R Gm_r,
                                          bool can_yield, double dt, long long step) {
   typedef typename P::R R;
   typedef typename P::X XT;
@@ -676,6 +681,15 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
   typedef Lay<DIM, NMAT, NH> L;
   constexpr int NF = L::NF, NX = PH::NX;
   (void)NX;
+  // the return and the damage take the fractions, strains and damage in FP64
+  double phi[NMAT], eps[NMAT], Dm[NMAT];
+#pragma unroll
+  for (int l = 0; l < NMAT; ++l) {
+    phi[l] = double(phir[l]);
+    eps[l] = double(Er[l]);
+    Dm[l] = double(Dr[l]);
+  }
+  const double phihat = double(phihat_r), Gm = double(Gm_r);
   // det Fbar = 1
   R X[9];
   PH::fullX(c, X);
@@ -824,7 +838,7 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
       for (int hh = 0; hh < NH; ++hh)
         if (a.hslot[l] == hh) {
           const R arho = c[L::oARHO + l];
-          const double Dn = double(damage_rk4<R>(a.mat[l], R(Dm[l]), R(eps[l]), R(dl), R(dt),
+          const double Dn = double(damage_rk4<R>(matp<R>(a, l), R(Dm[l]), R(eps[l]), R(dl), R(dt),
                                                  R(wx2[0]), R(seq), rho[l]));
           c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
           c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
@@ -858,47 +872,44 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
       report(a.err, ST_ENONFINITE, cell, step);
       continue;
     }
-    double phi[NMAT], eps[NMAT], Dm[NMAT];
-    R rho[NMAT], Dr[NMAT], phir[NMAT];
+    R rho[NMAT], Dr[NMAT], phir[NMAT], Er[NMAT];
     {
       XT phx[NMAT];
       PH::fractions(cx, phx);
 #pragma unroll
-      for (int l = 0; l < NMAT; ++l) phi[l] = double(phx[l]);
+      for (int l = 0; l < NMAT; ++l) phir[l] = R(phx[l]);
     }
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      phir[l] = R(phi[l]);
       rho[l] = w[L::oARHO + l];
-      eps[l] = 0.0;
-      Dm[l] = 0.0;
+      Er[l] = R(0);
+      Dr[l] = R(0);
 #pragma unroll
       for (int h = 0; h < NH; ++h)
         if (a.hslot[l] == h) {
-          eps[l] = double(w[L::oH + 2 * h]);
-          Dm[l] = double(w[L::oH + 2 * h + 1]);
+          Er[l] = w[L::oH + 2 * h];
+          Dr[l] = w[L::oH + 2 * h + 1];
         }
-      Dr[l] = R(Dm[l]);
     }
     R Xc[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) Xc[k] = w[L::oX + k];
-    const double phihat = double(lookup<DIM, R>(a, Xc));
+    const R phihat = lookup<DIM, R>(a, Xc);
     // shear modulus of the mixture; whether the cell may yield
-    double Gm = 0.0;
+    R Gm = R(0);
     bool can_yield = true;
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      const MatK& m = a.mat[l];
-      if (m.eos == 1 && m.G0 > 0.0 && m.plasticity != 1) can_yield = false;
+      const auto& m = matp<R>(a, l);
+      if (m.eos == 1 && m.G0 > 0 && m.plasticity != 1) can_yield = false;
       if constexpr (!P::split) {
         R te, tp, tdp, tG;
         thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
-        Gm += phi[l] * double(tG);
+        Gm += phir[l] * tG;
       }
     }
     // split path: G_mix of the recovery (G does not depend on J2)
-    if constexpr (P::split) Gm = double(mx0.Gm);
+    if constexpr (P::split) Gm = mx0.Gm;
     if constexpr (P::split) {
       // FP32 yield test against the rate-free yield stress; cells clearly
       // inside the yield surface only get det Fbar = 1 (and nothing is
@@ -906,12 +917,12 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
       R y0 = R(0);
 #pragma unroll
       for (int l = 0; l < NMAT; ++l) {
-        const MatK& m = a.mat[l];
+        const auto& m = matp<R>(a, l);
         if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_crit))) continue;
-        const R e = eps[l] > 0.0 ? R(eps[l]) : R(0);
+        const R e = Er[l] > R(0) ? Er[l] : R(0);
         R hard = R(m.c1);
-        if (m.c2 != 0.0) hard += R(m.c2) * mpow(e, R(m.n_hard));
-        y0 += phir[l] * R(phihat) * (m.damage != 0 ? R(1) - Dr[l] : R(1)) * hard;
+        if (m.c2 != 0) hard += R(m.c2) * mpow(e, R(m.n_hard));
+        y0 += phir[l] * phihat * (m.damage != 0 ? R(1) - Dr[l] : R(1)) * hard;
       }
       const R strf = R(2.449489743f) * mx0.Gm * msqrt(mx0.J2);
       if (!can_yield || !(mx0.Gm > R(0)) || !(strf > y0 * R(0.9999))) {
@@ -934,8 +945,8 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
         continue;
       }
     }
-    source_full<P, DIM, NMAT, NH>(a, cell, c, cx, eE, phi, eps, Dm, rho, Dr, phir, phihat, Gm,
-                                  can_yield, dt, step);
+    source_full<P, DIM, NMAT, NH>(a, cell, c, cx, eE, rho, Dr, phir, Er, phihat, Gm, can_yield,
+                                  dt, step);
   }
 }
 

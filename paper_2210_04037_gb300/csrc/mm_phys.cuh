@@ -126,6 +126,48 @@ __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, 
   G = Gs;
 }
 
+// The same closure in FP32 from the FP32 constants: one reciprocal of rho,
+// eta^(alpha-1) = eta^alpha / eta, and the precomputed K0/(2 alpha^2) and
+// K0/(alpha rho0) in place of divisions.
+__device__ __forceinline__ void thermo(const MatKf& m, float rho, float psi, float J2, float& e,
+                                       float& p, float& dp, float& G) {
+  if (m.eos == 0) {
+    e = 0.f; p = 0.f; dp = 0.f; G = 0.f;
+    return;
+  }
+  const float a = m.alpha, bb = m.beta;
+  const float ir = 1.f / rho;
+  const float eta = rho * m.inv_rho0;
+  const float ea = m.alpha_one ? eta : mpow(eta, a);
+  const float q = ea - 1.f;
+  const float k2 = psi * m.K0_2a2;
+  const float ec = k2 * ir * (q * q);
+  const float pc = k2 * (2.f * a * q * ea - q * q);
+  const float dpc = psi * m.K0_arho0 * (ea * m.rho0 * ir) * ((2.f * a - 1.f) * ea + (1.f - a));
+  const float Gs = psi * m.G0 * mpow(eta, bb + 1.f);
+  const float gj = Gs * J2;
+  e = ec + gj * ir;
+  p = pc + bb * gj;
+  dp = dpc + bb * (bb + 1.f) * gj * ir;
+  G = Gs;
+}
+
+// Material constants in the precision of the arithmetic: MatK (FP64) or
+// MatKf (FP32).
+template <class R> struct MatSel;
+template <> struct MatSel<double> {
+  typedef MatK T;
+  __device__ static __forceinline__ const MatK& get(const KArgs& a, int l) { return a.mat[l]; }
+};
+template <> struct MatSel<float> {
+  typedef MatKf T;
+  __device__ static __forceinline__ const MatKf& get(const KArgs& a, int l) { return a.matf[l]; }
+};
+template <class R>
+__device__ __forceinline__ const typename MatSel<R>::T& matp(const KArgs& a, int l) {
+  return MatSel<R>::get(a, l);
+}
+
 // ------------------------------------------- Hencky strain by Jacobi ----
 // One symmetric Schur rotation of the (P,Q) plane.
 template <int P, int Q, class R>
@@ -401,12 +443,12 @@ struct Phys {
     mx.Gm = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      const MatK& m = a.mat[l];
+      const auto& m = matp<R>(a, l);
       const R psi = m.damage != 0 ? R(1) - D[l] : R(1);
       R G;
       thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G);
       if constexpr (P::split)
-        mx.xi += phi[l] * R(m.xi);
+        mx.xi += phi[l] * m.xi;
       else
         mx.xi += phi[l] / R(m.Gamma);
       mx.Gm += phi[l] * G;
@@ -428,9 +470,12 @@ struct Phys {
     R s = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
-      const R Gam = R(a.mat[l].Gamma);
+      const R Gam = R(matp<R>(a, l).Gamma);
       const R cl2 = mx.dp[l] + (Gam + R(1)) * (p - mx.p[l]) / rho[l];
-      s += (arho[l] / ax.rho) * (R(1) / Gam) * cl2;
+      if constexpr (P::split)
+        s += (arho[l] / ax.rho) * matp<R>(a, l).xi * cl2;
+      else
+        s += (arho[l] / ax.rho) * (R(1) / Gam) * cl2;
     }
     const R c2 = s / mx.xi;
     ax.G = mx.Gm;
@@ -468,13 +513,21 @@ struct Phys {
     Mix mx;
     if (!mixture(a, phi, rho, D, X, mx)) return false;
     E rhoe = 0.0, ke = 0.0;
+    R ske = R(0);
+    (void)ske;
     if constexpr (P::split) {
       // FP32: the face states need float accuracy only
       R re = R(0);
 #pragma unroll
-      for (int l = 0; l < NMAT; ++l) re += arho[l] * mx.e[l] + phi[l] * R(a.mat[l].xi) * (p - mx.p[l]);
-      rhoe = E(re);
-      ke = E(R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]));
+      for (int l = 0; l < NMAT; ++l) re += arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * (p - mx.p[l]);
+      const R kef = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
+      // the FP32 sum equals the FP64 sum rounded to FP32 (double rounding is
+      // exact for one addition); the FP64 total is formed only when asked for
+      ske = re + kef;
+      if (rhoE_out) {
+        rhoe = E(re);
+        ke = E(kef);
+      }
     } else {
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
@@ -491,7 +544,10 @@ struct Phys {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) c[L::oMOM + k] = ax.rho * ax.u[k];
     c[L::oE] = R(0);
-    cx[0] = XT(rhoe + ke);
+    if constexpr (P::split)
+      cx[0] = XT(ske);
+    else
+      cx[0] = XT(rhoe + ke);
     if (rhoE_out) *rhoE_out = rhoe + ke;
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = w[L::oF + k];
@@ -556,7 +612,7 @@ struct Phys {
       const R ke = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
       R num = rhoE_d ? R(*rhoE_d - E(ke)) : R(cx[0]) - ke;
 #pragma unroll
-      for (int l = 0; l < NMAT; ++l) num += -arho[l] * mx.e[l] + phi[l] * R(a.mat[l].xi) * mx.p[l];
+      for (int l = 0; l < NMAT; ++l) num += -arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * mx.p[l];
       pE = E(num / mx.xi);
     } else {
       const E ke = 0.5 * E(ax.rho) *
