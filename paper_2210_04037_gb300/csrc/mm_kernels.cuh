@@ -5,6 +5,8 @@
 // translation units, which instantiate them for FP64 and FP32-split.
 #pragma once
 
+#include <type_traits>
+
 #include "mm_phys.cuh"
 
 namespace mm {
@@ -825,12 +827,13 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
     R w2[NF];
     XT wx2[NX];
     Aux<R> as;
-    if (!PH::template u2w<0>(a, c, cx, w2, wx2, as, &eE)) {
+    // the recovery's mixture is that of the returned state (same fractions,
+    // densities and damage, Fbar = X)
+    typename PH::Mix mx;
+    if (!PH::template u2w<0>(a, c, cx, w2, wx2, as, &eE, &mx)) {
       report(a.err, ST_ENONFINITE, cell, step);
       return;
     }
-    typename PH::Mix mx;
-    PH::mixture(a, phir, rho, Dr, X, mx);
     const double seq = sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2));
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
@@ -848,105 +851,194 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
   store_sources<P, DIM, NMAT, NH>(a, cell, c, dl > 0.0);
 }
 
+// Queue of cells at yield (split path), one per CTA in shared memory, as
+// [quantity][slot] columns: the conserved state of the cell and what the
+// yield test derived from it (rho_l, D_l, phi_l, eps_l, phi(X), G_mix).
+template <class P, int DIM, int NMAT, int NH>
+struct SrcQueue {
+  typedef typename P::R R;
+  typedef typename P::X XT;
+  static constexpr int NF = Lay<DIM, NMAT, NH>::NF, NX = Phys<P, DIM, NMAT, NH>::NX;
+  static constexpr int NT = 128, CAP = 2 * NT, NV = 4 * NMAT + 2;
+  R c[NF][CAP];
+  XT cx[NX][CAP];
+  R v[NV][CAP];
+  double eE[CAP];
+  long long cell[CAP];
+  unsigned char cy[CAP];
+  int n;
+};
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void src_dequeue(const KArgs& a, SrcQueue<P, DIM, NMAT, NH>& q, int s,
+                                            double dt, long long step) {
+  typedef SrcQueue<P, DIM, NMAT, NH> Q;
+  typename Q::R c[Q::NF], rho[NMAT], Dr[NMAT], phir[NMAT], Er[NMAT];
+  typename Q::XT cx[Q::NX];
+#pragma unroll
+  for (int k = 0; k < Q::NF; ++k) c[k] = q.c[k][s];
+#pragma unroll
+  for (int k = 0; k < Q::NX; ++k) cx[k] = q.cx[k][s];
+#pragma unroll
+  for (int l = 0; l < NMAT; ++l) {
+    rho[l] = q.v[l][s];
+    Dr[l] = q.v[NMAT + l][s];
+    phir[l] = q.v[2 * NMAT + l][s];
+    Er[l] = q.v[3 * NMAT + l][s];
+  }
+  source_full<P, DIM, NMAT, NH>(a, q.cell[s], c, cx, q.eE[s], rho, Dr, phir, Er,
+                                q.v[4 * NMAT][s], q.v[4 * NMAT + 1][s], q.cy[s] != 0, dt, step);
+}
+
 // Per-cell sources after the sweeps (in place): renormalise det Fbar = 1,
 // radial return in Hencky space to the perturbed yield stress (Newton on
-// the plastic increment in FP64), then RK4 damage.
+// the plastic increment in FP64), then RK4 damage.  Split path: cells
+// inside the yield surface take the short path at once; cells at yield are
+// queued and returned 128 at a time, so the return runs on full warps
+// wherever the yielding cells lie.  The CTA strides over the cells in
+// batches of 128 (uniform trip count: the barriers are reached by all).
 template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(128) k_sources(KArgs a) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
   typedef typename P::X XT;
+  typedef SrcQueue<P, DIM, NMAT, NH> Q;
   constexpr int NF = L::NF, NX = PH::NX;
+  static_assert(Q::NT == 128, "queue batch = CTA size");
+  __shared__ typename std::conditional<P::split, Q, int>::type qs;
   const double dt = a.info->dt;
   const long long step = a.info->steps;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
-       cell += (long long)gridDim.x * blockDim.x) {
-    R c[NF], w[NF];
-    XT cx[NX], wx[NX];
-    double eE;
-    load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
-    Aux<R> ax;
-    typename PH::Mix mx0;
-    if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {
-      report(a.err, ST_ENONFINITE, cell, step);
-      continue;
-    }
-    R rho[NMAT], Dr[NMAT], phir[NMAT], Er[NMAT];
-    {
-      XT phx[NMAT];
-      PH::fractions(cx, phx);
-#pragma unroll
-      for (int l = 0; l < NMAT; ++l) phir[l] = R(phx[l]);
-    }
-#pragma unroll
-    for (int l = 0; l < NMAT; ++l) {
-      rho[l] = w[L::oARHO + l];
-      Er[l] = R(0);
-      Dr[l] = R(0);
-#pragma unroll
-      for (int h = 0; h < NH; ++h)
-        if (a.hslot[l] == h) {
-          Er[l] = w[L::oH + 2 * h];
-          Dr[l] = w[L::oH + 2 * h + 1];
-        }
-    }
-    R Xc[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) Xc[k] = w[L::oX + k];
-    const R phihat = lookup<DIM, R>(a, Xc);
-    // shear modulus of the mixture; whether the cell may yield
-    R Gm = R(0);
-    bool can_yield = true;
-#pragma unroll
-    for (int l = 0; l < NMAT; ++l) {
-      const auto& m = matp<R>(a, l);
-      if (m.eos == 1 && m.G0 > 0 && m.plasticity != 1) can_yield = false;
-      if constexpr (!P::split) {
-        R te, tp, tdp, tG;
-        thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
-        Gm += phir[l] * tG;
+  if constexpr (P::split) {
+    if (threadIdx.x == 0) qs.n = 0;
+    __syncthreads();
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < a.ncell; base += stride) {
+    const long long cell = base + threadIdx.x;
+    do {
+      if (cell >= a.ncell) break;
+      R c[NF], w[NF];
+      XT cx[NX], wx[NX];
+      double eE;
+      load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
+      Aux<R> ax;
+      typename PH::Mix mx0;
+      if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {
+        report(a.err, ST_ENONFINITE, cell, step);
+        break;
       }
-    }
-    // split path: G_mix of the recovery (G does not depend on J2)
-    if constexpr (P::split) Gm = mx0.Gm;
-    if constexpr (P::split) {
-      // FP32 yield test against the rate-free yield stress; cells clearly
-      // inside the yield surface only get det Fbar = 1 (and nothing is
-      // written when that leaves Fbar as it is)
-      R y0 = R(0);
+      R rho[NMAT], Dr[NMAT], phir[NMAT], Er[NMAT];
+      {
+        XT phx[NMAT];
+        PH::fractions(cx, phx);
+#pragma unroll
+        for (int l = 0; l < NMAT; ++l) phir[l] = R(phx[l]);
+      }
+#pragma unroll
+      for (int l = 0; l < NMAT; ++l) {
+        rho[l] = w[L::oARHO + l];
+        Er[l] = R(0);
+        Dr[l] = R(0);
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+          if (a.hslot[l] == h) {
+            Er[l] = w[L::oH + 2 * h];
+            Dr[l] = w[L::oH + 2 * h + 1];
+          }
+      }
+      R Xc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) Xc[k] = w[L::oX + k];
+      const R phihat = lookup<DIM, R>(a, Xc);
+      // shear modulus of the mixture; whether the cell may yield
+      R Gm = R(0);
+      bool can_yield = true;
 #pragma unroll
       for (int l = 0; l < NMAT; ++l) {
         const auto& m = matp<R>(a, l);
-        if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_crit))) continue;
-        const R e = Er[l] > R(0) ? Er[l] : R(0);
-        R hard = R(m.c1);
-        if (m.c2 != 0) hard += R(m.c2) * mpow(e, R(m.n_hard));
-        y0 += phir[l] * phihat * (m.damage != 0 ? R(1) - Dr[l] : R(1)) * hard;
-      }
-      const R strf = R(2.449489743f) * mx0.Gm * msqrt(mx0.J2);
-      if (!can_yield || !(mx0.Gm > R(0)) || !(strf > y0 * R(0.9999))) {
-        R X[9];
-        PH::fullX(c, X);
-        const R ed = (X[0] + X[4] + X[8]) +
-                     (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
-                      X[5] * X[7]) +
-                     (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                      X[2] * (X[3] * X[7] - X[4] * X[6]));
-        if (ed != R(0)) {
-          const R cm1 = mexpm1(mlog1p(ed) / R(3));
-#pragma unroll
-          for (int k = 0; k < L::NFC; ++k) {
-            const int q = FC<DIM>::idx(k);
-            c[L::oF + k] = (X[q] - ((q % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
-          }
-          store_sources<P, DIM, NMAT, NH>(a, cell, c, false);
+        if (m.eos == 1 && m.G0 > 0 && m.plasticity != 1) can_yield = false;
+        if constexpr (!P::split) {
+          R te, tp, tdp, tG;
+          thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
+          Gm += phir[l] * tG;
         }
-        continue;
+      }
+      if constexpr (P::split) {
+        // G_mix of the recovery (G does not depend on J2)
+        Gm = mx0.Gm;
+        // FP32 yield test against the rate-free yield stress; cells clearly
+        // inside the yield surface only get det Fbar = 1 (and nothing is
+        // written when that leaves Fbar as it is)
+        R y0 = R(0);
+#pragma unroll
+        for (int l = 0; l < NMAT; ++l) {
+          const auto& m = matp<R>(a, l);
+          if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_crit))) continue;
+          const R e = Er[l] > R(0) ? Er[l] : R(0);
+          R hard = R(m.c1);
+          if (m.c2 != 0) hard += R(m.c2) * mpow(e, R(m.n_hard));
+          y0 += phir[l] * phihat * (m.damage != 0 ? R(1) - Dr[l] : R(1)) * hard;
+        }
+        const R strf = R(2.449489743f) * mx0.Gm * msqrt(mx0.J2);
+        if (!can_yield || !(mx0.Gm > R(0)) || !(strf > y0 * R(0.9999))) {
+          R X[9];
+          PH::fullX(c, X);
+          const R ed = (X[0] + X[4] + X[8]) +
+                       (X[0] * X[4] - X[1] * X[3] + X[0] * X[8] - X[2] * X[6] + X[4] * X[8] -
+                        X[5] * X[7]) +
+                       (X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                        X[2] * (X[3] * X[7] - X[4] * X[6]));
+          if (ed != R(0)) {
+            const R cm1 = mexpm1(mlog1p(ed) / R(3));
+#pragma unroll
+            for (int k = 0; k < L::NFC; ++k) {
+              const int q = FC<DIM>::idx(k);
+              c[L::oF + k] = (X[q] - ((q % 4 == 0) ? cm1 : R(0))) / (R(1) + cm1);
+            }
+            store_sources<P, DIM, NMAT, NH>(a, cell, c, false);
+          }
+          break;
+        }
+        // at yield: queue the cell (at most 2 x 128 - 1 entries: the queue is
+        // drained below whenever it holds 128)
+        const int sl = atomicAdd(&qs.n, 1);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) qs.c[k][sl] = c[k];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) qs.cx[k][sl] = cx[k];
+#pragma unroll
+        for (int l = 0; l < NMAT; ++l) {
+          qs.v[l][sl] = rho[l];
+          qs.v[NMAT + l][sl] = Dr[l];
+          qs.v[2 * NMAT + l][sl] = phir[l];
+          qs.v[3 * NMAT + l][sl] = Er[l];
+        }
+        qs.v[4 * NMAT][sl] = phihat;
+        qs.v[4 * NMAT + 1][sl] = Gm;
+        qs.eE[sl] = eE;
+        qs.cell[sl] = cell;
+        qs.cy[sl] = can_yield ? 1 : 0;
+      } else {
+        source_full<P, DIM, NMAT, NH>(a, cell, c, cx, eE, rho, Dr, phir, Er, phihat, Gm,
+                                      can_yield, dt, step);
+      }
+    } while (false);
+    if constexpr (P::split) {
+      __syncthreads();
+      const int n = qs.n;
+      if (n >= Q::NT) {
+        src_dequeue<P, DIM, NMAT, NH>(a, qs, n - Q::NT + (int)threadIdx.x, dt, step);
+        __syncthreads();
+        if (threadIdx.x == 0) qs.n = n - Q::NT;
+        __syncthreads();
       }
     }
-    source_full<P, DIM, NMAT, NH>(a, cell, c, cx, eE, rho, Dr, phir, Er, phihat, Gm, can_yield,
-                                  dt, step);
+  }
+  if constexpr (P::split) {
+    // the loop ended on a barrier after the last update of the count
+    const int n = qs.n;
+    if ((int)threadIdx.x < n) src_dequeue<P, DIM, NMAT, NH>(a, qs, (int)threadIdx.x, dt, step);
   }
 }
 
