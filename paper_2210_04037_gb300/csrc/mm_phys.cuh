@@ -257,38 +257,60 @@ __device__ __forceinline__ bool hencky(const R X[9], R devH[9], R h[3], R V[9]) 
   return true;
 }
 
-// ln(I + B) of a symmetric B with small norm by its power series
-// sum_k (-1)^(k+1) B^k / k in Horner form; returns false (leaving L unset)
-// when |B|_F is too large for the chosen number of terms, in which case the
-// caller takes the eigen-decomposition.  Truncation error <= |B|^(K+1)/(K+1)
-// relative to |B| < 1e-8 for the thresholds below.
+// Product O = X Y of two symmetric 3x3 matrices that commute (functions of
+// one matrix), so O is symmetric: the upper triangle is formed and mirrored.
+template <class R>
+__device__ __forceinline__ void sym_mul(const R X[9], const R Y[9], R O[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const R v = X[3 * i + 0] * Y[0 + j] + X[3 * i + 1] * Y[3 + j] + X[3 * i + 2] * Y[6 + j];
+      O[3 * i + j] = v;
+      O[3 * j + i] = v;
+    }
+}
+
+// ln(I + B) of a symmetric B with |B|_F <= 0.5 by the series of the inverse
+// hyperbolic tangent: ln(I + B) = 2 artanh(Z) = 2 sum_k Z^(2k-1)/(2k-1) with
+// Z = B (2I + B)^-1, a function of B whose eigenvalues z = b/(2 + b) obey
+// |z| <= |B|_F/(2 - |B|_F) <= 1/3.  K odd terms in Horner form in Z^2; the
+// truncation, below z^(2K)/(2K+1) relative, stays under 2e-8 for the
+// thresholds below (FP32 accuracy).  Returns false (leaving L unset) beyond
+// |B|_F = 0.5, where the caller takes the eigen-decomposition.
 template <class R>
 __device__ __forceinline__ bool log_series(const R B[9], R L[9]) {
   const R n2 = B[0] * B[0] + B[4] * B[4] + B[8] * B[8] + R(2) * (B[1] * B[1] + B[2] * B[2] + B[5] * B[5]);
   int K;
-  if (n2 <= R(4e-4)) K = 5;          // |B| <= 0.02
-  else if (n2 <= R(1e-2)) K = 9;     // |B| <= 0.1
+  if (n2 <= R(4e-4)) K = 2;         // |z| <= 0.0102: z^4/5 < 3e-9
+  else if (n2 <= R(1e-2)) K = 3;    // |z| <= 0.0527: z^6/7 < 4e-9
+  else if (n2 <= R(0.25)) K = 7;    // |z| <= 1/3: z^14/15 < 2e-8
   else return false;
-  // M <- I/K; then M <- I/k - B M for k = K-1 .. 1; L = B M
-  R M[9];
+  // C = 2I + B (eigenvalues in [1.5, 2.5]); C^-1 = adj(C)/det(C)
+  const R c00 = R(2) + B[0], c11 = R(2) + B[4], c22 = R(2) + B[8];
+  const R c01 = B[1], c02 = B[2], c12 = B[5];
+  const R a00 = c11 * c22 - c12 * c12, a11 = c00 * c22 - c02 * c02, a22 = c00 * c11 - c01 * c01;
+  const R a01 = c02 * c12 - c01 * c22, a02 = c01 * c12 - c02 * c11, a12 = c01 * c02 - c00 * c12;
+  const R id = R(1) / (c00 * a00 + c01 * a01 + c02 * a02);
+  const R Ci[9] = {a00 * id, a01 * id, a02 * id, a01 * id, a11 * id,
+                   a12 * id, a02 * id, a12 * id, a22 * id};
+  R Z[9], Z2[9], P[9];
+  sym_mul(B, Ci, Z);
+  sym_mul(Z, Z, Z2);
+  // P <- I/(2K-1); P <- I/(2k-1) + Z^2 P for k = K-1 .. 1; L = 2 Z P
+  const R cK = R(1) / R(2 * K - 1);
 #pragma unroll
-  for (int q = 0; q < 9; ++q) M[q] = (q % 4 == 0) ? R(1) / R(K) : R(0);
+  for (int q = 0; q < 9; ++q) P[q] = (q % 4 == 0) ? cK : R(0);
   for (int k = K - 1; k >= 1; --k) {
     R T[9];
+    sym_mul(Z2, P, T);
+    const R ck = R(1) / R(2 * k - 1);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        T[3 * i + j] = (i == j ? R(1) / R(k) : R(0)) -
-                       (B[3 * i + 0] * M[0 + j] + B[3 * i + 1] * M[3 + j] + B[3 * i + 2] * M[6 + j]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) M[q] = T[q];
+    for (int q = 0; q < 9; ++q) P[q] = T[q] + ((q % 4 == 0) ? ck : R(0));
   }
+  sym_mul(Z, P, L);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      L[3 * i + j] = B[3 * i + 0] * M[0 + j] + B[3 * i + 1] * M[3 + j] + B[3 * i + 2] * M[6 + j];
+  for (int q = 0; q < 9; ++q) L[q] *= R(2);
   return true;
 }
 
@@ -299,9 +321,9 @@ static __device__ __noinline__ bool hencky_jacobi_f32(const float* A, float* dev
   return hencky<true>(A, devH, h, V);
 }
 
-// dev(H) and J2 = tr(dev(H)^2) of A = Fbar - I, by the series when the
-// elastic stretch is small (every metal state and the diffuse zone kept near
-// the yield surface), else by the eigen-decomposition.
+// dev(H) and J2 = tr(dev(H)^2) of A = Fbar - I, by the series while
+// |Fbar Fbar^T - I|_F <= 0.5 (every metal state, and all but the most
+// distorted gas), else by the eigen-decomposition.
 template <class R>
 __device__ __forceinline__ bool hencky_fast(const R A[9], R devH[9], R& J2) {
   R B[9];
