@@ -1,9 +1,12 @@
 """Build the CUDA library libmmfrac.so in-tree for sm_103a (GB300).
 
 Each translation unit is compiled in parallel with one -gencode; the FP64
-unit is compiled with --fmad=false (separate rounding of products and sums,
-like the CPU reference arithmetic).  Outputs land next to this file and are
-git-ignored.
+units are compiled with --fmad=false (separate rounding of products and sums,
+like the CPU reference arithmetic).  The FP32-split units take FP32 division
+and square root to within 2 ulp (--prec-div=false --prec-sqrt=false, no IEEE
+round-to-nearest sequences) and flush FP32 denormals (--ftz=true); their FP64
+arithmetic (total energy, plastic-return iteration, totals) is unaffected.
+Outputs land next to this file and are git-ignored.
 """
 from __future__ import annotations
 
@@ -22,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {"mm_api.cu": [], "mm_noalloc.cu": []}
 for _d in (1, 2, 3):
     UNITS[f"mm_fp64_d{_d}.cu"] = ["--fmad=false"]
-    UNITS[f"mm_fp32_d{_d}.cu"] = []
+    UNITS[f"mm_fp32_d{_d}.cu"] = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
 
 
 def nvcc() -> str:
