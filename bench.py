@@ -205,9 +205,10 @@ def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True)
         if flush_buf is not None:
             flush_buf.add_(1)
         start[s].record(stream)
-        g.step(1)
+        g.step_async(1)
         stop[s].record(stream)
         launches += g.launches()
+    g.synchronize()  # raises on a failure latched by any of the steps
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in zip(start, stop))
     prof = mmfrac.profile_read(g.h, reset=True)
@@ -238,7 +239,13 @@ def run_gpu(args, rank: int, world: int):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        g, ms, prof, launches = time_device(case, prec, args.steps, args.warmup, stream, flush)
+        # the timed pass (events around each step only), then the same steps
+        # again with events around each launch for the per-kernel times
+        g, ms, _, launches = time_device(case, prec, args.steps, args.warmup, stream, flush,
+                                         profile=False)
+        gk, ms_k, prof, _ = time_device(case, prec, args.steps, args.warmup, stream, flush,
+                                        profile=True)
+        gk.close()
         torch.cuda.synchronize()
     ms = max_over_ranks(ms, dist)
     value = aggregate_rate(case.ncell, args.steps, ms, world)
@@ -256,7 +263,8 @@ def run_gpu(args, rank: int, world: int):
     fp64 = None
     if prec == W.FP32_SPLIT and not args.no_fp64:
         k64 = max(1, min(args.steps, args.fp64_steps))
-        g64, ms64, prof64, _ = time_device(case, W.FP64, k64, args.warmup, stream, flush)
+        g64, ms64, prof64, _ = time_device(case, W.FP64, k64, args.warmup, stream, flush,
+                                           profile=False)
         fp64 = {"value": world * case.ncell * k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
                 "steps": k64}
         g64.close()
@@ -303,6 +311,7 @@ def run_gpu(args, rank: int, world: int):
                      "traffic": None, "algorithmic_bytes_per_launch": algo,
                      "avg_launch_ms": dom_ms},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+        "ms_per_step_with_kernel_events": ms_k / args.steps,
         "e2e": {"value": world * case.ncell * args.steps / e2e_s, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),

@@ -122,6 +122,21 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
  * MM_EINVAL, MM_ENONFINITE, MM_ENOCONV, MM_EDT, MM_ECUDA. */
 mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info);
 
+/* The same n_steps steps as mm_step, enqueued on the grid's stream without
+ * waiting for them (no host synchronisation): for callers that overlap the
+ * stepping with other work or time it with events on the stream.  Argument
+ * and launch errors are returned at once (MM_ESTATE, MM_EINVAL, MM_ECUDA);
+ * a failure inside a step (MM_ENONFINITE, MM_ENOCONV, MM_EDT) is latched on
+ * the device (the first one, with its cell and step) and returned by the
+ * next mm_synchronize, mm_step or mm_read_fields; the state after it is
+ * undefined. */
+mm_status mm_step_async(mm_grid* g, int n_steps, double cfl);
+
+/* Wait for the work enqueued on the grid's stream and report the first
+ * failure latched by the steps since the last report (errors as mm_step).
+ * info (may be NULL) is filled as by mm_step. */
+mm_status mm_synchronize(mm_grid* g, mm_step_info* info);
+
 /* Copy fields to host_dst ([popcount(field_mask)][ncell] doubles, fields
  * in order; bit f of field_mask selects field f, ~0 for all).
  * primitive = 1 returns the primitive fields, 0 the conserved ones.
@@ -172,7 +187,8 @@ mm_status mm_destroy(mm_grid* g);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* mm_last_error(void);
 
-/* Kernels launched by the last mm_step call (for launch accounting). */
+/* Kernels launched by the last mm_step or mm_step_async call (for launch
+ * accounting). */
 int64_t mm_kernel_launches(const mm_grid* g);
 
 /* Kernel timing (tracing aid, no counterpart in the paper).  With enable = 1

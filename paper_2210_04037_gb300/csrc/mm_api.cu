@@ -421,11 +421,19 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   return MM_OK;
 }
 
-mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info) {
-  if (!g) return fail(MM_EINVAL, "mm_step: null grid");
-  if (!g->ready) return fail(MM_ESTATE, "mm_step before mm_set_materials");
+namespace {
+
+mm_status step_args(mm_grid* g, int n_steps, double cfl, const char* who) {
+  if (!g) return fail(MM_EINVAL, "%s: null grid", who);
+  if (!g->ready) return fail(MM_ESTATE, "%s before mm_set_materials", who);
   if (n_steps < 0) return fail(MM_EINVAL, "n_steps must be >= 0");
   if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(MM_EINVAL, "cfl must be in (0, 1]");
+  return MM_OK;
+}
+
+// Enqueue n_steps steps on the grid's stream: CFL reduction, dt, the split
+// sweeps, the sources.  dt stays on the device.
+mm_status enqueue_steps(mm_grid* g, int n_steps, double cfl) {
   g->launches = 0;
   for (int s = 0; s < n_steps; ++s) {
     KArgs a = args_for(g);
@@ -452,7 +460,12 @@ mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info) {
     CUDA_TRY(go(g, 4, 0, 0, c));
     prof_end(g);
   }
-  mm_status st = check_device_error(g, "mm_step");
+  return MM_OK;
+}
+
+// Synchronise, report a latched device failure, fill info.
+mm_status finish_steps(mm_grid* g, const char* who, mm_step_info* info) {
+  mm_status st = check_device_error(g, who);
   prof_collect(g);
   if (info) {
     DevInfo h;
@@ -470,6 +483,28 @@ mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info) {
     }
   }
   return st;
+}
+
+}  // namespace
+
+mm_status mm_step(mm_grid* g, int n_steps, double cfl, mm_step_info* info) {
+  mm_status st = step_args(g, n_steps, cfl, "mm_step");
+  if (st != MM_OK) return st;
+  st = enqueue_steps(g, n_steps, cfl);
+  if (st != MM_OK) return st;
+  return finish_steps(g, "mm_step", info);
+}
+
+mm_status mm_step_async(mm_grid* g, int n_steps, double cfl) {
+  mm_status st = step_args(g, n_steps, cfl, "mm_step_async");
+  if (st != MM_OK) return st;
+  return enqueue_steps(g, n_steps, cfl);
+}
+
+mm_status mm_synchronize(mm_grid* g, mm_step_info* info) {
+  if (!g) return fail(MM_EINVAL, "mm_synchronize: null grid");
+  if (!g->ready) return fail(MM_ESTATE, "mm_synchronize before mm_set_materials");
+  return finish_steps(g, "mm_synchronize", info);
 }
 
 mm_status mm_read_fields(mm_grid* g, uint64_t field_mask, int primitive, double* host_dst,

@@ -3,9 +3,9 @@ marshalling only.  Every step of the method runs in the CUDA library; if the
 library cannot be loaded or no GPU is present, calls raise ``MMError``.
 
 The functions carry the C names without the ``mm_`` prefix
-(``create_grid``, ``set_materials``, ``step``, ``read_fields``,
-``conserved_totals``, ``destroy``, ``last_error``); ``Grid`` bundles them
-for a ``workloads.Case``.
+(``create_grid``, ``set_materials``, ``step``, ``step_async``,
+``synchronize``, ``read_fields``, ``conserved_totals``, ``destroy``,
+``last_error``); ``Grid`` bundles them for a ``workloads.Case``.
 """
 from __future__ import annotations
 
@@ -63,7 +63,8 @@ class StepInfo(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
 
 
-EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
+EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async", "mm_synchronize",
+           "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
            "mm_conserved_totals_noalloc")
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
         lib.mm_create_grid.argtypes = [P(GridDesc), vp, P(vp)]
         lib.mm_set_materials.argtypes = [vp, P(Material), ctypes.c_int, P(Init)]
         lib.mm_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(StepInfo)]
+        lib.mm_step_async.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        lib.mm_synchronize.argtypes = [vp, P(StepInfo)]
         lib.mm_read_fields.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double),
                                        ctypes.c_size_t]
         lib.mm_conserved_totals.argtypes = [vp, P(ctypes.c_double), ctypes.c_size_t]
@@ -105,8 +108,8 @@ def load(path: str = LIB_PATH):
         lib.mm_conserved_totals_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
                                                     ctypes.c_int, P(ctypes.c_double), vp, vp]
         lib.mm_conserved_totals_noalloc.restype = ctypes.c_int
-        for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_read_fields",
-                   "mm_conserved_totals", "mm_destroy"):
+        for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async",
+                   "mm_synchronize", "mm_read_fields", "mm_conserved_totals", "mm_destroy"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -168,6 +171,19 @@ def set_materials(grid, case, prim: np.ndarray | None = None) -> None:
 def step(grid, n_steps: int, cfl: float) -> dict:
     info = StepInfo()
     _check(load().mm_step(grid, int(n_steps), float(cfl), ctypes.byref(info)))
+    return dict(t=info.t, dt_last=info.dt_last, smax=info.smax, steps=info.steps_done,
+                bad_cell=info.bad_cell)
+
+
+def step_async(grid, n_steps: int, cfl: float) -> None:
+    """Enqueue n_steps steps without waiting; in-step failures are reported
+    by the next synchronize / step / read_fields."""
+    _check(load().mm_step_async(grid, int(n_steps), float(cfl)))
+
+
+def synchronize(grid) -> dict:
+    info = StepInfo()
+    _check(load().mm_synchronize(grid, ctypes.byref(info)))
     return dict(t=info.t, dt_last=info.dt_last, smax=info.smax, steps=info.steps_done,
                 bad_cell=info.bad_cell)
 
@@ -242,6 +258,12 @@ class Grid:
 
     def step(self, n_steps: int, cfl: float | None = None) -> dict:
         return step(self.h, n_steps, self.case.cfl if cfl is None else cfl)
+
+    def step_async(self, n_steps: int, cfl: float | None = None) -> None:
+        step_async(self.h, n_steps, self.case.cfl if cfl is None else cfl)
+
+    def synchronize(self) -> dict:
+        return synchronize(self.h)
 
     def read(self, primitive: bool = True, field_mask: int = (1 << 64) - 1, out=None) -> np.ndarray:
         return read_fields(self.h, primitive, field_mask, out)

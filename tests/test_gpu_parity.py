@@ -104,6 +104,23 @@ def test_fp32_split_error_against_oracle_on_smooth_problem():
     assert abs(G0[5] - T0[5]) <= 1e-5 * abs(T0[5])
 
 
+@pytest.mark.parametrize("prec", [mmfrac.FP64, mmfrac.FP32_SPLIT])
+def test_async_steps_equal_blocking_steps(prec):
+    case = W.ring_2d(40)
+    g1 = mmfrac.Grid(case, prec)
+    i1 = g1.step(12)
+    u1 = g1.read(False)
+    g1.close()
+    g2 = mmfrac.Grid(case, prec)
+    for _ in range(3):
+        g2.step_async(4)
+    i2 = g2.synchronize()
+    u2 = g2.read(False)
+    g2.close()
+    assert np.array_equal(u1, u2)
+    assert i1 == i2
+
+
 def test_inadmissible_initial_state_is_reported():
     c = W.spall_1d(64)
     c.prim[c.layout.o_rho, 10] = -1.0
@@ -122,9 +139,14 @@ def test_argument_errors():
     with pytest.raises(mmfrac.MMError) as e:
         mmfrac.read_fields(g.h, out=np.empty((1, 3)))
     assert e.value.status == mmfrac.MM_EINVAL
+    with pytest.raises(mmfrac.MMError) as e:
+        mmfrac.step_async(g.h, -1, 0.5)
+    assert e.value.status == mmfrac.MM_EINVAL
     g.close()
     h = mmfrac.create_grid(c)
-    with pytest.raises(mmfrac.MMError) as e:
-        mmfrac.step(h, 1, 0.5)
-    assert e.value.status == mmfrac.MM_ESTATE
+    for call in (lambda: mmfrac.step(h, 1, 0.5), lambda: mmfrac.step_async(h, 1, 0.5),
+                 lambda: mmfrac.synchronize(h)):
+        with pytest.raises(mmfrac.MMError) as e:
+            call()
+        assert e.value.status == mmfrac.MM_ESTATE
     mmfrac.destroy(h)
