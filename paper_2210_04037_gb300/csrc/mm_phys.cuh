@@ -315,10 +315,16 @@ __device__ __forceinline__ bool log_series(const R B[9], R L[9]) {
 }
 
 // Large-strain fallback of hencky_fast: one out-of-line copy, so the rarely
-// taken eigen-decomposition does not bloat every inlined call site.
-static __device__ __noinline__ bool hencky_jacobi_f32(const float* A, float* devH) {
+// taken eigen-decomposition does not bloat every inlined call site.  Its
+// operands travel by value (in registers), so the call sites keep no copy of
+// the tensor in local memory for the branch they almost never take.
+struct F9 { float v[9]; };
+struct F10 { float v[9]; float ok; };
+static __device__ __noinline__ F10 hencky_jacobi_f32(F9 A) {
   float h[3], V[9];
-  return hencky<true>(A, devH, h, V);
+  F10 r;
+  r.ok = hencky<true>(A.v, r.v, h, V) ? 1.f : 0.f;
+  return r;
 }
 
 // dev(H) and J2 = tr(dev(H)^2) of A = Fbar - I, by the series while
@@ -342,7 +348,13 @@ __device__ __forceinline__ bool hencky_fast(const R A[9], R devH[9], R& J2) {
 #pragma unroll
     for (int q = 0; q < 9; ++q) devH[q] = R(0.5) * (L[q] - ((q % 4 == 0) ? tr : R(0)));
   } else {
-    if (!hencky_jacobi_f32(A, devH)) return false;
+    F9 a9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a9.v[q] = A[q];
+    const F10 r = hencky_jacobi_f32(a9);
+    if (r.ok == 0.f) return false;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) devH[q] = r.v[q];
   }
   J2 = R(0);
 #pragma unroll
