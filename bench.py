@@ -6,8 +6,13 @@ update = one cell through one full step), for the FP32-split path (the
 headline) beside the FP64 path, with the HBM roofline fraction of the
 dominant kernel.
 
-    python bench.py [--gpus N --steps K --warmup W] [--workload ring_2d|cylinder_3d|spall_1d]
+    python bench.py [--gpus N --steps K --warmup W]
+                    [--workload ring_2d|cylinder_3d|spall_1d|ensemble_2d]
                     [--precision fp32split|fp64] [--impl mmfrac|reference]
+
+``--workload ensemble_2d`` times a batch of seeded 2D rings of uneven size
+(``--size`` members, default 64) stepped together, beside the same members
+stepped one at a time in FP32-split and in FP64.
 
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload (the step does not shard on one grid here: replicas only); the
@@ -34,7 +39,7 @@ from paper_2210_04037_gb300 import workloads as W  # noqa: E402
 
 METRIC = ("cell-updates/s and % HBM roofline at 1 GB300, FP32-split vs FP64 at stated error")
 L2_BYTES = 129 * 2 ** 20
-DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000}
+DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000, "ensemble_2d": 64}
 WORKLOAD_TEXT = {
     "ring_2d": "2D expanding ring, {n}x{n} cells, Al-H32 annulus r 20-24 mm at 200 m/s in air, "
                "simple damage, phi0 ~ U(0.9,1.1) on a 0.5 mm lattice",
@@ -42,10 +47,25 @@ WORKLOAD_TEXT = {
                    "air, Bonora damage, phi0 ~ rectified N(1,0.1^2) on a 0.5 mm lattice",
     "spall_1d": "1D plate impact spall, {n} cells, CuBe flyer 2 mm at 300 m/s onto a 6 mm "
                 "target, Bonora damage, phi0 ~ rectified N(1,0.05^2) per cell",
+    "ensemble_2d": "batched ensemble: {n} seeded 2D expanding rings (the ring workload, seeds "
+                   "100..), grids uneven 128^2..768^2 in steps of 8, stepped together: one launch "
+                   "per kernel kind over all members, CUDA graph replay, autotuned tile shapes",
 }
 
 
+def ensemble_sizes(m: int):
+    """Grid edge of each member: 128 .. 768 evenly, multiples of 8."""
+    return [128 + 8 * round(80 * i / max(m - 1, 1)) for i in range(m)]
+
+
+def ensemble_cases(m: int):
+    return [W.ring_2d(n, seed=100 + i) for i, n in enumerate(ensemble_sizes(m))]
+
+
 def make_case(name: str, n: int):
+    if name == "ensemble_2d":
+        # the oracle's sample of an ensemble: its smallest member
+        return ensemble_cases(n)[0]
     return W.WORKLOADS[name](n)
 
 
@@ -156,7 +176,9 @@ def cpu_baseline(case_name: str, n: int, budget_s: float = 12.0, max_steps: int 
     el = time.perf_counter() - t0
     return {"value": case.ncell * steps / el, "unit": "cell-updates/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"{steps} FP64 steps of the same {case.ncell}-cell workload from its "
+            "sample": f"{steps} FP64 steps of the same {case.ncell}-cell workload"
+                      + (" (the ensemble's smallest member)" if case_name == "ensemble_2d" else "")
+                      + " from its "
                       f"initial state ({el:.1f} s wall)"}
 
 
@@ -215,9 +237,134 @@ def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True)
     return g, ms, prof, launches
 
 
+def time_alone(cases, precision, steps, stream):
+    """Each member alone (created, one warm-up step, `steps` timed enqueued
+    steps, freed): summed device time."""
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    total = 0.0
+    for c in cases:
+        g = mmfrac.Grid(c, precision, stream=stream.cuda_stream)
+        g.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step_async(steps)
+        e1.record(stream)
+        g.synchronize()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        g.close()
+    return total
+
+
+def run_ensemble(args, rank: int, world: int):
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    m = args.size or DEFAULT_SIZE["ensemble_2d"]
+    members = ensemble_cases(m)
+    ncell = sum(c.ncell for c in members)
+    prec = W.FP32_SPLIT if args.precision == "fp32split" else W.FP64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    grids = [mmfrac.Grid(c, prec, stream=stream.cuda_stream) for c in members]
+    b = mmfrac.Batch(grids, stream=stream.cuda_stream)
+    b.step(args.warmup)
+    chosen = b.autotune(reps=3)
+    b.step(1)  # captures the step with the chosen tiles
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stop = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            start[s].record(stream)
+            b.step_async(1)
+            stop[s].record(stream)
+        b.synchronize()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(z) for a, z in zip(start, stop)), dist)
+    value = aggregate_rate(ncell, args.steps, ms, world)
+    # per-kernel times: the same number of steps launched kernel by kernel
+    b.profile_enable(True)
+    b.step(args.steps)
+    prof = b.profile_read()
+    b.profile_enable(False)
+    b.close()
+    for g in grids:
+        g.close()
+    sbytes = sum(state_bytes(c, prec) for c in members)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    algo = 2 * sbytes if dom.startswith("sweep") or dom == "sources" else sbytes
+    peak, peak_kind = read_peaks()
+    achieved = algo / (dom_ms * 1e-3) / 1e9
+    # the same members one at a time: FP32-split, and the plain FP64 path
+    k1 = max(1, min(args.steps, 10))
+    ms32 = time_alone(members, W.FP32_SPLIT, k1, stream)
+    k64 = max(1, min(args.steps, args.fp64_steps, 3))
+    ms64 = time_alone(members, W.FP64, k64, stream)
+    alone32 = ncell * k1 / (ms32 * 1e-3)
+    alone64 = ncell * k64 / (ms64 * 1e-3)
+    # end to end through the C ABI: upload every member's initial state,
+    # batch, K steps, read every member back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eg = [mmfrac.Grid(c, prec, stream=stream.cuda_stream) for c in members]
+    eb = mmfrac.Batch(eg, stream=stream.cuda_stream)
+    eb.step(args.steps)
+    outs = [g.read() for g in eg]
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    eb.close()
+    for g in eg:
+        g.close()
+    h2d = sum(c.prim.nbytes + (c.phi0.nbytes if c.phi0 is not None else 0) for c in members)
+    d2h = sum(o.nbytes for o in outs)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == W.FP32_SPLIT else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["ensemble_2d"].format(n=m), "members": m,
+                   "cells": ncell, "precision": args.precision,
+                   "tile_variants": chosen[:2],
+                   "l2": "state larger than L2", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": algo,
+                     "avg_launch_ms": dom_ms},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+        "one_at_a_time": {
+            "fp32split": {"value": alone32, "ms_per_step": ms32 / k1, "steps": k1},
+            "fp64": {"value": alone64, "ms_per_step": ms64 / k64, "steps": k64},
+            "batched_over_fp64": value / alone64, "batched_over_fp32split": value / alone32},
+        "e2e": {"value": world * ncell * args.steps / e2e_s, "unit": "cell-updates/s",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps * (3 + 2),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline("ensemble_2d", m)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     from paper_2210_04037_gb300 import mmfrac
+    if args.workload == "ensemble_2d":
+        return run_ensemble(args, rank, world)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None

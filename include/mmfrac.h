@@ -144,6 +144,54 @@ mm_status mm_synchronize(mm_grid* g, mm_step_info* info);
 mm_status mm_read_fields(mm_grid* g, uint64_t field_mask, int primitive,
                          double* host_dst, size_t dst_len);
 
+/* ---- Batched ensembles.  Sec. 4.3 notes that one run of the expanding
+ * ring is a single sample and that fragment statistics need the model run
+ * many times: a batch steps many grids (seeded realisations of the
+ * perturbation field, of uneven size) together.  Each member keeps its own
+ * state, dt and time; one launch per kernel kind covers every member (CTAs
+ * take the members' tiles or cell chunks from a work counter), and from the
+ * second step on a step is one CUDA graph launch.  A member's results are
+ * those of mm_step on that member alone. */
+typedef struct mm_batch mm_batch;
+
+/* Batch the n grids (distinct, materials set, same dimension, precision and
+ * material layout, two materials).  The batch references the grids, which
+ * must outlive it; between mm_batch_step and mm_batch_synchronize the grids
+ * must not be used on their own.  cuda_stream: stream to order the batch's
+ * work on, or NULL for one the library creates.  Errors: MM_EINVAL,
+ * MM_ESTATE (a member without materials), MM_ENOMEM, MM_ECUDA. */
+mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_batch** out);
+
+/* use_graph: 1 (default) replays captured steps, 0 launches each kernel;
+ * tile_variant (may be NULL): tile shape per sweep axis, 0 or 1 (FP32-split
+ * has two shapes per axis, FP64 one).  Errors: MM_EINVAL. */
+mm_status mm_batch_set_options(mm_batch* b, int use_graph, const int tile_variant[3]);
+
+/* Enqueue n_steps steps of every member (each with its own dt = cfl dx_min
+ * / s_max) without waiting.  Failures inside a step are latched per member
+ * and returned by mm_batch_synchronize.  Errors: MM_EINVAL, MM_ECUDA. */
+mm_status mm_batch_step(mm_batch* b, int n_steps, double cfl);
+
+/* Time each tile shape of each sweep axis on the batch's current states
+ * (reps timed launches after one warm-up; a sweep into the free buffer
+ * leaves the state unchanged), keep the fastest, and return the choice in
+ * chosen (may be NULL).  Blocks.  Errors: MM_EINVAL, MM_ECUDA. */
+mm_status mm_batch_autotune(mm_batch* b, int reps, int chosen[3]);
+
+/* Wait for the batch's work and report the first failure latched by a
+ * member (its index in the message).  Errors as mm_step. */
+mm_status mm_batch_synchronize(mm_batch* b);
+
+/* Per-kernel timing of the batch's launches, as mm_profile_enable /
+ * mm_profile_read for a grid (while it is on, steps are launched kernel by
+ * kernel, not replayed from a graph; times are collected by
+ * mm_batch_synchronize).  Errors: MM_EINVAL. */
+mm_status mm_batch_profile_enable(mm_batch* b, int enable);
+mm_status mm_batch_profile_read(mm_batch* b, double* ms, int64_t* counts, int n, int reset);
+
+/* Wait for the batch's work and free the batch (not its grids). */
+mm_status mm_batch_destroy(mm_batch* b);
+
 /* Conserved totals sum_cells dV (phi rho)_l (N values), sum dV rho u
  * (3 values, 0 for k >= dim), sum dV rho E: N + 4 doubles, accumulated in
  * FP64.  out_len >= N + 4.  Errors: MM_EINVAL. */

@@ -24,8 +24,9 @@ LIB = os.path.join(HERE, "libmmfrac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {"mm_api.cu": [], "mm_noalloc.cu": []}
 for _d in (1, 2, 3):
-    UNITS[f"mm_fp64_d{_d}.cu"] = ["--fmad=false"]
-    UNITS[f"mm_fp32_d{_d}.cu"] = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
+    for _b in ("", "_batch"):
+        UNITS[f"mm_fp64_d{_d}{_b}.cu"] = ["--fmad=false"]
+        UNITS[f"mm_fp32_d{_d}{_b}.cu"] = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
 
 
 def nvcc() -> str:

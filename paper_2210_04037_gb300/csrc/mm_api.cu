@@ -33,7 +33,7 @@ mm_status fail(mm_status s, const char* fmt, ...) {
       return fail(MM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
-__global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin) {
+__device__ __forceinline__ void dt_update(DevInfo* info, DevErr* err, double cfl, double dxmin) {
   const double smax = __longlong_as_double((long long)info->smax_bits);
   info->smax_bits = 0ull;
   info->steps += 1;
@@ -47,6 +47,17 @@ __global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin) {
   info->dt = dt;
   info->smax = smax;
   info->t += dt;
+}
+
+// dt = cfl dx_min / s_max from the CFL reduction; advances t and the step count.
+__global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin) {
+  dt_update(info, err, cfl, dxmin);
+}
+
+// The same for every member of a batch (one thread per member).
+__global__ void k_dt_batch(const KArgs* args, int M, double cfl) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) dt_update(args[m].info, args[m].err, cfl, args[m].dxmin);
 }
 
 }  // namespace
@@ -137,8 +148,10 @@ mm_status check_device_error(mm_grid* g, const char* where) {
   return MM_OK;
 }
 
-// Start / stop the timing of one launch of the given kind.
-void prof_begin(mm_grid* g, int kind) {
+// Start / stop the timing of one launch of the given kind (G: a grid or a
+// batch, both carrying the same timing fields).
+template <class G>
+void prof_begin(G* g, int kind) {
   if (!g->prof) return;
   const size_t i = g->ev_kind.size();
   while (g->ev.size() < 2 * (i + 1)) {
@@ -150,13 +163,15 @@ void prof_begin(mm_grid* g, int kind) {
   cudaEventRecord(g->ev[2 * i], g->stream);
 }
 
-void prof_end(mm_grid* g) {
+template <class G>
+void prof_end(G* g) {
   if (!g->prof) return;
   cudaEventRecord(g->ev[2 * (g->ev_kind.size() - 1) + 1], g->stream);
 }
 
 // After a stream synchronisation: accumulate the recorded pairs.
-void prof_collect(mm_grid* g) {
+template <class G>
+void prof_collect(G* g) {
   if (!g->prof) return;
   for (size_t i = 0; i < g->ev_kind.size(); ++i) {
     float ms = 0.f;
@@ -580,3 +595,357 @@ mm_status mm_destroy(mm_grid* g) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ batches ----
+// Several grids stepped together: one launch per kernel kind covers every
+// member (persistent CTAs over the concatenated tiles or cell chunks), each
+// member with its own dt; a step is captured in a CUDA graph and replayed.
+
+namespace {
+
+constexpr long long kChunk = 8192;  // cells per unit of the CFL and source launches
+constexpr int kPhases = 5;          // CFL, sweeps x, y, z, sources
+
+typedef cudaError_t (*batch_launcher)(int, int, int, int, int, const BatchK&, cudaStream_t);
+typedef long long (*tiles_fn)(int, int, const int[3]);
+
+batch_launcher batch_launch_of(int prec, int dim) {
+  static const batch_launcher t[2][3] = {{mm_p64_d1_batch, mm_p64_d2_batch, mm_p64_d3_batch},
+                                         {mm_p32_d1_batch, mm_p32_d2_batch, mm_p32_d3_batch}};
+  return t[prec == MM_FP64 ? 0 : 1][dim - 1];
+}
+
+tiles_fn tiles_of(int prec, int dim) {
+  static const tiles_fn t[2][3] = {
+      {mm_p64_d1_batch_tiles, mm_p64_d2_batch_tiles, mm_p64_d3_batch_tiles},
+      {mm_p32_d1_batch_tiles, mm_p32_d2_batch_tiles, mm_p32_d3_batch_tiles}};
+  return t[prec == MM_FP64 ? 0 : 1][dim - 1];
+}
+
+KArgs args_at(const mm_grid* g, int c) {
+  KArgs a = g->base;
+  a.Uin = g->U[c];
+  a.Uout = g->U[c];
+  a.Ein = g->E[c];
+  a.Eout = g->E[c];
+  return a;
+}
+
+}  // namespace
+
+struct mm_batch {
+  std::vector<mm_grid*> m;
+  int M = 0, dim = 0, prec = 0, nmat = 0, nhist = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  KArgs* args = nullptr;                  // [2 parities][kPhases][M] member arguments
+  long long* tstart = nullptr;            // [3 axes][2 variants][M + 1] tile prefix
+  long long* cstart = nullptr;            // [M + 1] chunk prefix
+  unsigned long long* counter = nullptr;  // [8] work counters of one step
+  std::vector<long long> h_tstart, h_cstart;
+  int variant[3] = {0, 0, 0};
+  int parity = 0;  // flips with every sweep: the members' buffers relative to creation
+  int use_graph = 1;
+  bool warmed = false;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  double exec_cfl[2] = {0.0, 0.0};
+  // kernel timing (steps are launched one kernel at a time while it is on)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  double prof_ms[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+  long long prof_n[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+void batch_free(mm_batch* b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  cudaFree(b->args);
+  cudaFree(b->tstart);
+  cudaFree(b->cstart);
+  cudaFree(b->counter);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+void batch_drop_graphs(mm_batch* b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+    b->exec[p] = nullptr;
+  }
+}
+
+BatchK batch_k(const mm_batch* b, int phase, const long long* start, long long total) {
+  BatchK k;
+  k.args = b->args + ((size_t)b->parity * kPhases + phase) * b->M;
+  k.start = start;
+  k.counter = b->counter + phase;
+  k.total = total;
+  k.chunk = kChunk;
+  k.M = b->M;
+  return k;
+}
+
+// The launches of one step at the current parity (capturable).
+cudaError_t batch_enqueue(mm_batch* b, double cfl) {
+  batch_launcher L = batch_launch_of(b->prec, b->dim);
+  const int M = b->M;
+  cudaError_t e = cudaMemsetAsync(b->counter, 0, 8 * sizeof(unsigned long long), b->stream);
+  if (e != cudaSuccess) return e;
+  prof_begin(b, MM_K_CFL);
+  e = L(0, 0, 0, b->nmat, b->nhist, batch_k(b, 0, b->cstart, b->h_cstart[M]), b->stream);
+  prof_end(b);
+  if (e != cudaSuccess) return e;
+  prof_begin(b, MM_K_DT);
+  k_dt_batch<<<(M + 127) / 128, 128, 0, b->stream>>>(
+      b->args + (size_t)b->parity * kPhases * M, M, cfl);
+  prof_end(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int d = 0; d < b->dim; ++d) {
+    const int v = b->variant[d];
+    const size_t o = (size_t)(d * 2 + v) * (M + 1);
+    prof_begin(b, MM_K_SWEEP_X + d);
+    e = L(1, d, v, b->nmat, b->nhist, batch_k(b, 1 + d, b->tstart + o, b->h_tstart[o + M]),
+          b->stream);
+    prof_end(b);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(b, MM_K_SOURCES);
+  e = L(2, 0, 0, b->nmat, b->nhist, batch_k(b, 4, b->cstart, b->h_cstart[M]), b->stream);
+  prof_end(b);
+  return e;
+}
+
+void batch_advance(mm_batch* b) {
+  if (b->dim & 1) {
+    b->parity ^= 1;
+    for (mm_grid* g : b->m) g->cur ^= 1;
+  }
+}
+
+}  // namespace
+
+mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_batch** out) {
+  if (!grids || !out || n < 1) return fail(MM_EINVAL, "mm_batch_create: null argument or n < 1");
+  *out = nullptr;
+  const mm_grid* g0 = grids[0];
+  for (int i = 0; i < n; ++i) {
+    const mm_grid* g = grids[i];
+    if (!g) return fail(MM_EINVAL, "mm_batch_create: member %d is null", i);
+    if (!g->ready) return fail(MM_ESTATE, "mm_batch_create: member %d has no materials", i);
+    if (g->dim != g0->dim || g->prec != g0->prec || g->nmat != g0->nmat || g->nhist != g0->nhist)
+      return fail(MM_EINVAL,
+                  "mm_batch_create: member %d differs from member 0 in dimension, precision or "
+                  "material layout", i);
+    for (int j = 0; j < i; ++j)
+      if (grids[j] == g) return fail(MM_EINVAL, "mm_batch_create: member %d repeats member %d", i, j);
+  }
+  if (g0->nmat != 2)
+    return fail(MM_EINVAL, "mm_batch_create: batches are built for two materials");
+  for (int i = 0; i < n; ++i) CUDA_TRY(cudaStreamSynchronize(grids[i]->stream));
+  mm_batch* b = new mm_batch();
+  b->m.assign(grids, grids + n);
+  b->M = n;
+  b->dim = g0->dim;
+  b->prec = g0->prec;
+  b->nmat = g0->nmat;
+  b->nhist = g0->nhist;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      batch_free(b);
+      return fail(MM_ECUDA, "cudaStreamCreate failed");
+    }
+    b->own_stream = true;
+  }
+  // member arguments per step-start parity and phase
+  std::vector<KArgs> A((size_t)2 * kPhases * n);
+  for (int p = 0; p < 2; ++p)
+    for (int i = 0; i < n; ++i) {
+      const mm_grid* g = grids[i];
+      const int c0 = g->cur ^ p;
+      A[((size_t)p * kPhases + 0) * n + i] = args_at(g, c0);
+      for (int d = 0; d < 3; ++d) {
+        const int ci = c0 ^ (d & 1);
+        KArgs a = args_at(g, ci);
+        a.Uout = g->U[ci ^ 1];
+        a.Eout = g->E[ci ^ 1];
+        A[((size_t)p * kPhases + 1 + d) * n + i] = a;
+      }
+      A[((size_t)p * kPhases + 4) * n + i] = args_at(g, c0 ^ (g->dim & 1));
+    }
+  b->h_tstart.assign((size_t)3 * 2 * (n + 1), 0);
+  tiles_fn T = tiles_of(b->prec, b->dim);
+  for (int d = 0; d < b->dim; ++d)
+    for (int v = 0; v < 2; ++v) {
+      long long* st = &b->h_tstart[(size_t)(d * 2 + v) * (n + 1)];
+      for (int i = 0; i < n; ++i) {
+        const int nn[3] = {(int)grids[i]->desc.n[0], (int)grids[i]->desc.n[1], (int)grids[i]->desc.n[2]};
+        st[i + 1] = st[i] + T(d, v, nn);
+      }
+    }
+  b->h_cstart.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i)
+    b->h_cstart[i + 1] = b->h_cstart[i] + (grids[i]->ncell + kChunk - 1) / kChunk;
+  if (cudaMalloc(&b->args, sizeof(KArgs) * A.size()) != cudaSuccess ||
+      cudaMalloc(&b->tstart, sizeof(long long) * b->h_tstart.size()) != cudaSuccess ||
+      cudaMalloc(&b->cstart, sizeof(long long) * b->h_cstart.size()) != cudaSuccess ||
+      cudaMalloc(&b->counter, sizeof(unsigned long long) * 8) != cudaSuccess) {
+    batch_free(b);
+    return fail(MM_ENOMEM, "device allocation of the batch tables failed");
+  }
+  cudaError_t e = cudaMemcpy(b->args, A.data(), sizeof(KArgs) * A.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->tstart, b->h_tstart.data(), sizeof(long long) * b->h_tstart.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->cstart, b->h_cstart.data(), sizeof(long long) * b->h_cstart.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return fail(MM_ECUDA, "mm_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return MM_OK;
+}
+
+mm_status mm_batch_set_options(mm_batch* b, int use_graph, const int tile_variant[3]) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_set_options: null batch");
+  b->use_graph = use_graph != 0;
+  if (tile_variant)
+    for (int d = 0; d < 3; ++d) {
+      if (tile_variant[d] != 0 && tile_variant[d] != 1)
+        return fail(MM_EINVAL, "tile variants are 0 or 1");
+      b->variant[d] = tile_variant[d];
+    }
+  batch_drop_graphs(b);
+  return MM_OK;
+}
+
+mm_status mm_batch_step(mm_batch* b, int n_steps, double cfl) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_step: null batch");
+  if (n_steps < 0) return fail(MM_EINVAL, "n_steps must be >= 0");
+  if (!(cfl > 0.0) || !(cfl <= 1.0)) return fail(MM_EINVAL, "cfl must be in (0, 1]");
+  for (int s = 0; s < n_steps; ++s) {
+    const int p = b->parity;
+    if (b->use_graph && b->warmed && !b->prof) {
+      if (!b->exec[p] || b->exec_cfl[p] != cfl) {
+        if (b->exec[p]) cudaGraphExecDestroy(b->exec[p]);
+        b->exec[p] = nullptr;
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = batch_enqueue(b, cfl);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return fail(MM_ECUDA, "mm_batch_step: graph capture: %s",
+                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&b->exec[p], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          b->exec[p] = nullptr;
+          return fail(MM_ECUDA, "mm_batch_step: cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        b->exec_cfl[p] = cfl;
+      }
+      CUDA_TRY(cudaGraphLaunch(b->exec[p], b->stream));
+    } else {
+      // the first step runs uncaptured (it sets the kernels' attributes)
+      CUDA_TRY(batch_enqueue(b, cfl));
+      b->warmed = true;
+    }
+    batch_advance(b);
+  }
+  return MM_OK;
+}
+
+mm_status mm_batch_autotune(mm_batch* b, int reps, int chosen[3]) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_autotune: null batch");
+  if (reps < 1) reps = 1;
+  batch_launcher L = batch_launch_of(b->prec, b->dim);
+  const int M = b->M;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  for (int d = 0; d < b->dim; ++d) {
+    float best = -1.f;
+    for (int v = 0; v < (b->prec == MM_FP64 ? 1 : 2); ++v) {
+      const size_t o = (size_t)(d * 2 + v) * (M + 1);
+      // a sweep from the current state into the free buffer (phase 1 of the
+      // current parity) leaves the state as it is: it can be timed freely
+      const BatchK k = batch_k(b, 1, b->tstart + o, b->h_tstart[o + M]);
+      float ms = 0.f;
+      for (int r = -1; r < reps; ++r) {
+        CUDA_TRY(cudaMemsetAsync(b->counter + 1, 0, sizeof(unsigned long long), b->stream));
+        CUDA_TRY(cudaEventRecord(e0, b->stream));
+        CUDA_TRY(L(1, d, v, b->nmat, b->nhist, k, b->stream));
+        CUDA_TRY(cudaEventRecord(e1, b->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        if (r >= 0) ms += t;  // r = -1 warms up
+      }
+      if (best < 0.f || ms < best) {
+        best = ms;
+        b->variant[d] = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_drop_graphs(b);
+  if (chosen)
+    for (int d = 0; d < 3; ++d) chosen[d] = b->variant[d];
+  for (mm_grid* g : b->m) {
+    mm_status st = check_device_error(g, "mm_batch_autotune");
+    if (st != MM_OK) return st;
+  }
+  return MM_OK;
+}
+
+mm_status mm_batch_synchronize(mm_batch* b) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_synchronize: null batch");
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  prof_collect(b);
+  for (int i = 0; i < b->M; ++i) {
+    mm_status st = check_device_error(b->m[i], "mm_batch_synchronize");
+    if (st != MM_OK) {
+      std::string msg = g_error;
+      return fail(st, "member %d: %s", i, msg.c_str());
+    }
+  }
+  return MM_OK;
+}
+
+mm_status mm_batch_profile_enable(mm_batch* b, int enable) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_profile_enable: null batch");
+  b->prof = enable != 0;
+  return MM_OK;
+}
+
+mm_status mm_batch_profile_read(mm_batch* b, double* ms, int64_t* counts, int n, int reset) {
+  if (!b || n < 0) return fail(MM_EINVAL, "mm_batch_profile_read: bad argument");
+  for (int k = 0; k < n && k < MM_K_COUNT; ++k) {
+    if (ms) ms[k] = b->prof_ms[k];
+    if (counts) counts[k] = b->prof_n[k];
+  }
+  if (reset)
+    for (int k = 0; k < MM_K_COUNT; ++k) {
+      b->prof_ms[k] = 0.0;
+      b->prof_n[k] = 0;
+    }
+  return MM_OK;
+}
+
+mm_status mm_batch_destroy(mm_batch* b) {
+  if (!b) return MM_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return MM_OK;
+}

@@ -75,7 +75,21 @@ struct KArgs {
   double cfl, dxmin;
   double* prim;        // [nfield][ncell] doubles for init / read
   double* partial;     // per-block partial totals
-  int tiles[3];        // tiles along the sweep axis, the transverse axis, the rest
+};
+
+static_assert(sizeof(KArgs) % 8 == 0, "KArgs is copied as 8-byte words");
+
+// One batched launch over the members of a batch: member m owns work units
+// [start[m], start[m+1]) (tiles of a sweep, or chunks of `chunk` cells) and
+// its arguments args[m]; persistent CTAs take units from *counter (zero at
+// launch).
+struct BatchK {
+  const KArgs* args;
+  const long long* start;
+  unsigned long long* counter;
+  long long total;   // start[M]
+  long long chunk;   // cells per unit of the CFL and source launches (multiple of 128)
+  int M;
 };
 
 // Sets the message mm_last_error() returns on the calling thread.
@@ -95,3 +109,19 @@ MM_DECLARE_LAUNCHER(mm_p32_d1)
 MM_DECLARE_LAUNCHER(mm_p32_d2)
 MM_DECLARE_LAUNCHER(mm_p32_d3)
 #undef MM_DECLARE_LAUNCHER
+
+// Batched launchers (mm_fp{64,32}_d{1,2,3}_batch.cu): what 0 CFL, 1 sweep
+// along axis with tile variant `variant` (0 or 1; FP64 has one shape), 2
+// sources; two materials (nhist 0 or 1); persistent CTAs, one wave at full
+// occupancy.  name_tiles: tiles of one sweep of a grid of n cells per axis.
+#define MM_DECLARE_BATCH_LAUNCHER(name)                                                     \
+  cudaError_t name(int what, int axis, int variant, int nmat, int nhist, const BatchK& b, \
+                   cudaStream_t s);                                                         \
+  long long name##_tiles(int axis, int variant, const int n[3]);
+MM_DECLARE_BATCH_LAUNCHER(mm_p64_d1_batch)
+MM_DECLARE_BATCH_LAUNCHER(mm_p64_d2_batch)
+MM_DECLARE_BATCH_LAUNCHER(mm_p64_d3_batch)
+MM_DECLARE_BATCH_LAUNCHER(mm_p32_d1_batch)
+MM_DECLARE_BATCH_LAUNCHER(mm_p32_d2_batch)
+MM_DECLARE_BATCH_LAUNCHER(mm_p32_d3_batch)
+#undef MM_DECLARE_BATCH_LAUNCHER

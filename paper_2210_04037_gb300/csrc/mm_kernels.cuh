@@ -172,7 +172,7 @@ __device__ __forceinline__ void store_sources(const KArgs& a, long long idx,
 }
 
 // ------------------------------------------------------------------ sweep ----
-template <class P, int DIM, int AX> struct Tile;
+template <class P, int DIM, int AX, int V = 0> struct Tile;
 // The halo-extended tile (TL + 4) x TW equals the CTA, so each phase is one
 // pass of the threads (phases 2-4 have 2, 3 and 4 fewer rows of items).
 // FP64 (compute bound on GB300's FP64 rate): 64-thread CTAs.
@@ -189,12 +189,22 @@ template <> struct Tile<P32, 2, 1> { static constexpr int TL = 12, TW = 8, NT = 
 template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
 template <> struct Tile<P32, 3, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
 template <> struct Tile<P32, 3, 2> { static constexpr int TL = 12, TW = 8, NT = 128; };
+// Second shape per axis, one of the two the batched sweep's autotuner times
+// (the cell arithmetic does not depend on the tile, so either gives the same
+// bits): longer tiles along the sweep, narrower across it.
+template <class P, int DIM, int AX> struct Tile<P, DIM, AX, 1> : Tile<P, DIM, AX, 0> {};
+template <> struct Tile<P32, 1, 0, 1> { static constexpr int TL = 60, TW = 1, NT = 64; };
+template <> struct Tile<P32, 2, 0, 1> { static constexpr int TL = 60, TW = 2, NT = 128; };
+template <> struct Tile<P32, 2, 1, 1> { static constexpr int TL = 28, TW = 4, NT = 128; };
+template <> struct Tile<P32, 3, 0, 1> { static constexpr int TL = 60, TW = 2, NT = 128; };
+template <> struct Tile<P32, 3, 1, 1> { static constexpr int TL = 28, TW = 4, NT = 128; };
+template <> struct Tile<P32, 3, 2, 1> { static constexpr int TL = 28, TW = 4, NT = 128; };
 
-template <class P, int DIM, int NMAT, int NH, int AX>
+template <class P, int DIM, int NMAT, int NH, int AX, int V = 0>
 struct SweepShape {
   typedef typename P::R R;
-  static constexpr int TL = Tile<P, DIM, AX>::TL, TW = Tile<P, DIM, AX>::TW;
-  static constexpr int NT = Tile<P, DIM, AX>::NT;
+  static constexpr int TL = Tile<P, DIM, AX, V>::TL, TW = Tile<P, DIM, AX, V>::TW;
+  static constexpr int NT = Tile<P, DIM, AX, V>::NT;
   static constexpr int NF = Lay<DIM, NMAT, NH>::NF;
   static constexpr int C1 = NF + AuxRec<P>::N, C2 = NF + AuxRec<P>::N, C3 = NF + 4;
   static constexpr int N1 = (TL + 4) * TW, N2 = (TL + 2) * TW, N3 = (TL + 1) * TW, N4 = TL * TW;
@@ -215,38 +225,39 @@ struct SweepShape {
   }
 };
 
-// One sweep along AX: Uin -> Uout.  Phases over the tile (each a pass of
-// the CTA's threads over its items, separated by barriers):
+// One tile of one sweep along AX: Uin -> Uout.  Phases over the tile (each
+// a pass of the CTA's threads over its items, separated by barriers):
 //   1. load + primitive recovery of the tile cells with a halo of two,
 //   2. van Leer reconstruction + MUSCL-Hancock half step (face states),
 //   3. Riemann problem at each face,
 //   4. conservative update with the non-conservative terms, store.
-template <class P, int DIM, int NMAT, int NH, int AX>
-__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
-    k_sweep(KArgs a) {
+// b: tile index (along AX fastest, then across, then the remaining axis);
+// smem: SH::smem bytes; ok1, ok2: SH::N1, SH::N2 flags.  All threads of the
+// CTA call it together.
+template <class P, int DIM, int NMAT, int NH, int AX, int V>
+__device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigned char* smem,
+                                           unsigned char* ok1, unsigned char* ok2) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
-  typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
+  typedef SweepShape<P, DIM, NMAT, NH, AX, V> SH;
   typedef typename P::X XT;
   constexpr int NF = L::NF, NX = SH::NX, TL = SH::TL, TW = SH::TW, NT = SH::NT;
   constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3;
   constexpr int N1 = SH::N1, N2 = SH::N2, N3 = SH::N3, N4 = SH::N4;
   constexpr int TD = (AX == 0) ? 1 : 0;
-  extern __shared__ __align__(16) unsigned char smem[];
   XT* x1 = reinterpret_cast<XT*>(smem);  // N1 * NX
   XT* x2 = x1 + N1 * NX;                  // 2 * N2 * NX
   XT* x3 = x2 + 2 * N2 * NX;              // N3 * NX
   R* r1 = reinterpret_cast<R*>(x3 + N3 * NX);
   R* r2 = r1 + N1 * C1;
   R* r3 = r2 + 2 * N2 * C2;
-  __shared__ unsigned char ok1[N1], ok2[N2];
 
-  int b = blockIdx.x;
-  const int ta = b % a.tiles[0];
-  b /= a.tiles[0];
-  const int tw = b % a.tiles[1];
-  const int rr = b / a.tiles[1];
+  const int nta = (a.n[AX] + TL - 1) / TL, ntt = (a.n[TD] + TW - 1) / TW;
+  const int ta = int(bt % nta);
+  bt /= nta;
+  const int tw = int(bt % ntt);
+  const int rr = int(bt / ntt);
   const int na = a.n[AX], ntw = a.n[TD];
   const int a0 = ta * TL, w0 = tw * TW;
   const double dt = a.info->dt;
@@ -507,6 +518,56 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT)
       store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
     }
   }
+}
+
+// One CTA per tile of one grid.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep(KArgs a) {
+  typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
+  sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, blockIdx.x, smem, ok1, ok2);
+}
+
+// ------------------------------------------------------------ batches ----
+// Work of a batched launch: member m owns units [start[m], start[m+1]) of
+// the concatenated list; persistent CTAs take units from a counter.
+__device__ __forceinline__ int batch_member(const BatchK& bk, long long u) {
+  int lo = 0, hi = bk.M - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bk.start[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Next unit for the CTA (uniform); ka <- the arguments of its member.
+__device__ __forceinline__ bool batch_next(const BatchK& bk, KArgs& ka, long long& unit,
+                                           long long& s_unit) {
+  __syncthreads();  // the previous unit is finished by every thread
+  if (threadIdx.x == 0) s_unit = (long long)atomicAdd(bk.counter, 1ull);
+  __syncthreads();
+  const long long u = s_unit;
+  if (u >= bk.total) return false;
+  const int m = batch_member(bk, u);
+  unit = u - bk.start[m];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(bk.args + m);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ka);
+  for (int i = threadIdx.x; i < int(sizeof(KArgs) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return true;
+}
+
+// One sweep along AX over the tiles of every member of a batch.
+template <class P, int DIM, int NMAT, int NH, int AX, int V>
+__global__ void __launch_bounds__(Tile<P, DIM, AX, V>::NT) k_sweep_batch(BatchK bk) {
+  typedef SweepShape<P, DIM, NMAT, NH, AX, V> SH;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
+  __shared__ KArgs ka;
+  __shared__ long long s_unit;
+  long long t;
+  while (batch_next(bk, ka, t, s_unit)) sweep_tile<P, DIM, NMAT, NH, AX, V>(ka, t, smem, ok1, ok2);
 }
 
 // ------------------------------------------------------------- sources ----
@@ -895,27 +956,23 @@ __device__ __forceinline__ void src_dequeue(const KArgs& a, SrcQueue<P, DIM, NMA
 // the plastic increment in FP64), then RK4 damage.  Split path: cells
 // inside the yield surface take the short path at once; cells at yield are
 // queued and returned 128 at a time, so the return runs on full warps
-// wherever the yielding cells lie.  The CTA strides over the cells in
-// batches of 128 (uniform trip count: the barriers are reached by all).
+// wherever the yielding cells lie.
+//
+// sources_cells: cells [base, base + 128) of one grid, one per thread of the
+// 128-thread CTA, then the queue drained if it holds a full batch;
+// sources_flush: the rest of the queue.  All threads call both together.
 template <class P, int DIM, int NMAT, int NH>
-__global__ void __launch_bounds__(128) k_sources(KArgs a) {
+__device__ __forceinline__ void sources_cells(
+    const KArgs& a, long long base,
+    typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type& qs, double dt,
+    long long step) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
   typedef typename P::X XT;
   typedef SrcQueue<P, DIM, NMAT, NH> Q;
   constexpr int NF = L::NF, NX = PH::NX;
-  static_assert(Q::NT == 128, "queue batch = CTA size");
-  __shared__ typename std::conditional<P::split, Q, int>::type qs;
-  const double dt = a.info->dt;
-  const long long step = a.info->steps;
-  if constexpr (P::split) {
-    if (threadIdx.x == 0) qs.n = 0;
-    __syncthreads();
-  }
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < a.ncell; base += stride) {
-    const long long cell = base + threadIdx.x;
+  const long long cell = base + threadIdx.x;
     do {
       if (cell >= a.ncell) break;
       R c[NF], w[NF];
@@ -1024,35 +1081,84 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
                                       can_yield, dt, step);
       }
     } while (false);
-    if constexpr (P::split) {
+  if constexpr (P::split) {
+    __syncthreads();
+    const int n = qs.n;
+    if (n >= Q::NT) {
+      src_dequeue<P, DIM, NMAT, NH>(a, qs, n - Q::NT + (int)threadIdx.x, dt, step);
       __syncthreads();
-      const int n = qs.n;
-      if (n >= Q::NT) {
-        src_dequeue<P, DIM, NMAT, NH>(a, qs, n - Q::NT + (int)threadIdx.x, dt, step);
-        __syncthreads();
-        if (threadIdx.x == 0) qs.n = n - Q::NT;
-        __syncthreads();
-      }
+      if (threadIdx.x == 0) qs.n = n - Q::NT;
+      __syncthreads();
     }
   }
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void sources_flush(
+    const KArgs& a,
+    typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type& qs, double dt,
+    long long step) {
   if constexpr (P::split) {
-    // the loop ended on a barrier after the last update of the count
+    // sources_cells ended on a barrier after the last update of the count
     const int n = qs.n;
     if ((int)threadIdx.x < n) src_dequeue<P, DIM, NMAT, NH>(a, qs, (int)threadIdx.x, dt, step);
+    __syncthreads();
+    if (threadIdx.x == 0) qs.n = 0;
+    __syncthreads();
+  }
+}
+
+// One grid: the CTA strides over the cells in batches of 128 (uniform trip
+// count: the barriers are reached by all).
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(128) k_sources(KArgs a) {
+  static_assert(SrcQueue<P, DIM, NMAT, NH>::NT == 128, "queue batch = CTA size");
+  __shared__ typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type qs;
+  const double dt = a.info->dt;
+  const long long step = a.info->steps;
+  if constexpr (P::split) {
+    if (threadIdx.x == 0) qs.n = 0;
+    __syncthreads();
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < a.ncell; base += stride)
+    sources_cells<P, DIM, NMAT, NH>(a, base, qs, dt, step);
+  sources_flush<P, DIM, NMAT, NH>(a, qs, dt, step);
+}
+
+// Every member of a batch: units are chunks of bk.chunk cells (a multiple of
+// 128) of one member; the queue is drained at the end of each chunk.
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(128) k_sources_batch(BatchK bk) {
+  __shared__ typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type qs;
+  __shared__ KArgs ka;
+  __shared__ long long s_unit;
+  if constexpr (P::split) {
+    if (threadIdx.x == 0) qs.n = 0;
+  }
+  long long ch;
+  while (batch_next(bk, ka, ch, s_unit)) {
+    const double dt = ka.info->dt;
+    const long long step = ka.info->steps;
+    const long long b0 = ch * bk.chunk;
+    const long long b1 = b0 + bk.chunk < ka.ncell ? b0 + bk.chunk : ka.ncell;
+    for (long long base = b0; base < b1; base += 128)
+      sources_cells<P, DIM, NMAT, NH>(ka, base, qs, dt, step);
+    sources_flush<P, DIM, NMAT, NH>(ka, qs, dt, step);
   }
 }
 
 // --------------------------------------------------------------- CFL ----
+// Largest max_d |u_d| + c_L over cells begin, begin + stride, ... < end.
 template <class P, int DIM, int NMAT, int NH>
-__global__ void __launch_bounds__(256) k_cfl(KArgs a) {
+__device__ __forceinline__ double cfl_max(const KArgs& a, long long begin, long long end,
+                                          long long stride, long long step) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef typename P::X XT;
   constexpr int NF = Lay<DIM, NMAT, NH>::NF, NX = PH::NX;
-  const long long step = a.info->steps;
   double smax = 0.0;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
-       cell += (long long)gridDim.x * blockDim.x) {
+  for (long long cell = begin; cell < end; cell += stride) {
     R c[NF], w[NF];
     XT cx[NX], wx[NX];
     double eE;
@@ -1068,15 +1174,44 @@ __global__ void __launch_bounds__(256) k_cfl(KArgs a) {
     const double s = double(v + ax.cL);
     smax = s > smax ? s : smax;
   }
+  return smax;
+}
+
+// CTA maximum of a non-negative value into *dst (bits of a double); all
+// threads call it together.
+__device__ __forceinline__ void cta_max_to(unsigned long long* dst, double smax) {
+  __shared__ double red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  __shared__ double red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
-    atomicMax(&a.info->smax_bits, (unsigned long long)__double_as_longlong(m));
+    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_cfl(KArgs a) {
+  const double smax = cfl_max<P, DIM, NMAT, NH>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                                                a.ncell, (long long)gridDim.x * blockDim.x,
+                                                a.info->steps);
+  cta_max_to(&a.info->smax_bits, smax);
+}
+
+// Every member of a batch, in chunks of bk.chunk cells.
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_cfl_batch(BatchK bk) {
+  __shared__ KArgs ka;
+  __shared__ long long s_unit;
+  long long ch;
+  while (batch_next(bk, ka, ch, s_unit)) {
+    const long long b0 = ch * bk.chunk;
+    const long long b1 = b0 + bk.chunk < ka.ncell ? b0 + bk.chunk : ka.ncell;
+    const double smax = cfl_max<P, DIM, NMAT, NH>(ka, b0 + threadIdx.x, b1, blockDim.x,
+                                                  ka.info->steps);
+    cta_max_to(&ka.info->smax_bits, smax);
   }
 }
 

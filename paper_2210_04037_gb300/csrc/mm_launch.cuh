@@ -29,10 +29,8 @@ struct Launch {
       if (e != cudaSuccess) return e;
       attr = true;
     }
-    a.tiles[0] = (a.n[AX] + SH::TL - 1) / SH::TL;
-    a.tiles[1] = (a.n[TD] + SH::TW - 1) / SH::TW;
-    a.tiles[2] = a.n[RD];
-    const long long nb = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
+    const long long nb = (long long)((a.n[AX] + SH::TL - 1) / SH::TL) *
+                         ((a.n[TD] + SH::TW - 1) / SH::TW) * a.n[RD];
     k_sweep<P, DIM, NMAT, NH, AX><<<(unsigned)nb, SH::NT, SH::smem, s>>>(a);
     return cudaGetLastError();
   }
@@ -82,6 +80,81 @@ struct Launch {
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+  }
+
+  // ---- batched launches: persistent CTAs, one wave at full occupancy
+  template <class K>
+  static cudaError_t persistent(K kernel, int threads, size_t smem, BatchK b, cudaStream_t s) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) per = 1;
+    long long grid = (long long)sms * per;
+    if (grid > b.total) grid = b.total;
+    if (grid < 1) return cudaSuccess;
+    kernel<<<(unsigned)grid, threads, smem, s>>>(b);
+    return cudaGetLastError();
+  }
+
+  template <int DIM, int NMAT, int NH, int AX, int V>
+  static cudaError_t sweep_batch(BatchK b, cudaStream_t s) {
+    typedef SweepShape<P, DIM, NMAT, NH, AX, V> SH;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<P, DIM, NMAT, NH, AX, V>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    return persistent(k_sweep_batch<P, DIM, NMAT, NH, AX, V>, SH::NT, SH::smem, b, s);
+  }
+
+  template <int DIM, int NMAT, int NH>
+  static cudaError_t run_batch(int what, int axis, int variant, BatchK b, cudaStream_t s) {
+    if (what == 0) return persistent(k_cfl_batch<P, DIM, NMAT, NH>, 256, 0, b, s);
+    if (what == 2) return persistent(k_sources_batch<P, DIM, NMAT, NH>, 128, 0, b, s);
+    if (what != 1) return cudaErrorInvalidValue;
+#define MM_SWEEP_BATCH(AXIS)                                                     \
+  if (axis == AXIS) {                                                            \
+    if constexpr (P::split)                                                      \
+      if (variant == 1) return sweep_batch<DIM, NMAT, NH, AXIS, 1>(b, s);        \
+    return sweep_batch<DIM, NMAT, NH, AXIS, 0>(b, s);                            \
+  }
+    MM_SWEEP_BATCH(0)
+    if constexpr (DIM >= 2) { MM_SWEEP_BATCH(1) }
+    if constexpr (DIM >= 3) { MM_SWEEP_BATCH(2) }
+#undef MM_SWEEP_BATCH
+    return cudaErrorInvalidValue;
+  }
+
+  template <int DIM>
+  static cudaError_t by_mat_batch(int what, int axis, int variant, int nmat, int nhist, BatchK b,
+                                  cudaStream_t s) {
+    if (!P::split) variant = 0;  // one FP64 tile shape
+    if (nmat == 2 && nhist == 0) return run_batch<DIM, 2, 0>(what, axis, variant, b, s);
+    if (nmat == 2 && nhist == 1) return run_batch<DIM, 2, 1>(what, axis, variant, b, s);
+    return cudaErrorInvalidValue;
+  }
+
+  // Tiles of one sweep of a grid with n cells per axis (the tile shape does
+  // not depend on the materials).
+  template <int DIM>
+  static long long tiles(int axis, int variant, const int n[3]) {
+    int TL = 0, TW = 0;
+#define MM_TILE_OF(AXIS)                                                                  \
+  if (axis == AXIS) {                                                                     \
+    TL = variant == 0 ? Tile<P, DIM, AXIS, 0>::TL : Tile<P, DIM, AXIS, 1>::TL;            \
+    TW = variant == 0 ? Tile<P, DIM, AXIS, 0>::TW : Tile<P, DIM, AXIS, 1>::TW;            \
+  }
+    MM_TILE_OF(0)
+    if constexpr (DIM >= 2) { MM_TILE_OF(1) }
+    if constexpr (DIM >= 3) { MM_TILE_OF(2) }
+#undef MM_TILE_OF
+    if (TL == 0) return 0;
+    const int TD = axis == 0 ? 1 : 0, RD = 3 - axis - TD;
+    return (long long)((n[axis] + TL - 1) / TL) * ((n[TD] + TW - 1) / TW) * n[RD];
   }
 
   template <int DIM>

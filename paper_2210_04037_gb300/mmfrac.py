@@ -67,7 +67,9 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async", "mm
            "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
-           "mm_conserved_totals_noalloc")
+           "mm_conserved_totals_noalloc", "mm_batch_create", "mm_batch_set_options",
+           "mm_batch_step", "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
+           "mm_batch_profile_enable", "mm_batch_profile_read")
 KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources")
 
 _lock = threading.Lock()
@@ -89,6 +91,15 @@ def load(path: str = LIB_PATH):
         lib.mm_set_materials.argtypes = [vp, P(Material), ctypes.c_int, P(Init)]
         lib.mm_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(StepInfo)]
         lib.mm_step_async.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        lib.mm_batch_create.argtypes = [P(vp), ctypes.c_int, vp, P(vp)]
+        lib.mm_batch_set_options.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        lib.mm_batch_step.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        lib.mm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        lib.mm_batch_synchronize.argtypes = [vp]
+        lib.mm_batch_destroy.argtypes = [vp]
+        lib.mm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
+        lib.mm_batch_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64),
+                                              ctypes.c_int, ctypes.c_int]
         lib.mm_synchronize.argtypes = [vp, P(StepInfo)]
         lib.mm_read_fields.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double),
                                        ctypes.c_size_t]
@@ -109,7 +120,10 @@ def load(path: str = LIB_PATH):
                                                     ctypes.c_int, P(ctypes.c_double), vp, vp]
         lib.mm_conserved_totals_noalloc.restype = ctypes.c_int
         for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async",
-                   "mm_synchronize", "mm_read_fields", "mm_conserved_totals", "mm_destroy"):
+                   "mm_synchronize", "mm_read_fields", "mm_conserved_totals", "mm_destroy",
+                   "mm_batch_create", "mm_batch_set_options", "mm_batch_step",
+                   "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
+                   "mm_batch_profile_enable", "mm_batch_profile_read"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -277,6 +291,63 @@ class Grid:
     def close(self) -> None:
         if getattr(self, "h", None):
             destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Grids stepped together (``mm_batch_*``): one launch per kernel kind
+    over every member, each member with its own dt; the grids are
+    referenced, not owned, and must outlive the batch."""
+
+    def __init__(self, grids, stream=None, use_graph: bool = True, cfl: float | None = None):
+        lib = load()
+        self.grids = list(grids)
+        self.cfl = cfl if cfl is not None else self.grids[0].case.cfl
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(lib.mm_batch_create(arr, len(self.grids), stream, ctypes.byref(h)))
+        self.h = h
+        if not use_graph:
+            self.set_options(use_graph=False)
+
+    def set_options(self, use_graph: bool = True, tile_variant=None) -> None:
+        tv = None if tile_variant is None else (ctypes.c_int * 3)(*tile_variant)
+        _check(load().mm_batch_set_options(self.h, 1 if use_graph else 0, tv))
+
+    def step_async(self, n_steps: int, cfl: float | None = None) -> None:
+        _check(load().mm_batch_step(self.h, int(n_steps), float(self.cfl if cfl is None else cfl)))
+
+    def synchronize(self) -> None:
+        _check(load().mm_batch_synchronize(self.h))
+
+    def step(self, n_steps: int, cfl: float | None = None) -> None:
+        self.step_async(n_steps, cfl)
+        self.synchronize()
+
+    def autotune(self, reps: int = 3):
+        out = (ctypes.c_int * 3)()
+        _check(load().mm_batch_autotune(self.h, int(reps), out))
+        return list(out)
+
+    def profile_enable(self, on: bool = True) -> None:
+        _check(load().mm_batch_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        n = len(KERNEL_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(load().mm_batch_profile_read(self.h, ms, cnt, n, 1 if reset else 0))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().mm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

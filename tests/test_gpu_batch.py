@@ -1,0 +1,113 @@
+"""Batched ensembles through the C ABI: every member of a batch ends in the
+same state (bitwise) and at the same time as the same grid stepped alone, in
+FP64 and FP32-split, whatever the tile shapes, with or without graph replay;
+autotuning leaves the states as they are."""
+import numpy as np
+import pytest
+
+import cases
+from paper_2210_04037_gb300 import mmfrac, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(case, prec, steps, chunks=1):
+    g = mmfrac.Grid(case, prec)
+    for _ in range(chunks):
+        g.step(steps)
+    info = g.synchronize()
+    u = g.read(False)
+    g.close()
+    return u, info
+
+
+def batched(cases_, prec, steps, chunks=1, **opts):
+    grids = [mmfrac.Grid(c, prec) for c in cases_]
+    b = mmfrac.Batch(grids)
+    if opts:
+        b.set_options(**opts)
+    for _ in range(chunks):
+        b.step(steps)
+    out = [(g.read(False), g.synchronize()) for g in grids]
+    b.close()
+    for g in grids:
+        g.close()
+    return out
+
+
+def check_equal(cases_, prec, steps, chunks=1, **opts):
+    got = batched(cases_, prec, steps, chunks, **opts)
+    for c, (u, info) in zip(cases_, got):
+        ref, rinfo = alone(c, prec, steps, chunks)
+        assert np.array_equal(u, ref), c.name
+        assert info == rinfo, c.name
+
+
+@pytest.mark.parametrize("prec", [mmfrac.FP64, mmfrac.FP32_SPLIT])
+def test_ring_members_equal_single_runs(prec):
+    # uneven sizes, one seeded perturbation field each
+    members = [W.ring_2d(n, seed=10 + i) for i, n in enumerate((40, 56, 72, 48))]
+    check_equal(members, prec, 9, chunks=2)
+
+
+@pytest.mark.parametrize("prec", [mmfrac.FP64, mmfrac.FP32_SPLIT])
+def test_3d_members_equal_single_runs(prec):
+    # odd step counts: the members' ping-pong buffers swap parity each step
+    members = [W.cylinder_3d(n, nz=10, width=0.048, seed=20 + n) for n in (20, 24)]
+    check_equal(members, prec, 3, chunks=2)
+
+
+def test_1d_members_equal_single_runs():
+    members = [W.spall_1d(n) for n in (300, 500)]
+    check_equal(members, mmfrac.FP32_SPLIT, 20)
+
+
+def test_tile_shapes_and_graphs_do_not_change_results():
+    members = [W.ring_2d(n, seed=30 + n) for n in (44, 60)]
+    base = batched(members, mmfrac.FP32_SPLIT, 8)
+    for opts in (dict(use_graph=False, tile_variant=[1, 1, 0]),
+                 dict(use_graph=True, tile_variant=[0, 1, 0]),
+                 dict(use_graph=True, tile_variant=[1, 0, 0])):
+        got = batched(members, mmfrac.FP32_SPLIT, 8, **opts)
+        for (u, i), (v, j) in zip(base, got):
+            assert np.array_equal(u, v), opts
+            assert i == j
+
+
+def test_autotune_leaves_the_states_unchanged():
+    grids = [mmfrac.Grid(W.ring_2d(n, seed=40 + n), mmfrac.FP32_SPLIT) for n in (36, 52)]
+    for g in grids:
+        g.step(3)
+    before = [g.read(False) for g in grids]
+    b = mmfrac.Batch(grids)
+    chosen = b.autotune(reps=2)
+    assert all(v in (0, 1) for v in chosen)
+    after = [g.read(False) for g in grids]
+    for u, v in zip(before, after):
+        assert np.array_equal(u, v)
+    b.step(4)
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_batch_argument_errors():
+    g2 = mmfrac.Grid(W.ring_2d(32), mmfrac.FP32_SPLIT)
+    g1 = mmfrac.Grid(W.spall_1d(64), mmfrac.FP32_SPLIT)
+    g64 = mmfrac.Grid(W.ring_2d(32), mmfrac.FP64)
+    gas = mmfrac.Grid(cases.gas_riemann(64, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)),
+                      mmfrac.FP32_SPLIT)
+    for bad in ([g2, g1], [g2, g64], [g2, g2], [gas]):
+        with pytest.raises(mmfrac.MMError) as e:
+            mmfrac.Batch(bad)
+        assert e.value.status == mmfrac.MM_EINVAL
+    b = mmfrac.Batch([g2])
+    with pytest.raises(mmfrac.MMError) as e:
+        b.step(1, cfl=1.5)
+    assert e.value.status == mmfrac.MM_EINVAL
+    with pytest.raises(mmfrac.MMError) as e:
+        b.set_options(tile_variant=[2, 0, 0])
+    assert e.value.status == mmfrac.MM_EINVAL
+    b.close()
+    for g in (g2, g1, g64, gas):
+        g.close()
