@@ -39,7 +39,8 @@ from paper_2210_04037_gb300 import workloads as W  # noqa: E402
 
 METRIC = ("cell-updates/s and % HBM roofline at 1 GB300, FP32-split vs FP64 at stated error")
 L2_BYTES = 129 * 2 ** 20
-DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000, "ensemble_2d": 64}
+DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000, "ensemble_2d": 64,
+                "serve": 24}
 WORKLOAD_TEXT = {
     "ring_2d": "2D expanding ring, {n}x{n} cells, Al-H32 annulus r 20-24 mm at 200 m/s in air, "
                "simple damage, phi0 ~ U(0.9,1.1) on a 0.5 mm lattice",
@@ -50,7 +51,35 @@ WORKLOAD_TEXT = {
     "ensemble_2d": "batched ensemble: {n} seeded 2D expanding rings (the ring workload, seeds "
                    "100..), grids uneven 128^2..768^2 in steps of 8, stepped together: one launch "
                    "per kernel kind over all members, CUDA graph replay, autotuned tile shapes",
+    "serve": "served runs: {n} requests with Poisson arrivals (16/s, seeded) mixing 1D spall "
+             "(1e3..1e4 cells, 400 steps), 2D ring (256^2..1024^2, 60 steps) and 3D cylinder "
+             "(128^3..256^3, 10 steps), FP32-split, memory-based admission, continuous batching",
 }
+
+
+def serve_requests(count: int, seed: int = 7, rate: float = 16.0):
+    """(kind, size, steps, arrival time in s) of each request: seeded."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for i in range(count):
+        kind = rng.choice(["1d", "2d", "3d"], p=[0.35, 0.45, 0.2])
+        if kind == "1d":
+            n, steps = int(rng.integers(1000, 10001)), 400
+        elif kind == "2d":
+            n, steps = int(rng.choice([256, 384, 512, 640, 768, 1024])), 60
+        else:
+            n, steps = int(rng.choice([128, 160, 192, 256], p=[0.4, 0.3, 0.2, 0.1])), 10
+        out.append((str(kind), n, steps, t))
+        t += float(rng.exponential(1.0 / rate))
+    return out
+
+
+def serve_case(kind: str, n: int, seed: int):
+    if kind == "1d":
+        return W.spall_1d(n)
+    if kind == "2d":
+        return W.ring_2d(n, seed=seed)
+    return W.cylinder_3d(n, seed=seed)
 
 
 def ensemble_sizes(m: int):
@@ -66,6 +95,9 @@ def make_case(name: str, n: int):
     if name == "ensemble_2d":
         # the oracle's sample of an ensemble: its smallest member
         return ensemble_cases(n)[0]
+    if name == "serve":
+        # the oracle's sample of the served mix: its smallest 2D ring
+        return W.ring_2d(256)
     return W.WORKLOADS[name](n)
 
 
@@ -360,11 +392,79 @@ def run_ensemble(args, rank: int, world: int):
         dist.destroy_process_group()
 
 
+def run_serve(args, rank: int, world: int):
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    count = args.size or DEFAULT_SIZE["serve"]
+    reqs = serve_requests(count, seed=7 + rank)
+    cases = [serve_case(k, n, 200 + i) for i, (k, n, _, _) in enumerate(reqs)]
+    work = [c.ncell * st for c, (_, _, st, _) in zip(cases, reqs)]
+    srv = mmfrac.Server(steps_per_tick=8)
+    # warm-up: one small run of each dimension (first launches, graph capture)
+    for c in (W.spall_1d(1000), W.ring_2d(128), W.cylinder_3d(32)):
+        srv.wait(srv.submit(c, 4), timeout=600)
+    ids = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for c, (_, _, st, ta) in zip(cases, reqs):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(c, st))
+        infos = [srv.wait(rid, timeout=1800)[0] for rid in ids]
+    srv.close()
+    lat = np.array([i["done_s"] - i["submit_s"] for i in infos])
+    span = max(i["done_s"] for i in infos) - min(i["submit_s"] for i in infos)
+    value = sum(work) / span
+    # one at a time, first come first served: each run's service time alone
+    # (create, upload, steps, read back), replayed against the same arrivals
+    service = []
+    for c, (_, _, st, _) in zip(cases, reqs):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g = mmfrac.Grid(c, W.FP32_SPLIT)
+        g.step_async(st)
+        g.read()
+        g.close()
+        service.append(time.perf_counter() - t1)
+    arrive = [i["submit_s"] for i in infos]
+    finish, fifo_lat = 0.0, []
+    for a, sv in zip(arrive, service):
+        finish = max(finish, a) + sv
+        fifo_lat.append(finish - a)
+    fifo_span = finish - min(arrive)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": count, "warmup": 3, "ms_per_step": 1e3 * span / count,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["serve"].format(n=count), "requests": count,
+                   "mix": {k: sum(1 for r in reqs if r[0] == k) for k in ("1d", "2d", "3d")},
+                   "precision": "fp32split", "steps_per_tick": 8,
+                   "note": "steps = requests; ms_per_step = makespan per request",
+                   "parallelism": f"replicas x{world}"},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "makespan_s": span,
+        "one_at_a_time_fifo": {"value": sum(work) / fifo_span, "makespan_s": fifo_span,
+                               "p50": float(np.percentile(fifo_lat, 50)),
+                               "p99": float(np.percentile(fifo_lat, 99))},
+        "roofline": None,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     from paper_2210_04037_gb300 import mmfrac
     if args.workload == "ensemble_2d":
         return run_ensemble(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None

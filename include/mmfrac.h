@@ -45,7 +45,7 @@ typedef enum {
                          c_L^2 <= 0 or a non-finite value) */
   MM_ENOCONV = -5,    /* the plastic return did not converge */
   MM_EDT = -6,        /* non-positive or non-finite time step */
-  MM_ETIMEOUT = -7,   /* reserved */
+  MM_ETIMEOUT = -7,   /* a bounded wait ended before the work finished */
   MM_ESTATE = -8      /* call out of order (e.g. step before set_materials) */
 } mm_status;
 
@@ -191,6 +191,65 @@ mm_status mm_batch_profile_read(mm_batch* b, double* ms, int64_t* counts, int n,
 
 /* Wait for the batch's work and free the batch (not its grids). */
 mm_status mm_batch_destroy(mm_batch* b);
+
+/* ---- Served runs (continuous batching).  A server owns a scheduler thread
+ * that admits submitted runs first come, first served while the device
+ * memory they need fits its budget, steps all admitted runs together (one
+ * batch per group of runs with the same dimension, precision, material
+ * layout and CFL number, the groups on separate streams), and retires each
+ * run when it has done its steps: its primitive fields go to host memory and
+ * its device memory is freed, which admits the next runs.  Runs submitted
+ * while others are on the GPU join them at the next tick (every
+ * steps_per_tick steps).  A run's result is the same as that of the same
+ * grid stepped alone with mm_step. */
+typedef struct mm_server mm_server;
+
+typedef struct {
+  int64_t id;
+  int32_t status;      /* mm_status of the run */
+  int32_t nfield;      /* the result holds nfield x ncell doubles */
+  int64_t ncell;
+  int64_t steps_done;
+  double t;            /* simulated time reached */
+  double submit_s, admit_s, done_s;  /* seconds since the server was created */
+} mm_run_info;
+
+typedef struct {
+  uint64_t budget_bytes, used_bytes;
+  int64_t pending, admitted, retired;
+} mm_server_info;
+
+/* Create a server on the current device.  memory_budget: device bytes its
+ * runs may hold at once (0: 90 % of the free memory now); steps_per_tick:
+ * steps between admissions (<= 0: 8).  Errors: MM_EINVAL, MM_ECUDA. */
+mm_status mm_server_create(size_t memory_budget, int steps_per_tick, mm_server** out);
+
+/* Queue a run of n_steps steps at the given CFL number on the grid desc
+ * with the materials and initial state given (as for mm_create_grid and
+ * mm_set_materials; all host data are copied before the call returns).
+ * Two materials.  *id receives the run's id.  Errors: MM_EINVAL (arguments,
+ * or a run larger than the memory budget), MM_ESTATE (server shutting
+ * down).  Errors of the run itself are returned by mm_server_wait. */
+mm_status mm_server_submit(mm_server* s, const mm_grid_desc* desc, const mm_material* mats,
+                           int n_mat, const mm_init* init, int n_steps, double cfl,
+                           int64_t* id);
+
+/* Wait up to timeout_ms (< 0: without limit) for run id.  On MM_ETIMEOUT
+ * nothing changes.  When the run has finished, info (may be NULL) is filled;
+ * a failed run returns its error and is released; a successful run copies
+ * its primitive fields ([nfield][ncell], as mm_read_fields) to host_dst and
+ * is released, or, with host_dst NULL, only fills info and stays available.
+ * Errors: MM_EINVAL (unknown id, destination too small), MM_ETIMEOUT, the
+ * run's own error. */
+mm_status mm_server_wait(mm_server* s, int64_t id, int timeout_ms, mm_run_info* info,
+                         double* host_dst, size_t dst_len);
+
+/* Memory budget and use, and run counts.  Errors: MM_EINVAL. */
+mm_status mm_server_stats(mm_server* s, mm_server_info* info);
+
+/* Stop admitting, finish the admitted runs, cancel the queued ones (their
+ * wait returns MM_ESTATE), join the scheduler and free the server. */
+mm_status mm_server_destroy(mm_server* s);
 
 /* Conserved totals sum_cells dV (phi rho)_l (N values), sum dV rho u
  * (3 values, 0 for k >= dim), sum dV rho E: N + 4 doubles, accumulated in

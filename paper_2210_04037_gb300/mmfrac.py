@@ -58,6 +58,19 @@ class Init(ctypes.Structure):
                 ("phi0_h", ctypes.c_double * 3)]
 
 
+class RunInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("nfield", ctypes.c_int32),
+                ("ncell", ctypes.c_int64), ("steps_done", ctypes.c_int64), ("t", ctypes.c_double),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64),
+                ("pending", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("retired", ctypes.c_int64)]
+
+
 class StepInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("smax", ctypes.c_double),
                 ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
@@ -69,7 +82,8 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async", "mm
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
            "mm_conserved_totals_noalloc", "mm_batch_create", "mm_batch_set_options",
            "mm_batch_step", "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
-           "mm_batch_profile_enable", "mm_batch_profile_read")
+           "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
+           "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy")
 KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources")
 
 _lock = threading.Lock()
@@ -98,6 +112,13 @@ def load(path: str = LIB_PATH):
         lib.mm_batch_synchronize.argtypes = [vp]
         lib.mm_batch_destroy.argtypes = [vp]
         lib.mm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
+        lib.mm_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, P(vp)]
+        lib.mm_server_submit.argtypes = [vp, P(GridDesc), P(Material), ctypes.c_int, P(Init),
+                                         ctypes.c_int, ctypes.c_double, P(ctypes.c_int64)]
+        lib.mm_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_int, P(RunInfo),
+                                       P(ctypes.c_double), ctypes.c_size_t]
+        lib.mm_server_stats.argtypes = [vp, P(ServerInfo)]
+        lib.mm_server_destroy.argtypes = [vp]
         lib.mm_batch_profile_read.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int64),
                                               ctypes.c_int, ctypes.c_int]
         lib.mm_synchronize.argtypes = [vp, P(StepInfo)]
@@ -123,7 +144,8 @@ def load(path: str = LIB_PATH):
                    "mm_synchronize", "mm_read_fields", "mm_conserved_totals", "mm_destroy",
                    "mm_batch_create", "mm_batch_set_options", "mm_batch_step",
                    "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
-                   "mm_batch_profile_enable", "mm_batch_profile_read"):
+                   "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
+                   "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -149,7 +171,7 @@ def material_struct(m) -> Material:
     return s
 
 
-def create_grid(case, precision: int = FP64, stream=None) -> ctypes.c_void_p:
+def _desc(case, precision: int) -> GridDesc:
     d = GridDesc()
     d.dim = case.dim
     for k in range(3):
@@ -160,12 +182,19 @@ def create_grid(case, precision: int = FP64, stream=None) -> ctypes.c_void_p:
         d.bc[k][1] = int(case.bc[2 * k + 1]) if k < case.dim else 0
     d.precision = int(precision)
     d.n_materials = len(case.materials)
+    return d
+
+
+def create_grid(case, precision: int = FP64, stream=None) -> ctypes.c_void_p:
+    d = _desc(case, precision)
     h = ctypes.c_void_p()
     _check(load().mm_create_grid(ctypes.byref(d), stream, ctypes.byref(h)))
     return h
 
 
-def set_materials(grid, case, prim: np.ndarray | None = None) -> None:
+def _init(case, prim: np.ndarray | None = None):
+    """Materials and initial-state structs of a case, with the arrays they
+    point into (kept alive by the caller for the call)."""
     mats = (Material * len(case.materials))(*[material_struct(m) for m in case.materials])
     prim = np.ascontiguousarray(case.prim if prim is None else prim, dtype=np.float64)
     init = Init()
@@ -179,6 +208,11 @@ def set_materials(grid, case, prim: np.ndarray | None = None) -> None:
             init.phi0_n[k] = int(case.pn[k])
             init.phi0_lo[k] = float(case.plo[k])
             init.phi0_h[k] = float(case.ph[k])
+    return mats, init, keep
+
+
+def set_materials(grid, case, prim: np.ndarray | None = None) -> None:
+    mats, init, keep = _init(case, prim)
     _check(load().mm_set_materials(grid, mats, len(case.materials), ctypes.byref(init)))
 
 
@@ -348,6 +382,55 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "h", None):
             load().mm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Served runs with continuous batching (``mm_server_*``): runs are
+    admitted while their device memory fits the budget, stepped together
+    with the runs already on the GPU, and retired with their primitive
+    fields copied to the host."""
+
+    def __init__(self, memory_budget: int = 0, steps_per_tick: int = 8):
+        h = ctypes.c_void_p()
+        _check(load().mm_server_create(int(memory_budget), int(steps_per_tick), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, case, n_steps: int, precision: int = FP32_SPLIT,
+               cfl: float | None = None) -> int:
+        d = _desc(case, precision)
+        mats, init, keep = _init(case)
+        rid = ctypes.c_int64()
+        _check(load().mm_server_submit(self.h, ctypes.byref(d), mats, len(case.materials),
+                                       ctypes.byref(init), int(n_steps),
+                                       float(case.cfl if cfl is None else cfl), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout: float | None = None):
+        """(info, primitive fields [nfield][ncell]) of run rid; raises MMError
+        (status MM_ETIMEOUT) if it has not finished within timeout seconds."""
+        lib = load()
+        info = RunInfo()
+        ms = -1 if timeout is None else max(0, int(timeout * 1000))
+        _check(lib.mm_server_wait(self.h, int(rid), ms, ctypes.byref(info), None, 0))
+        out = np.empty((info.nfield, info.ncell))
+        _check(lib.mm_server_wait(self.h, int(rid), 0, ctypes.byref(info), _dptr(out), out.size))
+        return {k: getattr(info, k) for k, _ in RunInfo._fields_}, out
+
+    def stats(self) -> dict:
+        st = ServerInfo()
+        _check(load().mm_server_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerInfo._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().mm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

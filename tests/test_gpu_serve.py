@@ -1,0 +1,85 @@
+"""Served runs with continuous batching through the C ABI: a run's result is
+the same (bit for bit) as the same grid stepped alone, whatever was served
+beside it; admission follows the memory budget; bounded waits time out."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2210_04037_gb300 import mmfrac, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(case, steps, prec=mmfrac.FP32_SPLIT):
+    g = mmfrac.Grid(case, prec)
+    info = g.step(steps)
+    out = g.read()
+    g.close()
+    return out, info
+
+
+def test_served_mix_equals_runs_alone():
+    runs = [(W.ring_2d(48, seed=3), 12), (W.spall_1d(300), 30),
+            (W.cylinder_3d(16, nz=10, width=0.048, seed=5), 5)]
+    late = [(W.ring_2d(40, seed=7), 9), (W.spall_1d(200), 17),
+            (W.cylinder_3d(18, nz=8, width=0.048, seed=6), 6)]
+    srv = mmfrac.Server(steps_per_tick=4)
+    ids = [srv.submit(c, n) for c, n in runs]
+    time.sleep(0.02)  # the later runs arrive while the first ones are on the GPU
+    ids += [srv.submit(c, n) for c, n in late]
+    for rid, (case, n) in zip(ids, runs + late):
+        info, out = srv.wait(rid, timeout=120)
+        ref, rinfo = alone(case, n)
+        assert info["status"] == mmfrac.MM_OK
+        assert info["steps_done"] == n
+        assert info["t"] == rinfo["t"]
+        assert info["submit_s"] <= info["admit_s"] <= info["done_s"]
+        assert np.array_equal(out, ref), case.name
+    st = srv.stats()
+    assert st["used_bytes"] == 0 and st["pending"] == 0
+    assert st["admitted"] == st["retired"] == len(ids)
+    srv.close()
+
+
+def test_memory_budget_serves_one_run_at_a_time():
+    cases = [W.ring_2d(40, seed=11), W.ring_2d(40, seed=12), W.ring_2d(40, seed=13)]
+    srv = mmfrac.Server(memory_budget=2_000_000, steps_per_tick=4)
+    ids = [srv.submit(c, 8) for c in cases]
+    infos = []
+    for rid, case in zip(ids, cases):
+        info, out = srv.wait(rid, timeout=120)
+        infos.append(info)
+        assert np.array_equal(out, alone(case, 8)[0])
+    for a, b in zip(infos, infos[1:]):
+        assert b["admit_s"] >= a["done_s"]
+    with pytest.raises(mmfrac.MMError) as e:
+        srv.submit(W.ring_2d(256), 4)
+    assert e.value.status == mmfrac.MM_EINVAL
+    srv.close()
+
+
+def test_bounded_wait_times_out_then_completes():
+    srv = mmfrac.Server(steps_per_tick=2)
+    case = W.ring_2d(96, seed=21)
+    rid = srv.submit(case, 200)
+    with pytest.raises(mmfrac.MMError) as e:
+        srv.wait(rid, timeout=0)
+    assert e.value.status == mmfrac.MM_ETIMEOUT
+    info, out = srv.wait(rid, timeout=300)
+    assert info["steps_done"] == 200
+    with pytest.raises(mmfrac.MMError) as e:
+        srv.wait(rid, timeout=0)  # already collected
+    assert e.value.status == mmfrac.MM_EINVAL
+    srv.close()
+
+
+def test_submit_argument_errors():
+    srv = mmfrac.Server()
+    with pytest.raises(mmfrac.MMError) as e:
+        srv.submit(W.ring_2d(32), -1)
+    assert e.value.status == mmfrac.MM_EINVAL
+    with pytest.raises(mmfrac.MMError) as e:
+        srv.submit(W.ring_2d(32), 4, cfl=0.0)
+    assert e.value.status == mmfrac.MM_EINVAL
+    srv.close()
