@@ -50,6 +50,7 @@ struct DevInfo {
   double t, dt, smax, pad;
   long long steps;
   unsigned long long smax_bits;  // running max of the signal speed (bits of a >= 0 double)
+  double lam[3];                 // dt / dx_k of the step (0 for an axis the grid lacks)
 };
 
 // Everything a kernel needs, passed by value.

@@ -260,9 +260,8 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigne
   const int rr = int(bt / ntt);
   const int na = a.n[AX], ntw = a.n[TD];
   const int a0 = ta * TL, w0 = tw * TW;
-  const double dt = a.info->dt;
   const long long step = a.info->steps;
-  const R lam = R(dt / a.dx[AX]);
+  const R lam = R(a.info->lam[AX]);  // dt / dx_AX of the step
 
   // 1. primitive recovery of every tile cell, halo of two included
   for (int it = threadIdx.x; it < N1; it += NT) {
