@@ -22,6 +22,7 @@ oracle on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -89,6 +90,32 @@ def ensemble_sizes(m: int):
 
 def ensemble_cases(m: int):
     return [W.ring_2d(n, seed=100 + i) for i, n in enumerate(ensemble_sizes(m))]
+
+
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2) per
+# launch of the bench's kernels at their default size, with the SHA-256 of the
+# kernel sources and build script they were measured on; reported as null
+# once those differ (profiles/traffic_ring2d_512_fp32split.md).
+TRAFFIC_SRC_SHA256 = "648345bb610e7a41085f9adebc75b37615ac4f086a82deb1f719cd760376bd26"
+TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892864, "sweep_y": 17915392,
+                                           "sources": 18494464}}
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2210_04037_gb300", "csrc")
+    for f in sorted(os.listdir(cs)) + ["../build.py"]:
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, n: int, precision: str, kernel: str):
+    t = TRAFFIC.get((workload, n, precision), {}).get(kernel)
+    if t is None or kernel_src_hash() != TRAFFIC_SRC_SHA256:
+        return None
+    return t
 
 
 def make_case(name: str, n: int):
@@ -555,8 +582,8 @@ def run_gpu(args, rank: int, world: int):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": algo,
-                     "avg_launch_ms": dom_ms},
+                     "traffic": measured_traffic(args.workload, n, args.precision, dom),
+                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": dom_ms},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
         "ms_per_step_with_kernel_events": ms_k / args.steps,
         "e2e": {"value": world * case.ncell * args.steps / e2e_s, "unit": "cell-updates/s",
