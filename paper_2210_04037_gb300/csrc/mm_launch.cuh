@@ -2,6 +2,8 @@
 // materials) triple to the kernel instantiations of one precision policy.
 #pragma once
 
+#include <atomic>
+
 #include "mm_kernels.cuh"
 
 namespace mm {
@@ -15,6 +17,23 @@ inline int grid_for(long long n, int threads) {
   return (int)b;
 }
 
+// Opt a kernel in to `smem` bytes of dynamic shared memory once per device
+// and kernel (a bit per device, set after the call: threads that race both
+// make the same call).  The kernel is a template argument so that every
+// kernel has its own flags (kernels of one signature share a pointer type).
+template <auto Kernel>
+cudaError_t smem_attr(size_t smem) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
 template <class P>
 struct Launch {
   template <int DIM, int NMAT, int NH, int AX>
@@ -22,13 +41,8 @@ struct Launch {
     typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
     constexpr int TD = (AX == 0) ? 1 : 0;
     constexpr int RD = 3 - AX - TD;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_sweep<P, DIM, NMAT, NH, AX>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    cudaError_t e = smem_attr<k_sweep<P, DIM, NMAT, NH, AX>>(SH::smem);
+    if (e != cudaSuccess) return e;
     const long long nb = (long long)((a.n[AX] + SH::TL - 1) / SH::TL) *
                          ((a.n[TD] + SH::TW - 1) / SH::TW) * a.n[RD];
     k_sweep<P, DIM, NMAT, NH, AX><<<(unsigned)nb, SH::NT, SH::smem, s>>>(a);
@@ -101,13 +115,8 @@ struct Launch {
   template <int DIM, int NMAT, int NH, int AX, int V>
   static cudaError_t sweep_batch(BatchK b, cudaStream_t s) {
     typedef SweepShape<P, DIM, NMAT, NH, AX, V> SH;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<P, DIM, NMAT, NH, AX, V>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    cudaError_t e = smem_attr<k_sweep_batch<P, DIM, NMAT, NH, AX, V>>(SH::smem);
+    if (e != cudaSuccess) return e;
     return persistent(k_sweep_batch<P, DIM, NMAT, NH, AX, V>, SH::NT, SH::smem, b, s);
   }
 
