@@ -115,7 +115,10 @@ mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** 
 mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_init* init);
 
 /* Advance n_steps explicit steps with dt = cfl * min_k dx_k / max_cells
- * (max_k |u_k| + c_L), each step = sweeps x, y, z then the sources.
+ * (max_k |u_k| + c_L), each step = sweeps x, y, z then the sources.  After
+ * the first step on a state, steps are replayed from a captured CUDA graph
+ * (the same kernels; launch by launch while kernel timing is on, or on a
+ * stream that cannot be captured).  Calls on one grid must not overlap.
  * info (may be NULL) receives time, last dt, last signal speed, steps done
  * and the first bad cell.  On MM_ENONFINITE / MM_ENOCONV the state after
  * the failing step is undefined.  Errors: MM_ESTATE (no materials yet),
