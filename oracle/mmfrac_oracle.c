@@ -49,6 +49,7 @@ struct or_grid {
   double plo[3], ph[3];
   double t, dt_last, smax;
   long steps, bad_cell;
+  int xscheme; /* 0: X carried by the sweeps (R20); 1: WENO3 + RK3 (R28) */
 };
 
 /* Derived quantities of one state that the flux and the Riemann solver use. */
@@ -658,6 +659,128 @@ static int sweep(or_grid* g, int d, double dt) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Lagrangian coordinates by third-order WENO and three-stage RK (Sec.      */
+/* 3.2.1), the alternative to carrying X in the sweeps (R28):               */
+/*   dX/dt = -sum_d [u_{d,i+1/2} (X_{i+1/2} - X_i)                          */
+/*                   - u_{d,i-1/2} (X_{i-1/2} - X_i)] / dx_d,                */
+/* the difference of the fluxes X u_d plus X div(u), so that DX/Dt = 0.     */
+/* Face velocity: mean of the two cell velocities.  Face value of X: the    */
+/* WENO3 value reconstructed in the upwind cell.  Time: Shu and Osher's     */
+/* three-stage TVD Runge-Kutta scheme with the velocities of the step's     */
+/* start.  Ghost cells follow the rules of the sweeps.                       */
+/* ------------------------------------------------------------------------ */
+
+/* WENO3 value at the face between cells b and c, reconstructed in cell b
+   from its neighbours a (away from the face) and c (across it): candidates
+   -a/2 + 3b/2 and (b + c)/2, linear weights 1/3 and 2/3, smoothness
+   ((b - a)/dx)^2 and ((c - b)/dx)^2, eps = 1e-6 (Jiang and Shu). */
+static double weno3_face(double a, double b, double c, double dx) {
+  const double q0 = -0.5 * a + 1.5 * b;
+  const double q1 = 0.5 * b + 0.5 * c;
+  const double s0 = (b - a) / dx, s1 = (c - b) / dx;
+  const double e0 = 1e-6 + s0 * s0, e1 = 1e-6 + s1 * s1;
+  const double a0 = (1.0 / 3.0) / (e0 * e0);
+  const double a1 = (2.0 / 3.0) / (e1 * e1);
+  return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+/* Component k of X and velocity u_d of the cell o steps along axis d from
+   the cell at linear index cell (coordinate i along d), ghosts included. */
+static void x_at(const or_grid* g, const double* X, const double* vel, long cell,
+                 long i, int d, int o, int k, double* Xk, double* ud) {
+  const long n = g->n[d], stride = line_stride(g, d);
+  long j = i + o;
+  double shift = 0.0;
+  int mirror = 0, side = 0;
+  if (j < 0 || j >= n) {
+    side = j < 0 ? 0 : 1;
+    const int bc = g->bc[d][side];
+    if (bc == OR_BC_PERIODIC) {
+      shift = side == 0 ? -(g->hi[d] - g->lo[d]) : (g->hi[d] - g->lo[d]);
+      j = side == 0 ? j + n : j - n;
+    } else if (bc == OR_BC_REFLECTIVE) {
+      mirror = 1;
+      j = side == 0 ? -1 - j : 2 * n - 1 - j;
+    } else {
+      j = side == 0 ? 0 : n - 1;
+    }
+  }
+  const long src = cell + (j - i) * stride;
+  *Xk = X[(size_t)k * g->ncell + src];
+  *ud = vel[(size_t)d * g->ncell + src];
+  if (k == d) {
+    if (mirror) *Xk = 2.0 * (side == 0 ? g->lo[d] : g->hi[d]) - *Xk;
+    *Xk += shift;
+  }
+  if (mirror) *ud = -*ud;
+}
+
+/* The right-hand side of dX_k/dt at one cell. */
+static double x_rhs(const or_grid* g, const double* X, const double* vel, long cell, int k) {
+  long idx[3] = {cell % g->n[0], (cell / g->n[0]) % g->n[1], cell / (g->n[0] * g->n[1])};
+  double L = 0.0;
+  for (int d = 0; d < g->dim; ++d) {
+    double x[5], u[5];
+    for (int o = -2; o <= 2; ++o) x_at(g, X, vel, cell, idx[d], d, o, k, &x[o + 2], &u[o + 2]);
+    const double uL = 0.5 * (u[1] + u[2]), uR = 0.5 * (u[2] + u[3]);
+    const double XR = uR >= 0.0 ? weno3_face(x[1], x[2], x[3], g->dx[d])
+                                : weno3_face(x[4], x[3], x[2], g->dx[d]);
+    const double XL = uL >= 0.0 ? weno3_face(x[0], x[1], x[2], g->dx[d])
+                                : weno3_face(x[3], x[2], x[1], g->dx[d]);
+    L -= (uR * (XR - x[2]) - uL * (XL - x[2])) / g->dx[d];
+  }
+  return L;
+}
+
+/* X at the end of a step of length dt from the present state, into Xn
+   ([dim][ncell]). */
+static int x_weno_rk3(const or_grid* g, double dt, double* Xn) {
+  const long nc = g->ncell;
+  const size_t sz = sizeof(double) * (size_t)g->dim * nc;
+  double* vel = malloc(sz);
+  double* X0 = malloc(sz);
+  double* X1 = malloc(sz);
+  double* X2 = malloc(sz);
+  if (!vel || !X0 || !X1 || !X2) {
+    free(vel); free(X0); free(X1); free(X2);
+    return OR_EINVAL;
+  }
+#pragma omp parallel for
+  for (long c = 0; c < nc; ++c) {
+    double rho = 0.0;
+    for (int l = 0; l < g->nmat; ++l) rho += g->U[(size_t)(g->o_arho + l) * nc + c];
+    for (int d = 0; d < g->dim; ++d) {
+      vel[(size_t)d * nc + c] = g->U[(size_t)(g->o_mom + d) * nc + c] / rho;
+      X0[(size_t)d * nc + c] = g->U[(size_t)(g->o_X + d) * nc + c];
+    }
+  }
+#pragma omp parallel for
+  for (long c = 0; c < nc; ++c)
+    for (int k = 0; k < g->dim; ++k)
+      X1[(size_t)k * nc + c] = X0[(size_t)k * nc + c] + dt * x_rhs(g, X0, vel, c, k);
+#pragma omp parallel for
+  for (long c = 0; c < nc; ++c)
+    for (int k = 0; k < g->dim; ++k) {
+      const size_t q = (size_t)k * nc + c;
+      X2[q] = 0.75 * X0[q] + 0.25 * (X1[q] + dt * x_rhs(g, X1, vel, c, k));
+    }
+#pragma omp parallel for
+  for (long c = 0; c < nc; ++c)
+    for (int k = 0; k < g->dim; ++k) {
+      const size_t q = (size_t)k * nc + c;
+      Xn[q] = (1.0 / 3.0) * X0[q] + (2.0 / 3.0) * (X2[q] + dt * x_rhs(g, X2, vel, c, k));
+    }
+  free(vel); free(X0); free(X1); free(X2);
+  return OR_OK;
+}
+
+int or_set_x_scheme(or_grid* g, int scheme) {
+  if (!g || scheme < 0 || scheme > 1) return OR_EINVAL;
+  g->xscheme = scheme;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Perturbation field phi(x,t) = phi0(X(x,t)) (Eq. for phi, Sec. 3.2.2):    */
 /* multilinear interpolation on the lattice, 1 outside it (R13).            */
 /* ------------------------------------------------------------------------ */
@@ -1091,7 +1214,22 @@ int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed, double* info) {
       rc = or_cfl_dt(g, cfl, &dt, &smax);
       if (rc != OR_OK) break;
     }
+    double* Xn = NULL;
+    if (g->xscheme == 1) {
+      /* X from the state at the step's start; the sweeps' X is replaced */
+      Xn = malloc(sizeof(double) * (size_t)g->dim * g->ncell);
+      rc = Xn ? x_weno_rk3(g, dt, Xn) : OR_EINVAL;
+      if (rc != OR_OK) {
+        free(Xn);
+        break;
+      }
+    }
     for (int d = 0; d < g->dim && rc == OR_OK; ++d) rc = sweep(g, d, dt);
+    if (Xn) {
+      if (rc == OR_OK)
+        memcpy(g->U + (size_t)g->o_X * g->ncell, Xn, sizeof(double) * (size_t)g->dim * g->ncell);
+      free(Xn);
+    }
     if (rc != OR_OK) break;
     rc = sources(g, dt);
     if (rc != OR_OK) break;

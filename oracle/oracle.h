@@ -81,6 +81,10 @@ int or_read(const or_grid* g, int primitive, double* out);
 int or_write_conserved(or_grid* g, const double* U);
 int or_totals(const or_grid* g, double* out /* N + 4 */);
 void or_set_threads(int n);
+/* Transport of the Lagrangian coordinates X: 0 (default) carried by the
+ * sweeps like the volume fractions; 1 third-order WENO with three-stage RK
+ * from the state at the step's start (Sec. 3.2.1).  OR_EINVAL otherwise. */
+int or_set_x_scheme(or_grid* g, int scheme);
 
 /* ---- single-point routines exported for the pins ---- */
 void or_thermo(const or_material* m, double rho, double psi, double J2,

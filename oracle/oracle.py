@@ -77,6 +77,7 @@ def load():
         lib.or_write_conserved.argtypes = [ctypes.c_void_p, P(d)]
         lib.or_totals.argtypes = [ctypes.c_void_p, P(d)]
         lib.or_set_threads.argtypes = [i]
+        lib.or_set_x_scheme.argtypes = [ctypes.c_void_p, i]
         lib.or_thermo.argtypes = [P(Material), d, d, d, P(d)]
         lib.or_hencky.argtypes = [P(d), P(d), P(d), P(d)]
         lib.or_lookup.restype = d
@@ -136,6 +137,11 @@ class OracleGrid:
         if getattr(self, "h", None):
             self.lib.or_destroy(self.h)
             self.h = None
+
+    def set_x_scheme(self, scheme: int) -> None:
+        """0: X carried by the sweeps; 1: WENO3 + RK3 (Sec. 3.2.1)."""
+        if self.lib.or_set_x_scheme(self.h, int(scheme)) != 0:
+            raise ValueError("x scheme must be 0 or 1")
 
     def step(self, nsteps: int, cfl: float | None = None, dt: float = 0.0) -> dict:
         info = np.zeros(5)
