@@ -269,12 +269,12 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
-def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True):
+def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True, x_transport=0):
     """Device time of `steps` single-step calls (CUDA events on the grid's
     stream), L2 flushed between steps when the state fits in L2."""
     import torch
     from paper_2210_04037_gb300 import mmfrac
-    g = mmfrac.Grid(case, precision, stream=stream.cuda_stream)
+    g = mmfrac.Grid(case, precision, stream=stream.cuda_stream, x_transport=x_transport)
     g.step(warmup)
     mmfrac.profile_enable(g.h, profile)
     mmfrac.profile_read(g.h, reset=True)
@@ -515,10 +515,11 @@ def run_gpu(args, rank: int, world: int):
     with ClockSampler(local) as clk:
         # the timed pass (events around each step only), then the same steps
         # again with events around each launch for the per-kernel times
+        xt = 1 if args.x_transport == "weno3rk3" else 0
         g, ms, _, launches = time_device(case, prec, args.steps, args.warmup, stream, flush,
-                                         profile=False)
+                                         profile=False, x_transport=xt)
         gk, ms_k, prof, _ = time_device(case, prec, args.steps, args.warmup, stream, flush,
-                                        profile=True)
+                                        profile=True, x_transport=xt)
         gk.close()
         torch.cuda.synchronize()
     ms = max_over_ranks(ms, dist)
@@ -576,7 +577,7 @@ def run_gpu(args, rank: int, world: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == W.FP32_SPLIT else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=n), "cells": case.ncell,
-                   "precision": args.precision,
+                   "precision": args.precision, "x_transport": args.x_transport,
                    "l2": "flushed between steps (256 MiB write)" if flush is not None
                    else "state larger than L2",
                    "parallelism": f"replicas x{world}"},
@@ -614,6 +615,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--x-transport", default="sweep", choices=["sweep", "weno3rk3"],
+                    help="transport of the Lagrangian coordinates (default: with the sweeps)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

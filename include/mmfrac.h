@@ -140,6 +140,19 @@ mm_status mm_step_async(mm_grid* g, int n_steps, double cfl);
  * info (may be NULL) is filled as by mm_step. */
 mm_status mm_synchronize(mm_grid* g, mm_step_info* info);
 
+/* Transport of the Lagrangian coordinates X (Sec. 3.2.1).  MM_X_SWEEP
+ * (default): X is carried by the split MUSCL-Hancock sweeps like the volume
+ * fractions.  MM_X_WENO3_RK3: the scheme the paper states for X, third-order
+ * WENO face values from the upwind cell and the three-stage TVD Runge-Kutta
+ * scheme with the velocities of the step's start, computed before the sweeps
+ * and replacing their X (dX/dt = -div(X u) + X div(u), face velocity the
+ * mean of the cell velocities; ghosts follow the boundary rules).  The first
+ * call with MM_X_WENO3_RK3 allocates 3 x dim x ncell values of scratch.
+ * Grids in a batch must use MM_X_SWEEP; MM_X_WENO3_RK3 takes grids of fewer
+ * than 2^31 cells.  Errors: MM_EINVAL, MM_ENOMEM. */
+enum { MM_X_SWEEP = 0, MM_X_WENO3_RK3 = 1 };
+mm_status mm_set_x_transport(mm_grid* g, int scheme);
+
 /* Copy fields to host_dst ([popcount(field_mask)][ncell] doubles, fields
  * in order; bit f of field_mask selects field f, ~0 for all).
  * primitive = 1 returns the primitive fields, 0 the conserved ones.
@@ -304,12 +317,14 @@ int64_t mm_kernel_launches(const mm_grid* g);
 /* Kernel timing (tracing aid, no counterpart in the paper).  With enable = 1
  * every later mm_step brackets each of its launches with CUDA events on the
  * grid's stream and accumulates the elapsed device time per kernel kind:
- * MM_K_CFL, MM_K_DT, MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES.
+ * MM_K_CFL, MM_K_DT, MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES,
+ * MM_K_XTRANSPORT (the X update of MM_X_WENO3_RK3, its four launches and the
+ * copy together).
  * mm_profile_read copies min(n, MM_K_COUNT) accumulated milliseconds and
  * launch counts (either pointer may be NULL) and, if reset = 1, zeroes them.
  * Errors: MM_EINVAL, MM_ECUDA. */
 enum { MM_K_CFL = 0, MM_K_DT = 1, MM_K_SWEEP_X = 2, MM_K_SWEEP_Y = 3, MM_K_SWEEP_Z = 4,
-       MM_K_SOURCES = 5, MM_K_COUNT = 6 };
+       MM_K_SOURCES = 5, MM_K_XTRANSPORT = 6, MM_K_COUNT = 7 };
 mm_status mm_profile_enable(mm_grid* g, int enable);
 mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int reset);
 

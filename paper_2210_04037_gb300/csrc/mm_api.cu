@@ -112,8 +112,11 @@ struct mm_grid {
   bool prof = false;
   std::vector<cudaEvent_t> ev;      // pool, two per timed launch
   std::vector<int> ev_kind;         // kind of each started pair
-  double prof_ms[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
-  long long prof_n[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[MM_K_COUNT] = {};
+  long long prof_n[MM_K_COUNT] = {};
+  // X by WENO3 + RK3: scheme and its scratch (velocities, two stages)
+  int xscheme = MM_X_SWEEP;
+  void* xs[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -480,6 +483,13 @@ mm_status enqueue_one(mm_grid* g, double cfl) {
     prof_end(g);
     g->launches += 1;
     CUDA_TRY(cudaGetLastError());
+    if (g->xscheme == MM_X_WENO3_RK3) {
+      // X of the step's end from its start (the state the sweeps read)
+      prof_begin(g, MM_K_XTRANSPORT);
+      CUDA_TRY(go(g, 6, 0, 0, a));
+      for (int st = 1; st <= 3; ++st) CUDA_TRY(go(g, 7, 0, st, a));
+      prof_end(g);
+    }
     for (int d = 0; d < g->dim; ++d) {
       KArgs b = args_for(g);
       b.Uout = g->U[1 - g->cur];
@@ -488,6 +498,15 @@ mm_status enqueue_one(mm_grid* g, double cfl) {
       CUDA_TRY(go(g, 3, d, 0, b));
       prof_end(g);
       g->cur = 1 - g->cur;
+    }
+    if (g->xscheme == MM_X_WENO3_RK3) {
+      // the sweeps' X is replaced (X are the last dim fields of the layout)
+      const size_t es = elem_size(g);
+      prof_begin(g, MM_K_XTRANSPORT);
+      CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(g->U[g->cur]) + es * (size_t)(g->nfield - g->dim) * g->ncell,
+                               g->xs[1], es * (size_t)g->dim * g->ncell, cudaMemcpyDeviceToDevice,
+                               g->stream));
+      prof_end(g);
     }
     KArgs c = args_for(g);
     prof_begin(g, MM_K_SOURCES);
@@ -647,10 +666,35 @@ mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int re
   return MM_OK;
 }
 
+mm_status mm_set_x_transport(mm_grid* g, int scheme) {
+  if (!g) return fail(MM_EINVAL, "mm_set_x_transport: null grid");
+  if (scheme != MM_X_SWEEP && scheme != MM_X_WENO3_RK3)
+    return fail(MM_EINVAL, "mm_set_x_transport: unknown scheme %d", scheme);
+  if (scheme == MM_X_WENO3_RK3 && g->ncell >= (1ll << 31))
+    return fail(MM_EINVAL, "mm_set_x_transport: WENO3 + RK3 takes grids of fewer than 2^31 cells");
+  if (scheme == MM_X_WENO3_RK3 && !g->xs[0]) {
+    const size_t bytes = elem_size(g) * (size_t)g->dim * g->ncell;
+    for (int i = 0; i < 3; ++i) {
+      if (cudaMalloc(&g->xs[i], bytes) != cudaSuccess) {
+        for (int j = 0; j <= i; ++j) {
+          cudaFree(g->xs[j]);
+          g->xs[j] = nullptr;
+        }
+        return fail(MM_ENOMEM, "device allocation of the X scratch failed");
+      }
+    }
+    for (int i = 0; i < 3; ++i) g->base.xs[i] = g->xs[i];
+  }
+  g->xscheme = scheme;
+  drop_graphs(g);
+  return MM_OK;
+}
+
 mm_status mm_destroy(mm_grid* g) {
   if (!g) return MM_OK;
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  for (int i = 0; i < 3; ++i) cudaFree(g->xs[i]);
   free_state(g);
   cudaFree(g->info);
   cudaFree(g->err);
@@ -720,8 +764,8 @@ struct mm_batch {
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
-  double prof_ms[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
-  long long prof_n[MM_K_COUNT] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[MM_K_COUNT] = {};
+  long long prof_n[MM_K_COUNT] = {};
 };
 
 namespace {
@@ -813,6 +857,10 @@ mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_ba
   }
   if (g0->nmat != 2)
     return fail(MM_EINVAL, "mm_batch_create: batches are built for two materials");
+  for (int i = 0; i < n; ++i)
+    if (grids[i]->xscheme != MM_X_SWEEP)
+      return fail(MM_EINVAL, "mm_batch_create: member %d transports X by WENO3 + RK3; batches "
+                  "carry X in the sweeps", i);
   for (int i = 0; i < n; ++i) CUDA_TRY(cudaStreamSynchronize(grids[i]->stream));
   mm_batch* b = new mm_batch();
   b->m.assign(grids, grids + n);

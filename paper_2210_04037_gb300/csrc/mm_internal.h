@@ -76,6 +76,7 @@ struct KArgs {
   double cfl, dxmin;
   double* prim;        // [nfield][ncell] doubles for init / read
   double* partial;     // per-block partial totals
+  void* xs[3];         // X by WENO3 + RK3: cell velocities, stage 1, stage 2 ([dim][ncell], R)
 };
 
 static_assert(sizeof(KArgs) % 8 == 0, "KArgs is copied as 8-byte words");
@@ -99,7 +100,8 @@ void mm_internal_set_error(const char* msg);
 // Launchers implemented in the precision x dimension translation units
 // (mm_fp64_d{1,2,3}.cu, mm_fp32_d{1,2,3}.cu).  what: 0 init, 1 read
 // (flag = primitive), 2 CFL reduction, 3 sweep along axis, 4 sources,
-// 5 totals into out (nblocks partials).
+// 5 totals into out (nblocks partials), 6 cell velocities for X, 7 X stage
+// (flag = 1, 2, 3).
 #define MM_DECLARE_LAUNCHER(name)                                                          \
   cudaError_t name(int what, int axis, int flag, const KArgs& a, double* out, int nblocks, \
                    cudaStream_t s);

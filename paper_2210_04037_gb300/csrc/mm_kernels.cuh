@@ -1214,6 +1214,148 @@ __global__ void __launch_bounds__(256) k_cfl_batch(BatchK bk) {
   }
 }
 
+// ------------------------------------- X by WENO3 + RK3 (Sec. 3.2.1) ----
+// The alternative to carrying X in the sweeps:
+//   dX/dt = -sum_d [u_{d,i+1/2} (X_{i+1/2} - X_i) - u_{d,i-1/2} (X_{i-1/2} - X_i)] / dx_d
+// (the difference of the fluxes X u_d plus X div(u), so DX/Dt = 0), face
+// velocity the mean of the two cell velocities, face X the third-order WENO
+// value reconstructed in the upwind cell, Shu and Osher's three-stage TVD
+// Runge-Kutta scheme with the velocities of the step's start; ghosts follow
+// the sweeps' boundary rules.  All before the sweeps; the result replaces X
+// after them.
+
+// Cell velocities of the step's start into xs[0].
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_xvel(KArgs a) {
+  typedef typename P::R R;
+  typedef Lay<DIM, NMAT, NH> L;
+  const R* U = static_cast<const R*>(a.Uin);
+  R* V = static_cast<R*>(a.xs[0]);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    R rho = R(0);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) rho += U[(long long)(L::oARHO + l) * a.ncell + c];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) V[(long long)d * a.ncell + c] = U[(long long)(L::oMOM + d) * a.ncell + c] / rho;
+  }
+}
+
+// WENO3 value at the face between cells b and c reconstructed in cell b
+// from its neighbours a (away from the face) and c (across it): candidates
+// -a/2 + 3b/2 and (b + c)/2, linear weights 1/3 and 2/3, smoothness
+// ((b - a)/dx)^2 and ((c - b)/dx)^2, eps = 1e-6 (Jiang and Shu).
+template <class R>
+__device__ __forceinline__ R weno3_face(R a, R b, R c, R dx) {
+  const R q0 = R(-0.5) * a + R(1.5) * b;
+  const R q1 = R(0.5) * b + R(0.5) * c;
+  const R s0 = (b - a) / dx, s1 = (c - b) / dx;
+  const R e0 = R(1e-6) + s0 * s0, e1 = R(1e-6) + s1 * s1;
+  const R a0 = (R(1) / R(3)) / (e0 * e0);
+  const R a1 = (R(2) / R(3)) / (e1 * e1);
+  return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+// One RK stage (1, 2, 3): stage s reads X from src (stage 1: the state)
+// and writes dst = X0 + dt L (1), 3/4 X0 + 1/4 (X1 + dt L) (2),
+// 1/3 X0 + 2/3 (X2 + dt L) (3), X0 the state's X.
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_xstage(KArgs a, int stage) {
+  typedef typename P::R R;
+  typedef Lay<DIM, NMAT, NH> L;
+  const long long nc = a.ncell;
+  const R* X0 = static_cast<const R*>(a.Uin) + (long long)L::oX * nc;
+  const R* V = static_cast<const R*>(a.xs[0]);
+  const R* src = stage == 1 ? X0 : static_cast<const R*>(a.xs[stage - 1]);
+  R* dst = static_cast<R*>(a.xs[stage == 2 ? 2 : 1]);
+  const R dt = R(a.info->dt);
+  // grids here hold fewer than 2^31 cells (checked on the host): 32-bit indices
+  const int n0 = a.n[0], n1 = a.n[1];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < (int)nc; c += gridDim.x * blockDim.x) {
+    const int idx[3] = {c % n0, (c / n0) % n1, c / (n0 * n1)};
+    R Lk[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) Lk[k] = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int n = a.n[d];
+      const int stride = d == 0 ? 1 : (d == 1 ? n0 : n0 * n1);
+      const bool inner = idx[d] >= 2 && idx[d] + 2 < n;  // the whole stencil inside the grid
+      // velocity component d on the stencil (negated across a mirror wall)
+      R u[5];
+#pragma unroll
+      for (int o = -2; o <= 2; ++o) {
+        if (inner) {
+          u[o + 2] = V[(long long)d * nc + c + o * stride];
+        } else {
+          int j = idx[d] + o;
+          bool mirror = false;
+          if (j < 0 || j >= n) {
+            const int side = j < 0 ? 0 : 1;
+            const int bc = a.bc[d][side];
+            if (bc == BC_P) j = side == 0 ? j + n : j - n;
+            else if (bc == BC_R) { mirror = true; j = side == 0 ? -1 - j : 2 * n - 1 - j; }
+            else j = side == 0 ? 0 : n - 1;
+          }
+          const R uv = V[(long long)d * nc + c + (j - idx[d]) * stride];
+          u[o + 2] = mirror ? -uv : uv;
+        }
+      }
+      const R dx = R(a.dx[d]);
+      const R uL = R(0.5) * (u[1] + u[2]), uR = R(0.5) * (u[2] + u[3]);
+      const bool pr = uR >= R(0), pl = uL >= R(0);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        R x[5];
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+          if (inner) {
+            x[o + 2] = src[(long long)k * nc + c + o * stride];
+          } else {
+            int j = idx[d] + o;
+            R shift = R(0);
+            bool mirror = false;
+            int side = 0;
+            if (j < 0 || j >= n) {
+              side = j < 0 ? 0 : 1;
+              const int bc = a.bc[d][side];
+              if (bc == BC_P) {
+                shift = side == 0 ? -R(a.hi[d] - a.lo[d]) : R(a.hi[d] - a.lo[d]);
+                j = side == 0 ? j + n : j - n;
+              } else if (bc == BC_R) {
+                mirror = true;
+                j = side == 0 ? -1 - j : 2 * n - 1 - j;
+              } else {
+                j = side == 0 ? 0 : n - 1;
+              }
+            }
+            R xv = src[(long long)k * nc + c + (j - idx[d]) * stride];
+            if (k == d) {
+              if (mirror) xv = R(2) * R(side == 0 ? a.lo[d] : a.hi[d]) - xv;
+              xv += shift;
+            }
+            x[o + 2] = xv;
+          }
+        }
+        // the upwind cell's stencil first, then one reconstruction per face
+        const R XR = weno3_face(pr ? x[1] : x[4], pr ? x[2] : x[3], pr ? x[3] : x[2], dx);
+        const R XL = weno3_face(pl ? x[0] : x[3], pl ? x[1] : x[2], pl ? x[2] : x[1], dx);
+        Lk[k] -= (uR * (XR - x[2]) - uL * (XL - x[2])) / dx;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const long long q = (long long)k * nc + c;
+      if (stage == 1)
+        dst[q] = X0[q] + dt * Lk[k];
+      else if (stage == 2)
+        dst[q] = R(0.75) * X0[q] + R(0.25) * (src[q] + dt * Lk[k]);
+      else
+        dst[q] = (R(1) / R(3)) * X0[q] + (R(2) / R(3)) * (src[q] + dt * Lk[k]);
+    }
+  }
+}
+
 // ------------------------------------------------------ init and read ----
 template <class P, int DIM, int NMAT, int NH>
 __global__ void k_init(KArgs a) {

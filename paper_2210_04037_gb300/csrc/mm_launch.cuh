@@ -77,6 +77,14 @@ struct Launch {
       }
       case 3:
         return sweep_t<DIM, NMAT, NH>(axis, a, s);
+      case 6: {
+        k_xvel<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a);
+        break;
+      }
+      case 7: {
+        k_xstage<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a, flag);
+        break;
+      }
       case 4: {
         k_sources<P, DIM, NMAT, NH><<<grid_for(a.ncell, 128), 128, 0, s>>>(a);
         break;

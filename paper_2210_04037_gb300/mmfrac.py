@@ -76,7 +76,8 @@ class StepInfo(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
 
 
-EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async", "mm_synchronize",
+EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport", "mm_step",
+           "mm_step_async", "mm_synchronize",
            "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
@@ -84,7 +85,8 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async", "mm
            "mm_batch_step", "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
            "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
            "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy")
-KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources")
+KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources", "xtransport")
+X_SWEEP, X_WENO3_RK3 = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -105,6 +107,8 @@ def load(path: str = LIB_PATH):
         lib.mm_set_materials.argtypes = [vp, P(Material), ctypes.c_int, P(Init)]
         lib.mm_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(StepInfo)]
         lib.mm_step_async.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        lib.mm_set_x_transport.argtypes = [vp, ctypes.c_int]
+        lib.mm_set_x_transport.restype = ctypes.c_int
         lib.mm_batch_create.argtypes = [P(vp), ctypes.c_int, vp, P(vp)]
         lib.mm_batch_set_options.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
         lib.mm_batch_step.argtypes = [vp, ctypes.c_int, ctypes.c_double]
@@ -223,6 +227,11 @@ def step(grid, n_steps: int, cfl: float) -> dict:
                 bad_cell=info.bad_cell)
 
 
+def set_x_transport(grid, scheme: int) -> None:
+    """X_SWEEP (X carried by the sweeps) or X_WENO3_RK3 (Sec. 3.2.1)."""
+    _check(load().mm_set_x_transport(grid, int(scheme)))
+
+
 def step_async(grid, n_steps: int, cfl: float) -> None:
     """Enqueue n_steps steps without waiting; in-step failures are reported
     by the next synchronize / step / read_fields."""
@@ -293,11 +302,13 @@ def conserved_totals_noalloc(d_cons: int, dim: int, ncell: int, n_materials: int
 class Grid:
     """A grid built from a ``workloads.Case`` on the current CUDA device."""
 
-    def __init__(self, case, precision: int = FP64, stream=None):
+    def __init__(self, case, precision: int = FP64, stream=None, x_transport: int = X_SWEEP):
         self.case = case
         self.nmat = len(case.materials)
         self.h = create_grid(case, precision, stream)
         try:
+            if x_transport != X_SWEEP:
+                set_x_transport(self.h, x_transport)
             set_materials(self.h, case)
         except Exception:
             destroy(self.h)
