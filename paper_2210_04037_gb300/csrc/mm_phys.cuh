@@ -671,11 +671,16 @@ struct Phys {
     for (int k = 0; k < L::NFC; ++k) w[L::oF + k] = c[L::oF + k];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) w[L::oX + k] = c[L::oX + k];
+    // every value finite: a sum of them is finite exactly then (a NaN or an
+    // infinity propagates; admissible states are far from overflowing it),
+    // one test instead of one per value
+    R sw = R(0);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) ok = ok && mfinite(w[k]) && mfinite(c[k]);
+    for (int k = 0; k < NF; ++k) sw += w[k] + c[k];
+    XT sx = XT(0);
 #pragma unroll
-    for (int k = 0; k < NX; ++k) ok = ok && mfinite(cx[k]) && mfinite(wx[k]);
-    if (!ok) return false;
+    for (int k = 0; k < NX; ++k) sx += cx[k] + wx[k];
+    if (!(ok && mfinite(sw) && mfinite(sx))) return false;
     if (mxo) *mxo = mx;
     return finish<AX>(a, R(pE), rho, arho, mx, ax);
   }
