@@ -231,12 +231,17 @@ struct SweepShape {
 //   2. van Leer reconstruction + MUSCL-Hancock half step (face states),
 //   3. Riemann problem at each face,
 //   4. conservative update with the non-conservative terms, store.
-// b: tile index (along AX fastest, then across, then the remaining axis);
-// smem: SH::smem bytes; ok1, ok2: SH::N1, SH::N2 flags.  All threads of the
+// (ta, tw, rr): tile along AX, across it, and the index along the remaining
+// axis; smem: SH::smem bytes; ok1, ok2: SH::N1, SH::N2 flags.  first = false:
+// the tile follows tile ta - 1 of the same CTA, whose last four recovered
+// cells, last two half-stepped cells and last face are already in place
+// (carried), so each phase computes only the tile's new items.  carry: move
+// those records to the front for tile ta + 1 at the end.  All threads of the
 // CTA call it together.
 template <class P, int DIM, int NMAT, int NH, int AX, int V>
-__device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigned char* smem,
-                                           unsigned char* ok1, unsigned char* ok2) {
+__device__ __forceinline__ void sweep_tile(const KArgs& a, int ta, int tw, int rr, bool first,
+                                           bool carry, unsigned char* smem, unsigned char* ok1,
+                                           unsigned char* ok2) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
@@ -253,20 +258,19 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigne
   R* r2 = r1 + N1 * C1;
   R* r3 = r2 + 2 * N2 * C2;
 
-  const int nta = (a.n[AX] + TL - 1) / TL, ntt = (a.n[TD] + TW - 1) / TW;
-  const int ta = int(bt % nta);
-  bt /= nta;
-  const int tw = int(bt % ntt);
-  const int rr = int(bt / ntt);
   const int na = a.n[AX], ntw = a.n[TD];
   const int a0 = ta * TL, w0 = tw * TW;
   const long long step = a.info->steps;
   const R lam = R(a.info->lam[AX]);  // dt / dx_AX of the step
 
   // 1. primitive recovery of every tile cell, halo of two included
-  for (int it = threadIdx.x; it < N1; it += NT) {
+  // (positions 0..3 carried when the tile follows one of the same CTA)
+  const int s1 = first ? 0 : 4;
+  for (int it0 = threadIdx.x; it0 < (TL + 4 - s1) * TW; it0 += NT) {
     int p, w;
-    SH::pos(it, TL + 4, p, w);
+    SH::pos(it0, TL + 4 - s1, p, w);
+    p += s1;
+    const int it = SH::idx(p, w, TL + 4);
     const int gi = a0 - 2 + p;
     unsigned char okv = 0;
     if (w0 + w < ntw && gi >= -2 && gi < na + 2) {
@@ -289,9 +293,13 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigne
   __syncthreads();
 
   // 2. van Leer reconstruction and MUSCL-Hancock half step on cells -1..TL
-  for (int it = threadIdx.x; it < N2; it += NT) {
+  // (items 0, 1 carried)
+  const int s2 = first ? 0 : 2;
+  for (int it0 = threadIdx.x; it0 < (TL + 2 - s2) * TW; it0 += NT) {
     int p2, w;
-    SH::pos(it, TL + 2, p2, w);
+    SH::pos(it0, TL + 2 - s2, p2, w);
+    p2 += s2;
+    const int it = SH::idx(p2, w, TL + 2);
     const int gi = a0 - 1 + p2;
     const int im = SH::idx(p2, w, TL + 4), ic = SH::idx(p2 + 1, w, TL + 4),
               ip = SH::idx(p2 + 2, w, TL + 4);
@@ -448,10 +456,13 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigne
   }
   __syncthreads();
 
-  // 3. Riemann problem at faces -1/2 .. TL-1/2
-  for (int it = threadIdx.x; it < N3; it += NT) {
+  // 3. Riemann problem at faces -1/2 .. TL-1/2 (face 0 carried)
+  const int s3 = first ? 0 : 1;
+  for (int it0 = threadIdx.x; it0 < (TL + 1 - s3) * TW; it0 += NT) {
     int f, w;
-    SH::pos(it, TL + 1, f, w);
+    SH::pos(it0, TL + 1 - s3, f, w);
+    f += s3;
+    const int it = SH::idx(f, w, TL + 1);
     const int il = SH::idx(f, w, TL + 2), ir = SH::idx(f + 1, w, TL + 2);
     if (ok2[il] == 1 && ok2[ir] == 1) {
       const R* ql = r2 + (2 * il + 1) * C2;  // right face state of the left cell
@@ -517,6 +528,43 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, long long bt, unsigne
       store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
     }
   }
+  if (carry) {
+    // the next tile's first recovered cells (4), half-stepped cells (2) and
+    // face (1) are this tile's last ones
+    __syncthreads();
+    for (int it0 = threadIdx.x; it0 < 7 * TW; it0 += NT) {
+      const int w = it0 % TW, kind = it0 / TW;
+      if (kind < 4) {
+        const int d = SH::idx(kind, w, TL + 4), sidx = SH::idx(kind + TL, w, TL + 4);
+        for (int k = 0; k < C1; ++k) r1[d * C1 + k] = r1[sidx * C1 + k];
+        for (int k = 0; k < NX; ++k) x1[d * NX + k] = x1[sidx * NX + k];
+        ok1[d] = ok1[sidx];
+      } else if (kind < 6) {
+        const int j = kind - 4;
+        const int d = SH::idx(j, w, TL + 2), sidx = SH::idx(j + TL, w, TL + 2);
+        for (int k = 0; k < 2 * C2; ++k) r2[2 * d * C2 + k] = r2[2 * sidx * C2 + k];
+        for (int k = 0; k < 2 * NX; ++k) x2[2 * d * NX + k] = x2[2 * sidx * NX + k];
+        ok2[d] = ok2[sidx];
+      } else {
+        const int d = SH::idx(0, w, TL + 1), sidx = SH::idx(TL, w, TL + 1);
+        for (int k = 0; k < C3; ++k) r3[d * C3 + k] = r3[sidx * C3 + k];
+        for (int k = 0; k < NX; ++k) x3[d * NX + k] = x3[sidx * NX + k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Tile coordinates of tile index b of a sweep (along AX fastest, then
+// across, then the remaining axis).
+template <int AX, int TL, int TW>
+__device__ __forceinline__ void tile_of(const KArgs& a, long long b, int& ta, int& tw, int& rr) {
+  constexpr int TD = (AX == 0) ? 1 : 0;
+  const int nta = (a.n[AX] + TL - 1) / TL, ntt = (a.n[TD] + TW - 1) / TW;
+  ta = int(b % nta);
+  b /= nta;
+  tw = int(b % ntt);
+  rr = int(b / ntt);
 }
 
 // One CTA per tile of one grid.
@@ -525,7 +573,30 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep(KArgs a) {
   typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
-  sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, blockIdx.x, smem, ok1, ok2);
+  int ta, tw, rr;
+  tile_of<AX, SH::TL, SH::TW>(a, blockIdx.x, ta, tw, rr);
+  sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, ta, tw, rr, true, false, smem, ok1, ok2);
+}
+
+// One CTA per chunk of K consecutive tiles along the sweep axis (large
+// grids): each tile after the chunk's first reuses the overlap its
+// predecessor recovered and half-stepped, so no halo cell is computed twice
+// inside a chunk.  Blocks: chunk fastest, then across, then the remaining axis.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep_col(KArgs a, int K) {
+  typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
+  constexpr int TD = (AX == 0) ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
+  const int nta = (a.n[AX] + SH::TL - 1) / SH::TL, ntt = (a.n[TD] + SH::TW - 1) / SH::TW;
+  const int nch = (nta + K - 1) / K;
+  long long b = blockIdx.x;
+  const int ch = int(b % nch);
+  b /= nch;
+  const int tw = int(b % ntt), rr = int(b / ntt);
+  const int t0 = ch * K, t1 = t0 + K < nta ? t0 + K : nta;
+  for (int ta = t0; ta < t1; ++ta)
+    sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, ta, tw, rr, ta == t0, ta + 1 < t1, smem, ok1, ok2);
 }
 
 // ------------------------------------------------------------ batches ----
@@ -566,7 +637,11 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX, V>::NT) k_sweep_batch(BatchK 
   __shared__ KArgs ka;
   __shared__ long long s_unit;
   long long t;
-  while (batch_next(bk, ka, t, s_unit)) sweep_tile<P, DIM, NMAT, NH, AX, V>(ka, t, smem, ok1, ok2);
+  while (batch_next(bk, ka, t, s_unit)) {
+    int ta, tw, rr;
+    tile_of<AX, SH::TL, SH::TW>(ka, t, ta, tw, rr);
+    sweep_tile<P, DIM, NMAT, NH, AX, V>(ka, ta, tw, rr, true, false, smem, ok1, ok2);
+  }
 }
 
 // ------------------------------------------------------------- sources ----

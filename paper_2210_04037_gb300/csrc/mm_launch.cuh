@@ -41,11 +41,25 @@ struct Launch {
     typedef SweepShape<P, DIM, NMAT, NH, AX> SH;
     constexpr int TD = (AX == 0) ? 1 : 0;
     constexpr int RD = 3 - AX - TD;
-    cudaError_t e = smem_attr<k_sweep<P, DIM, NMAT, NH, AX>>(SH::smem);
+    const long long nta = (a.n[AX] + SH::TL - 1) / SH::TL;
+    const long long cols = (long long)((a.n[TD] + SH::TW - 1) / SH::TW) * a.n[RD];
+    // 3D y and z sweeps: chunks of K tiles along the sweep axis per CTA while
+    // about 2432 CTAs (16 per SM) remain; K = 1 is one CTA per tile.  Measured
+    // on GB300: the 256^3 z sweep 3.99 -> 3.57 ms, y 3.72 -> 3.67; x tiles are
+    // long (halo 4 of TL + 4) and lost (3.63 -> 4.01), the 2048^2 2D y sweep
+    // lost (0.50 -> 0.58 ms): those keep one tile per CTA
+    long long K = (DIM == 3 && AX != 0) ? nta * cols / (152LL * 16) : 1;
+    if (K > nta) K = nta;
+    if (K <= 1) {
+      cudaError_t e = smem_attr<k_sweep<P, DIM, NMAT, NH, AX>>(SH::smem);
+      if (e != cudaSuccess) return e;
+      k_sweep<P, DIM, NMAT, NH, AX><<<(unsigned)(nta * cols), SH::NT, SH::smem, s>>>(a);
+      return cudaGetLastError();
+    }
+    cudaError_t e = smem_attr<k_sweep_col<P, DIM, NMAT, NH, AX>>(SH::smem);
     if (e != cudaSuccess) return e;
-    const long long nb = (long long)((a.n[AX] + SH::TL - 1) / SH::TL) *
-                         ((a.n[TD] + SH::TW - 1) / SH::TW) * a.n[RD];
-    k_sweep<P, DIM, NMAT, NH, AX><<<(unsigned)nb, SH::NT, SH::smem, s>>>(a);
+    const long long nch = (nta + K - 1) / K;
+    k_sweep_col<P, DIM, NMAT, NH, AX><<<(unsigned)(nch * cols), SH::NT, SH::smem, s>>>(a, (int)K);
     return cudaGetLastError();
   }
 
