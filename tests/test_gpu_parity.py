@@ -48,8 +48,8 @@ PARITY_CASES = {
     "reflective_mix_3d_12x14x10": (lambda: cases.periodic_mix_3d(12, nz=10, bc=2), 100),
     "sod_gas_1d_300": (lambda: cases.gas_riemann(300, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)), 100),
     "impact_al_periodic_1d": (lambda: cases.periodic_impact_1d(200), 100),
-    # large enough that the 3D sweeps run chunks of consecutive tiles per CTA
-    # (x: 5, y and z: 9), reusing each tile's overlap with the next
+    # large enough that the 3D y and z sweeps run chunks of 9 consecutive
+    # tiles per CTA, reusing each tile's overlap with the next
     "cylinder_3d_128_tile_chunks": (lambda: W.cylinder_3d(128), 3),
 }
 
