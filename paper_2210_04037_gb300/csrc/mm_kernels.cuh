@@ -187,8 +187,8 @@ template <> struct Tile<P32, 1, 0> { static constexpr int TL = 124, TW = 1, NT =
 template <> struct Tile<P32, 2, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
 template <> struct Tile<P32, 2, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
 template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
-template <> struct Tile<P32, 3, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
-template <> struct Tile<P32, 3, 2> { static constexpr int TL = 12, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
 // Second shape per axis, one of the two the batched sweep's autotuner times
 // (the cell arithmetic does not depend on the tile, so either gives the same
 // bits): longer tiles along the sweep, narrower across it.
