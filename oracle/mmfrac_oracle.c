@@ -18,7 +18,9 @@
  *                   -> per-cell sources: phi0(X) lookup, plastic return,
  *                      RK4 damage (Godunov split, R12)
  *   one sweep     = primitive recovery -> van Leer slopes on primitives (R9)
- *                   -> MUSCL-Hancock half step -> HLLC flux (R11)
+ *                   -> MUSCL-Hancock half step (first order where a face
+ *                      state is inadmissible or a phase density leaves the
+ *                      half step's bound) -> HLLC flux (R11)
  *                   -> conservative update + non-conservative terms
  */
 #include "oracle.h"
@@ -49,6 +51,7 @@ struct or_grid {
   double plo[3], ph[3];
   double t, dt_last, smax;
   long steps, bad_cell;
+  long nbound; /* faces sent to first order by the phase-density bound */
   int xscheme; /* 0: X carried by the sweeps (R20); 1: WENO3 + RK3 (R28) */
 };
 
@@ -477,12 +480,31 @@ static void noncons(const or_grid* g, int d, const double* wc, const aux_t* ac,
   (void)d;
 }
 
+/* A half step of length dt/2 changes the log of a phase density by
+ * (dt/2) |du/dx| at most, and with dt <= cfl dx / S (S = max |u| + c_L over the
+ * grid, |u_R - u_L| <= 2 S, cfl <= 1) that is at most 1.  A half-stepped face
+ * state whose phase density differs from the reconstructed one by more than a
+ * factor e is therefore not the half step's compression: it comes from the
+ * near-cancelling increments of phi_l and phi_l rho_l where phi_l is a trace
+ * fraction, and it is treated as inadmissible. */
+static int phase_density_in_bound(const or_grid* g, const double* w_rec,
+                                  const double* w_half) {
+  const double e = 2.718281828459045;
+  for (int l = 0; l < g->nmat; ++l) {
+    const double r0 = w_rec[g->o_arho + l], r1 = w_half[g->o_arho + l];
+    if (!(r1 <= e * r0 && r0 <= e * r1)) return 0;
+  }
+  return 1;
+}
+
 /* Face states of one cell after the MUSCL-Hancock half step.  Falls back to
- * the cell average on both faces when a state leaves the admissible set. */
-static void face_states(const or_grid* g, int d, double lam, const double* wm,
-                        const double* wc, const double* wp, const double* uc,
-                        const aux_t* ac, double* UL, aux_t* aL, double* UR,
-                        aux_t* aR) {
+ * the cell average on both faces when a state leaves the admissible set or a
+ * phase density leaves the half step's bound (phase_density_in_bound). */
+static int face_states(const or_grid* g, int d, double lam, const double* wm,
+                       const double* wc, const double* wp, const double* uc,
+                       const aux_t* ac, double* UL, aux_t* aL, double* UR,
+                       aux_t* aR) {
+  int bound = 0;
   double wL[MAXF], wR[MAXF];
   for (int k = 0; k < g->nfield; ++k) {
     const double s = van_leer(wc[k] - wm[k], wp[k] - wc[k]);
@@ -498,23 +520,28 @@ static void face_states(const or_grid* g, int d, double lam, const double* wm,
     phys_flux(g, d, uR0, &xR, FR);
     for (int j = 0; j < 3; ++j) dF[j] = xR.F[3 * d + j] - xL.F[3 * d + j];
     noncons(g, d, wc, ac, xR.u[d] - xL.u[d], dF, nc);
-    double uL1[MAXF], uR1[MAXF], tmp[MAXF];
+    double uL1[MAXF], uR1[MAXF], wL1[MAXF], wR1[MAXF];
     for (int k = 0; k < g->nfield; ++k) {
       const double inc = 0.5 * lam * ((FL[k] - FR[k]) + nc[k]);
       uL1[k] = uL0[k] + inc;
       uR1[k] = uR0[k] + inc;
     }
-    ok = u2w(g, uL1, tmp, aL) == 0 && u2w(g, uR1, tmp, aR) == 0;
+    ok = u2w(g, uL1, wL1, aL) == 0 && u2w(g, uR1, wR1, aR) == 0;
+    if (ok && !(phase_density_in_bound(g, wL, wL1) && phase_density_in_bound(g, wR, wR1))) {
+      ok = 0;
+      bound = 1;
+    }
     if (ok) {
       memcpy(UL, uL1, sizeof(double) * g->nfield);
       memcpy(UR, uR1, sizeof(double) * g->nfield);
-      return;
+      return 0;
     }
   }
   memcpy(UL, uc, sizeof(double) * g->nfield);
   memcpy(UR, uc, sizeof(double) * g->nfield);
   *aL = *ac;
   *aR = *ac;
+  return bound;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -575,7 +602,7 @@ static long line_base(const or_grid* g, int d, long line) {
 }
 
 static int sweep_line(const or_grid* g, int d, double dt, long line,
-                      long* bad) {
+                      long* bad, long* nbound) {
   const long n = g->n[d];
   const int nf = g->nfield;
   const long base = line_base(g, d, line), stride = line_stride(g, d);
@@ -607,9 +634,9 @@ static int sweep_line(const or_grid* g, int d, double dt, long line,
   }
   /* 2. reconstruction + half step on cells -1 .. n (ext 1 .. n+2) */
   for (size_t e = 1; e <= (size_t)n + 2; ++e) {
-    face_states(g, d, lam, W + (e - 1) * nf, W + e * nf, W + (e + 1) * nf,
-                ext + e * nf, &A[e], FS + (2 * e) * nf, &FA[2 * e],
-                FS + (2 * e + 1) * nf, &FA[2 * e + 1]);
+    *nbound += face_states(g, d, lam, W + (e - 1) * nf, W + e * nf, W + (e + 1) * nf,
+                           ext + e * nf, &A[e], FS + (2 * e) * nf, &FA[2 * e],
+                           FS + (2 * e + 1) * nf, &FA[2 * e + 1]);
   }
   /* 3. HLLC on faces between ext e and e+1, e = 1 .. n+1 */
   for (size_t e = 1; e <= (size_t)n + 1; ++e) {
@@ -636,11 +663,11 @@ done:
 static int sweep(or_grid* g, int d, double dt) {
   const long nlines = g->ncell / g->n[d];
   int rc = OR_OK;
-  long bad = -1;
-#pragma omp parallel for schedule(dynamic, 4)
+  long bad = -1, nb = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : nb)
   for (long line = 0; line < nlines; ++line) {
     long b = -1;
-    const int r = sweep_line(g, d, dt, line, &b);
+    const int r = sweep_line(g, d, dt, line, &b, &nb);
     if (r != OR_OK) {
 #pragma omp critical
       {
@@ -652,6 +679,7 @@ static int sweep(or_grid* g, int d, double dt) {
     g->bad_cell = bad;
     return rc;
   }
+  g->nbound += nb;
   double* t = g->U;
   g->U = g->V;
   g->V = t;
@@ -1244,6 +1272,7 @@ int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed, double* info) {
     info[2] = g->smax;
     info[3] = (double)g->steps;
     info[4] = (double)g->bad_cell;
+    info[5] = (double)g->nbound;
   }
   return rc;
 }

@@ -74,7 +74,9 @@ int or_nfield(const or_grid* g);
 long or_ncell(const or_grid* g);
 /* Advance nsteps.  dt_fixed > 0 imposes that dt; otherwise the CFL rule. */
 int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed,
-            double* info /* [t, dt_last, smax, steps, bad_cell] */);
+            double* info /* [t, dt_last, smax, steps, bad_cell, nbound] */);
+/* nbound: faces, since creation, whose half step was replaced by the cell
+ * average because a phase density left the half step's bound (a factor e). */
 /* Time step the CFL rule gives for the present state. */
 int or_cfl_dt(or_grid* g, double cfl, double* dt, double* smax);
 int or_read(const or_grid* g, int primitive, double* out);

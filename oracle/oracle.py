@@ -144,11 +144,11 @@ class OracleGrid:
             raise ValueError("x scheme must be 0 or 1")
 
     def step(self, nsteps: int, cfl: float | None = None, dt: float = 0.0) -> dict:
-        info = np.zeros(5)
+        info = np.zeros(6)
         cfl = self.case.cfl if cfl is None else cfl
         rc = self.lib.or_step(self.h, int(nsteps), float(cfl), float(dt), _dp(info))
         out = dict(t=info[0], dt_last=info[1], smax=info[2], steps=int(info[3]),
-                   bad_cell=int(info[4]), status=rc)
+                   bad_cell=int(info[4]), half_step_bound=int(info[5]), status=rc)
         if rc != 0:
             raise RuntimeError(f"oracle step failed: {out}")
         return out

@@ -422,6 +422,19 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, int ta, int tw, int r
               good = false;
               break;
             }
+            // A half step changes ln(rho_l) by (dt/2)|du/dx| <= cfl <= 1 (dt <=
+            // cfl dx / S, |u_R - u_L| <= 2 S).  A larger change of a phase
+            // density comes from the near-cancelling increments of phi_l and
+            // phi_l rho_l at a trace fraction, and the face falls back.
+            const R hs = s == 0 ? R(-0.5) : R(0.5);
+            const R eb = R(2.718281828459045);
+#pragma unroll
+            for (int l = 0; l < NMAT; ++l) {
+              const R r0 = wc[L::oARHO + l] + hs * sl[L::oARHO + l];
+              const R r1 = tmp[L::oARHO + l];
+              good = good && r1 <= eb * r0 && r0 <= eb * r1;
+            }
+            if (!good) break;
 #pragma unroll
             for (int k = 0; k < NF; ++k) q[k] = cs[k];
 #pragma unroll

@@ -1,13 +1,16 @@
-"""FP32-split against the FP64 oracle on the fronts of the workloads: shock
-fronts (the largest pressure jump) and the fracture front (the extent of the
-critically damaged region) within one cell.
+"""FP32-split against the FP64 oracle on the fronts of the workloads, each
+within one cell: shock fronts, free surfaces and the fracture front (the
+extent of the critically damaged region).
 
 1D spall at its full 1000 cells: compared at step 1500, when the first cells
-reach critical damage, and the shock front again at step 2000. After failure
-the damaged zone evolves chaotically. Measured with the oracle against itself,
-with the initial state perturbed by 1e-15, at step 2000: the pressure differs
-by 11 % (relative L1) and the ends of the damaged region move by up to 16
-cells. Its extent after failure is therefore not compared.
+reach critical damage, and again at step 2000. The shock fronts there are the
+air shocks that the outer surfaces drive into the gas (the outermost cells
+whose pressure departs from the ambient 1e5 Pa by more than 5 %), and the free
+surfaces are where the copper fraction crosses 1/2. Inside the copper, the
+largest pressure jumps at both steps lie in the damaged zone and are several
+of comparable size (5.5e8 and 5.1e8 Pa at step 1500), so their argmax is not
+a front. After failure the damaged zone evolves chaotically; its extent is
+compared at step 1500 only.
 """
 import numpy as np
 import pytest
@@ -26,6 +29,20 @@ def shock_front(p):
     return int(np.argmax(np.abs(np.diff(p))))
 
 
+def gas_fronts(p, ambient=1.0e5):
+    k = np.where(np.abs(p - ambient) > 0.05 * ambient)[0]
+    return int(k[0]), int(k[-1])
+
+
+def surfaces(phi):
+    k = np.where(phi > 0.5)[0]
+    return int(k[0]), int(k[-1])
+
+
+def close(a, b):
+    return all(abs(x - y) <= 1 for x, y in zip(a, b))
+
+
 def test_spall_fronts_within_one_cell():
     case = W.spall_1d(1000)
     names = case.layout.names()
@@ -35,8 +52,9 @@ def test_spall_fronts_within_one_cell():
     g.step(1500)
     o.step(1500)
     a, b = g.read(), o.read()
-    ip, iD = names.index("p"), names.index("D0")
-    assert abs(shock_front(a[ip]) - shock_front(b[ip])) <= 1
+    ip, iD, iphi = names.index("p"), names.index("D0"), names.index("phi0")
+    assert close(gas_fronts(a[ip]), gas_fronts(b[ip]))
+    assert close(surfaces(a[iphi]), surfaces(b[iphi]))
     ca = np.where(a[iD] >= Dc * (1 - 1e-6))[0]
     cb = np.where(b[iD] >= Dc * (1 - 1e-6))[0]
     assert len(cb) > 0, "the oracle should show fracture by step 1500"
@@ -48,7 +66,10 @@ def test_spall_fronts_within_one_cell():
     g.step(500)
     o.step(500)
     a, b = g.read(), o.read()
-    assert abs(shock_front(a[ip]) - shock_front(b[ip])) <= 1
+    # by step 2000 the gas behind the flyer is rarefied up to the left end:
+    # the right front and both surfaces remain
+    assert abs(gas_fronts(a[ip])[1] - gas_fronts(b[ip])[1]) <= 1
+    assert close(surfaces(a[iphi]), surfaces(b[iphi]))
     g.close()
 
 
