@@ -126,3 +126,20 @@ def test_batch_argument_errors():
     b.close()
     for g in (g2, g1, g64, gas):
         g.close()
+
+
+def test_trace_fraction_rings_run_through():
+    # members 4, 51, 56, 59 of the 64-ring ensemble (168^2 .. 728^2, seeds
+    # 104, 151, 156, 159): without the half step's phase-density bound their
+    # FP32-split runs met an inadmissible state at steps 64-103
+    sizes = [128 + 8 * round(80 * i / 63) for i in range(64)]
+    members = [W.ring_2d(sizes[i], seed=100 + i) for i in (4, 51, 56, 59)]
+    grids = [mmfrac.Grid(c, mmfrac.FP32_SPLIT) for c in members]
+    b = mmfrac.Batch(grids)
+    b.step(120)
+    infos = [g.synchronize() for g in grids]
+    b.close()
+    for g, info in zip(grids, infos):
+        assert info["steps"] == 120
+        assert np.all(np.isfinite(g.read(False)))
+        g.close()
