@@ -1321,3 +1321,96 @@ int or_totals(const or_grid* g, double* out) {
   }
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Fragments (Sec. 4.2, 4.3): the paper demarcates fragments by a contour    */
+/* nu = theta of the void volume fraction (theta = 0.25, 0.5, 0.75) and      */
+/* reports each fragment's mass.  This model carries gas, not void, and a   */
+/* crack is critically damaged solid (D >= D_crit, Sec. 3.1).  Reading: the  */
+/* non-intact fraction of a cell is 1 - phi_s (phi_s the summed fraction of  */
+/* the solid materials) where no solid is critically damaged, else 1; a     */
+/* cell is in a fragment when that fraction is below theta, i.e.            */
+/* phi_s > 1 - theta and no solid at D >= D_crit.  Fragments are the        */
+/* components of such cells under face adjacency (periodic faces wrap);     */
+/* a fragment's mass is the sum of dV (phi rho)_l over its cells and solid  */
+/* materials.  Labels: the smallest cell index of the component.  D comes   */
+/* back as (phi rho D) / (phi rho), so a cell capped at D_crit can read one  */
+/* rounding below it: critical means D >= D_crit (1 - 1e-6).                 */
+/* ------------------------------------------------------------------------ */
+
+static int in_fragment(const or_grid* g, double theta, long c) {
+  const double* U = g->U;
+  const long n = g->ncell;
+  double phis = 0.0, last = 1.0;
+  for (int l = 0; l < g->nmat; ++l) {
+    const double phi = l + 1 < g->nmat ? U[(size_t)(g->o_phi + l) * n + c] : last;
+    if (l + 1 < g->nmat) last -= phi;
+    if (g->mat[l].eos != 1) continue;
+    phis += phi;
+    const int h = g->hslot[l];
+    if (is_damaged(&g->mat[l]) && h >= 0) {
+      const double arho = U[(size_t)(g->o_arho + l) * n + c];
+      const double D = U[(size_t)(g->o_hist + 2 * h + 1) * n + c] / arho;
+      if (D >= g->mat[l].D_crit * (1.0 - 1e-6)) return 0;
+    }
+  }
+  return phis > 1.0 - theta;
+}
+
+long or_fragments(const or_grid* g, double theta, long* labels, long* frag_label,
+                  long* frag_cells, double* frag_mass, long max_frag) {
+  const long n = g->ncell;
+  double dV = 1.0;
+  for (int k = 0; k < g->dim; ++k) dV *= g->dx[k];
+  long* lab = labels ? labels : malloc(sizeof(long) * (size_t)n);
+  long* queue = malloc(sizeof(long) * (size_t)n);
+  for (long c = 0; c < n; ++c) lab[c] = in_fragment(g, theta, c) ? n : -1; /* n: unvisited */
+  long nfrag = 0;
+  for (long c0 = 0; c0 < n; ++c0) {
+    if (lab[c0] != n) continue;
+    /* breadth-first search from the smallest unvisited member */
+    long head = 0, tail = 0, cells = 0;
+    double s = 0.0, comp = 0.0;
+    lab[c0] = c0;
+    queue[tail++] = c0;
+    while (head < tail) {
+      const long c = queue[head++];
+      ++cells;
+      for (int l = 0; l < g->nmat; ++l) {
+        if (g->mat[l].eos != 1) continue;
+        const double y = g->U[(size_t)(g->o_arho + l) * n + c] * dV - comp;
+        const double t = s + y;
+        comp = (t - s) - y;
+        s = t;
+      }
+      long rest = c, stride = 1;
+      for (int d = 0; d < g->dim; ++d) {
+        const long nd = g->n[d];
+        const long i = rest % nd;
+        rest /= nd;
+        for (int side = 0; side < 2; ++side) {
+          long j = side == 0 ? i - 1 : i + 1;
+          if (j < 0 || j >= nd) {
+            if (g->bc[d][side] != OR_BC_PERIODIC) continue;
+            j = j < 0 ? nd - 1 : 0;
+          }
+          const long nb = c + (j - i) * stride;
+          if (lab[nb] == n) {
+            lab[nb] = c0;
+            queue[tail++] = nb;
+          }
+        }
+        stride *= nd;
+      }
+    }
+    if (nfrag < max_frag) {
+      if (frag_label) frag_label[nfrag] = c0;
+      if (frag_cells) frag_cells[nfrag] = cells;
+      if (frag_mass) frag_mass[nfrag] = s;
+    }
+    ++nfrag;
+  }
+  free(queue);
+  if (!labels) free(lab);
+  return nfrag;
+}

@@ -88,6 +88,13 @@ void or_set_threads(int n);
  * from the state at the step's start (Sec. 3.2.1).  OR_EINVAL otherwise. */
 int or_set_x_scheme(or_grid* g, int scheme);
 
+/* Fragments at void cut-off theta (Sec. 4.2, 4.3; reading in the source):
+ * labels[ncell] (may be NULL) gets each cell's fragment label, the smallest
+ * cell index of its fragment, or -1; the first max_frag fragments in label
+ * order get label, cell count and mass.  Returns the number of fragments. */
+long or_fragments(const or_grid* g, double theta, long* labels, long* frag_label,
+                  long* frag_cells, double* frag_mass, long max_frag);
+
 /* ---- single-point routines exported for the pins ---- */
 void or_thermo(const or_material* m, double rho, double psi, double J2,
                double* out /* e_ref, p_ref, dpref_drho, G, Gamma */);

@@ -78,6 +78,8 @@ def load():
         lib.or_totals.argtypes = [ctypes.c_void_p, P(d)]
         lib.or_set_threads.argtypes = [i]
         lib.or_set_x_scheme.argtypes = [ctypes.c_void_p, i]
+        lib.or_fragments.restype = L
+        lib.or_fragments.argtypes = [ctypes.c_void_p, d, P(L), P(L), P(L), P(d), L]
         lib.or_thermo.argtypes = [P(Material), d, d, d, P(d)]
         lib.or_hencky.argtypes = [P(d), P(d), P(d), P(d)]
         lib.or_lookup.restype = d
@@ -169,6 +171,22 @@ class OracleGrid:
     def write_conserved(self, U: np.ndarray) -> None:
         U = np.ascontiguousarray(U, dtype=np.float64)
         self.lib.or_write_conserved(self.h, _dp(U))
+
+    def fragments(self, theta: float = 0.5, max_frag: int | None = None):
+        """Fragments of the present state at void cut-off theta (Sec. 4.2, 4.3):
+        per-cell labels (smallest cell index of the fragment, -1 outside) and,
+        in label order, each fragment's label, cell count and solid mass."""
+        PL = ctypes.POINTER(ctypes.c_long)
+        labels = np.empty(self.ncell, dtype=np.int64)
+        cap = self.ncell if max_frag is None else int(max_frag)
+        fl = np.empty(max(cap, 1), dtype=np.int64)
+        fc = np.empty(max(cap, 1), dtype=np.int64)
+        fm = np.empty(max(cap, 1))
+        nf = self.lib.or_fragments(self.h, float(theta), labels.ctypes.data_as(PL),
+                                   fl.ctypes.data_as(PL), fc.ctypes.data_as(PL), _dp(fm), cap)
+        k = min(nf, cap)
+        return labels, dict(n=int(nf), label=fl[:k].copy(), cells=fc[:k].copy(),
+                            mass=fm[:k].copy())
 
     def totals(self) -> np.ndarray:
         out = np.zeros(len(self.case.materials) + 4)

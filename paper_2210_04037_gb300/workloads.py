@@ -373,4 +373,67 @@ def cylinder_3d(n: int = 256, seed: int = 3, sd: float = 0.1, v: float = 250.0,
     return case
 
 
+def _stratified(seed: int, k: int, jitter: float = 0.6) -> np.ndarray:
+    """k positions in [0, 1): one per stratum, jittered by +-jitter/2 of it."""
+    return np.mod((np.arange(k) + jitter * (uniform01(seed, k) - 0.5)) / k, 1.0)
+
+
+def _crack_mask(case: Case, r: np.ndarray, theta: np.ndarray, angles: np.ndarray,
+                zc: np.ndarray, z: Optional[np.ndarray], half: float) -> np.ndarray:
+    """Cells whose centre lies within `half` of a radial crack plane (angles)
+    or of a crack plane z = const (zc, periodic in z)."""
+    m = np.zeros(theta.shape, dtype=bool)
+    for a in angles:
+        d = np.abs(np.mod(theta - a + np.pi, 2.0 * np.pi) - np.pi)
+        m |= (d * r < half) & (d < 0.5 * np.pi)
+    if z is not None and len(zc):
+        L = case.hi[2] - case.lo[2]
+        for c in zc:
+            d = np.abs(np.mod(z - c + 0.5 * L, L) - 0.5 * L)
+            m |= d < half
+    return m
+
+
+def fractured_ring(n: int = 512, cracks: int = 12, seed: int = 11, **kw) -> Case:
+    """The expanding-ring geometry at fragmentation (Sec. 4.3), input for
+    fragment labelling: the annulus cut by `cracks` radial cracks of
+    critically damaged metal (D = D_crit, as the RK4 cap leaves it) at
+    stratified seeded angles, 1.5 cells wide; D ~ U(0, 0.9 D_crit) elsewhere.
+    Solid fractions from 5 x 5 sub-sampling are multiples of 1/25, so no cell
+    lies on a cut-off of 0.25, 0.5 or 0.75."""
+    case = ring_2d(n, seed=seed, **kw)
+    lay = case.layout
+    r0, r1 = kw.get("r0", 0.020), kw.get("r1", 0.024)
+    x, y = case.centres()
+    dx = case.dx[0]
+    case.prim[lay.o_phi] = np.clip(_annulus_fraction(x, y, dx, r0, r1, 5), PHI_MIN, 1.0 - PHI_MIN)
+    Dc = case.materials[0]["D_crit"]
+    crack = _crack_mask(case, np.hypot(x, y), np.arctan2(y, x),
+                        2.0 * np.pi * _stratified(seed, cracks), np.zeros(0), None, 0.75 * dx)
+    case.prim[lay.o_hist + 1] = np.where(crack, Dc, 0.9 * Dc * uniform01(seed + 1, case.ncell))
+    return case
+
+
+def fractured_cylinder(n: int = 256, cracks_theta: int = 8, cracks_z: int = 3, seed: int = 13,
+                       nz: Optional[int] = None, **kw) -> Case:
+    """The thin-cylinder geometry at fragmentation, input for fragment
+    labelling: the shell cut by `cracks_theta` axial and `cracks_z`
+    circumferential cracks of critically damaged metal (D = D_crit) at
+    stratified seeded positions, 1.5 cells wide, periodic in z, so that it
+    falls into cracks_theta x cracks_z patches; D ~ U(0, 0.9 D_crit)
+    elsewhere; solid fractions from 5 x 5 sub-sampling (multiples of 1/25)."""
+    case = cylinder_3d(n, seed=seed, nz=nz, **kw)
+    lay = case.layout
+    r0, r1 = kw.get("r0", 0.018), kw.get("r1", 0.020)
+    x, y, z = case.centres()
+    dx = case.dx[0]
+    case.prim[lay.o_phi] = np.clip(_annulus_fraction(x, y, dx, r0, r1, 5), PHI_MIN, 1.0 - PHI_MIN)
+    Dc = case.materials[0]["D_crit"]
+    zc = case.lo[2] + (case.hi[2] - case.lo[2]) * _stratified(seed + 2, cracks_z)
+    crack = _crack_mask(case, np.hypot(x, y), np.arctan2(y, x),
+                        2.0 * np.pi * _stratified(seed, cracks_theta), zc, z, 0.75 * dx)
+    case.prim[lay.o_hist + 1] = np.where(crack, Dc, 0.9 * Dc * uniform01(seed + 1, case.ncell))
+    return case
+
+
 WORKLOADS = {"spall_1d": spall_1d, "ring_2d": ring_2d, "cylinder_3d": cylinder_3d}
