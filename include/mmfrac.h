@@ -153,6 +153,37 @@ mm_status mm_synchronize(mm_grid* g, mm_step_info* info);
 enum { MM_X_SWEEP = 0, MM_X_WENO3_RK3 = 1 };
 mm_status mm_set_x_transport(mm_grid* g, int scheme);
 
+/* Fragments of the present state (Sec. 4.2, 4.3 demarcate fragments by the
+ * contour nu = theta of the void volume fraction, theta = 0.25, 0.5, 0.75,
+ * and report fragment masses).  This model carries gas in place of void and
+ * a crack is critically damaged solid (Sec. 3.1), so a cell belongs to a
+ * fragment when the summed volume fraction of its solid (Romenskii)
+ * materials exceeds 1 - theta and no damaged solid in it has
+ * D >= D_crit (1 - 1e-6) (D comes back as (phi rho D)/(phi rho), one rounding
+ * below a cap at D_crit).  Fragments are the components of such cells under
+ * face adjacency; periodic faces wrap.  A fragment's label is its smallest
+ * linear cell index (x fastest), its mass sum dV (phi rho) over its cells
+ * and solids (FP64; summed in no fixed order).
+ *   theta      cut-off in (0, 1].
+ *   labels     host int64[labels_len] or NULL; labels_len must equal the
+ *              cell count.  Receives each cell's label or -1.
+ *   frags      host array of max_frags records or NULL (max_frags 0).
+ *              Receives the first min(max_frags, *n_frags) fragments in
+ *              label order.
+ *   n_frags    receives the number of fragments (may exceed max_frags).
+ * Runs on the grid's stream and synchronises.  The first call allocates
+ * 16 bytes per cell of scratch, kept until mm_destroy.  Takes grids of
+ * fewer than 2^31 cells.  Errors: MM_EINVAL (arguments), MM_ESTATE (before
+ * mm_set_materials), MM_ENOMEM, MM_ETIMEOUT (a union that did not settle,
+ * which the labelling's invariants exclude), MM_ECUDA. */
+typedef struct {
+  int64_t label; /* smallest cell index of the fragment */
+  int64_t cells; /* number of cells */
+  double mass;   /* solid mass, kg (per metre in 2D, per m^2 in 1D) */
+} mm_fragment;
+mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_len,
+                       mm_fragment* frags, size_t max_frags, int64_t* n_frags);
+
 /* Copy fields to host_dst ([popcount(field_mask)][ncell] doubles, fields
  * in order; bit f of field_mask selects field f, ~0 for all).
  * primitive = 1 returns the primitive fields, 0 the conserved ones.

@@ -22,7 +22,7 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmfrac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"mm_api.cu": [], "mm_noalloc.cu": [], "mm_server.cu": []}
+UNITS = {"mm_api.cu": [], "mm_noalloc.cu": [], "mm_server.cu": [], "mm_frag.cu": []}
 for _d in (1, 2, 3):
     for _b in ("", "_batch"):
         UNITS[f"mm_fp64_d{_d}{_b}.cu"] = ["--fmad=false"]

@@ -117,6 +117,17 @@ struct mm_grid {
   // X by WENO3 + RK3: scheme and its scratch (velocities, two stages)
   int xscheme = MM_X_SWEEP;
   void* xs[3] = {nullptr, nullptr, nullptr};
+  // fragment labelling scratch (allocated on the first mm_fragments):
+  // per-cell parents, fragment numbers of the roots and solid masses, the
+  // per-block root offsets, and per-fragment labels, cell counts and masses
+  int* fparent = nullptr;
+  int* ffid = nullptr;
+  double* fcm = nullptr;
+  int* fboff = nullptr;
+  long long* flab = nullptr;
+  unsigned long long* fcnt = nullptr;
+  double* fmas = nullptr;
+  long long fcap = 0;
 };
 
 namespace {
@@ -690,11 +701,117 @@ mm_status mm_set_x_transport(mm_grid* g, int scheme) {
   return MM_OK;
 }
 
+mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_len,
+                       mm_fragment* frags, size_t max_frags, int64_t* n_frags) {
+  if (!g || !n_frags) return fail(MM_EINVAL, "mm_fragments: null argument");
+  if (!(theta > 0.0 && theta <= 1.0))
+    return fail(MM_EINVAL, "mm_fragments: the cut-off must lie in (0, 1], got %g", theta);
+  if (!g->ready) return fail(MM_ESTATE, "mm_fragments before mm_set_materials");
+  if (labels && labels_len != (size_t)g->ncell)
+    return fail(MM_EINVAL, "mm_fragments: labels holds %zu entries, the grid %lld cells",
+                labels_len, g->ncell);
+  if (max_frags > 0 && !frags) return fail(MM_EINVAL, "mm_fragments: null fragment array");
+  if (g->ncell >= (1ll << 31))
+    return fail(MM_EINVAL, "mm_fragments takes grids of fewer than 2^31 cells");
+  const long long nblk = (g->ncell + MM_FRAG_CELLS - 1) / MM_FRAG_CELLS;
+  if (!g->fparent) {
+    const size_t n = (size_t)g->ncell;
+    if (cudaMalloc(&g->fparent, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(&g->ffid, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc(&g->fcm, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&g->fboff, sizeof(int) * (size_t)(nblk + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(g->fparent);
+      cudaFree(g->ffid);
+      cudaFree(g->fcm);
+      cudaFree(g->fboff);
+      g->fparent = g->ffid = g->fboff = nullptr;
+      g->fcm = nullptr;
+      return fail(MM_ENOMEM, "device allocation of the fragment scratch failed");
+    }
+  }
+  KArgs a = args_for(g);
+  a.frag = g->fparent;
+  a.fmass = g->fcm;
+  a.fcut = theta;
+  CUDA_TRY(go(g, 8, 0, 0, a));
+  CUDA_TRY(mm_frag_label(a, g->stream));
+  CUDA_TRY(mm_frag_count(a, g->fboff, g->stream));
+  g->launches += 4;
+  int nf = 0;
+  CUDA_TRY(cudaMemcpyAsync(&nf, g->fboff + nblk, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  mm_status st = check_device_error(g, "mm_fragments");
+  if (st != MM_OK) return st;
+  if (nf > g->fcap) {
+    cudaFree(g->flab);
+    cudaFree(g->fcnt);
+    cudaFree(g->fmas);
+    g->flab = nullptr;
+    g->fcnt = nullptr;
+    g->fmas = nullptr;
+    g->fcap = 0;
+    const long long cap = nf + nf / 4 + 64;
+    if (cudaMalloc(&g->flab, sizeof(long long) * cap) != cudaSuccess ||
+        cudaMalloc(&g->fcnt, sizeof(unsigned long long) * cap) != cudaSuccess ||
+        cudaMalloc(&g->fmas, sizeof(double) * cap) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(g->flab);
+      cudaFree(g->fcnt);
+      cudaFree(g->fmas);
+      g->flab = nullptr;
+      g->fcnt = nullptr;
+      g->fmas = nullptr;
+      return fail(MM_ENOMEM, "device allocation of %d fragment records failed", nf);
+    }
+    g->fcap = cap;
+  }
+  if (nf > 0) {
+    CUDA_TRY(cudaMemsetAsync(g->fcnt, 0, sizeof(unsigned long long) * nf, g->stream));
+    CUDA_TRY(cudaMemsetAsync(g->fmas, 0, sizeof(double) * nf, g->stream));
+    CUDA_TRY(mm_frag_collect(a, g->fboff, g->ffid, g->flab, g->fcnt, g->fmas, g->stream));
+    g->launches += 2;
+  }
+  const size_t k = max_frags < (size_t)nf ? max_frags : (size_t)nf;
+  std::vector<long long> hl(k);
+  std::vector<unsigned long long> hc(k);
+  std::vector<double> hm(k);
+  std::vector<int> hp(labels ? (size_t)g->ncell : 0);
+  if (k > 0) {
+    CUDA_TRY(cudaMemcpyAsync(hl.data(), g->flab, sizeof(long long) * k, cudaMemcpyDeviceToHost,
+                             g->stream));
+    CUDA_TRY(cudaMemcpyAsync(hc.data(), g->fcnt, sizeof(unsigned long long) * k,
+                             cudaMemcpyDeviceToHost, g->stream));
+    CUDA_TRY(cudaMemcpyAsync(hm.data(), g->fmas, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                             g->stream));
+  }
+  if (labels)
+    CUDA_TRY(cudaMemcpyAsync(hp.data(), g->fparent, sizeof(int) * (size_t)g->ncell,
+                             cudaMemcpyDeviceToHost, g->stream));
+  st = check_device_error(g, "mm_fragments");
+  if (st != MM_OK) return st;
+  for (size_t i = 0; i < k; ++i) {
+    frags[i].label = hl[i];
+    frags[i].cells = (int64_t)hc[i];
+    frags[i].mass = hm[i];
+  }
+  if (labels)
+    for (long long c = 0; c < g->ncell; ++c) labels[c] = hp[(size_t)c];
+  *n_frags = nf;
+  return MM_OK;
+}
+
 mm_status mm_destroy(mm_grid* g) {
   if (!g) return MM_OK;
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   for (int i = 0; i < 3; ++i) cudaFree(g->xs[i]);
+  cudaFree(g->fparent);
+  cudaFree(g->ffid);
+  cudaFree(g->fcm);
+  cudaFree(g->fboff);
+  cudaFree(g->flab);
+  cudaFree(g->fcnt);
+  cudaFree(g->fmas);
   free_state(g);
   cudaFree(g->info);
   cudaFree(g->err);

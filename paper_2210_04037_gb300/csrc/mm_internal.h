@@ -77,9 +77,27 @@ struct KArgs {
   double* prim;        // [nfield][ncell] doubles for init / read
   double* partial;     // per-block partial totals
   void* xs[3];         // X by WENO3 + RK3: cell velocities, stage 1, stage 2 ([dim][ncell], R)
+  int* frag;           // fragment labelling: per-cell parent index, -1 outside fragments
+  double* fmass;       // fragment labelling: per-cell solid mass dV sum (phi rho)_solid
+  double fcut;         // fragment labelling: void cut-off theta
 };
 
 static_assert(sizeof(KArgs) % 8 == 0, "KArgs is copied as 8-byte words");
+
+// Fragment labelling (mm_frag.cu), after the marking kernel has set
+// a.frag[i] = i on fragment cells and -1 elsewhere (a.ncell < 2^31):
+// mm_frag_label joins face neighbours (periodic faces wrap) by union-find
+// with links to the smaller root, then points every cell at its root, the
+// smallest cell index of its fragment.  mm_frag_count writes, per block of
+// MM_FRAG_CELLS cells, the exclusive count of roots before it (boff[b],
+// nblocks + 1 entries) and the total to boff[nblocks].  mm_frag_collect
+// numbers the roots in index order (fid) and accumulates each fragment's
+// label, cell count and mass.
+#define MM_FRAG_CELLS 2048
+cudaError_t mm_frag_label(const KArgs& a, cudaStream_t s);
+cudaError_t mm_frag_count(const KArgs& a, int* boff, cudaStream_t s);
+cudaError_t mm_frag_collect(const KArgs& a, const int* boff, int* fid, long long* flabel,
+                            unsigned long long* fcells, double* fmass, cudaStream_t s);
 
 // One batched launch over the members of a batch: member m owns work units
 // [start[m], start[m+1]) (tiles of a sweep, or chunks of `chunk` cells) and

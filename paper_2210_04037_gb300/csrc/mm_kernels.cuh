@@ -1550,4 +1550,51 @@ __global__ void __launch_bounds__(256) k_totals(KArgs a) {
   }
 }
 
+// ----------------------------------------------------------- fragments ----
+// Marks the cells of fragments at void cut-off a.fcut (Sec. 4.2, 4.3
+// demarcate fragments by a contour of the void fraction; in this gas-filled
+// model a cell is in a fragment when its solid fraction exceeds 1 - theta
+// and no solid in it is critically damaged, D >= D_crit within 1e-6 because
+// D comes back as (phi rho D) / (phi rho)): a.frag[cell] = cell there and
+// -1 elsewhere; a.fmass[cell] = dV sum (phi rho) over the solids.
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_frag_mark(KArgs a) {
+  typedef typename P::R R;
+  typedef typename P::S S;
+  typedef typename P::X XT;
+  typedef Phys<P, DIM, NMAT, NH> PH;
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NX = PH::NX;
+  const S* U = (const S*)a.Uin;
+  double dV = 1.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) dV *= a.dx[k];
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+       cell += (long long)gridDim.x * blockDim.x) {
+    XT cx[NX], phid[NMAT];
+    cx[0] = XT(0);
+#pragma unroll
+    for (int l = 0; l < PH::NPX; ++l) cx[1 + l] = XT(U[phislot<P, DIM, NMAT, NH>(a, l, cell)]);
+    PH::fractions(cx, phid);
+    double phis = 0.0, ms = 0.0;
+    bool crit = false;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      if (a.mat[l].eos != 1) continue;
+      phis += double(phid[l]);
+      const R arho = R(U[(long long)(L::oARHO + l) * a.ncell + cell]);
+      ms += double(arho) * dV;
+#pragma unroll
+      for (int h = 0; h < NH; ++h)
+        if (h == a.hslot[l] && a.mat[l].damage != 0) {
+          const R D = R(U[(long long)(L::oH + 2 * h + 1) * a.ncell + cell]) / arho;
+          crit = crit || D >= R(a.mat[l].D_crit * (1.0 - 1e-6));
+        }
+    }
+    const bool in = phis > 1.0 - a.fcut && !crit;
+    a.frag[cell] = in ? (int)cell : -1;
+    a.fmass[cell] = in ? ms : 0.0;
+  }
+}
+
 }  // namespace mm

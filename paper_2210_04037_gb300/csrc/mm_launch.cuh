@@ -99,6 +99,10 @@ struct Launch {
         k_xstage<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a, flag);
         break;
       }
+      case 8: {
+        k_frag_mark<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a);
+        break;
+      }
       case 4: {
         k_sources<P, DIM, NMAT, NH><<<grid_for(a.ncell, 128), 128, 0, s>>>(a);
         break;

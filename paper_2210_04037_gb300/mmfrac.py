@@ -71,6 +71,10 @@ class ServerInfo(ctypes.Structure):
                 ("retired", ctypes.c_int64)]
 
 
+class Fragment(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_int64), ("cells", ctypes.c_int64), ("mass", ctypes.c_double)]
+
+
 class StepInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("smax", ctypes.c_double),
                 ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
@@ -109,6 +113,9 @@ def load(path: str = LIB_PATH):
         lib.mm_step_async.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         lib.mm_set_x_transport.argtypes = [vp, ctypes.c_int]
         lib.mm_set_x_transport.restype = ctypes.c_int
+        lib.mm_fragments.argtypes = [vp, ctypes.c_double, P(ctypes.c_int64), ctypes.c_size_t,
+                                     P(Fragment), ctypes.c_size_t, P(ctypes.c_int64)]
+        lib.mm_fragments.restype = ctypes.c_int
         lib.mm_batch_create.argtypes = [P(vp), ctypes.c_int, vp, P(vp)]
         lib.mm_batch_set_options.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
         lib.mm_batch_step.argtypes = [vp, ctypes.c_int, ctypes.c_double]
@@ -263,6 +270,26 @@ def conserved_totals(grid, nmat: int) -> np.ndarray:
     return out
 
 
+def fragments(grid, theta: float = 0.5, labels: bool = True, max_frags: int | None = None):
+    """Fragments at void cut-off theta (mm_fragments): per-cell labels
+    (int64, -1 outside fragments; None unless asked for) and, in label order,
+    each fragment's label, cell count and mass."""
+    ncell = int(load().mm_num_cells(grid))
+    lab = np.empty(ncell, dtype=np.int64) if labels else None
+    cap = ncell if max_frags is None else int(max_frags)
+    recs = (Fragment * max(cap, 1))()
+    n = ctypes.c_int64()
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    _check(load().mm_fragments(grid, float(theta),
+                               lab.ctypes.data_as(P64) if labels else None,
+                               ncell if labels else 0, recs, cap, ctypes.byref(n)))
+    k = min(n.value, cap)
+    arr = np.frombuffer(recs, dtype=np.dtype([("label", "<i8"), ("cells", "<i8"),
+                                              ("mass", "<f8")]), count=k)
+    return lab, dict(n=int(n.value), label=arr["label"].copy(), cells=arr["cells"].copy(),
+                     mass=arr["mass"].copy())
+
+
 def destroy(grid) -> None:
     if grid:
         _check(load().mm_destroy(grid))
@@ -332,6 +359,9 @@ class Grid:
 
     def launches(self) -> int:
         return kernel_launches(self.h)
+
+    def fragments(self, theta: float = 0.5, labels: bool = True, max_frags: int | None = None):
+        return fragments(self.h, theta, labels, max_frags)
 
     def close(self) -> None:
         if getattr(self, "h", None):
