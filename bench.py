@@ -7,12 +7,14 @@ headline) beside the FP64 path, with the HBM roofline fraction of the
 dominant kernel.
 
     python bench.py [--gpus N --steps K --warmup W]
-                    [--workload ring_2d|cylinder_3d|spall_1d|ensemble_2d]
+                    [--workload ring_2d|cylinder_3d|spall_1d|ensemble_2d|serve|fragments]
                     [--precision fp32split|fp64] [--impl mmfrac|reference]
 
 ``--workload ensemble_2d`` times a batch of seeded 2D rings of uneven size
 (``--size`` members, default 64) stepped together, beside the same members
-stepped one at a time in FP32-split and in FP64.
+stepped one at a time in FP32-split and in FP64.  ``--workload fragments``
+times the fragment labelling (cells labelled/s) of a fractured 3D shell
+(``--size`` cells per edge, default 256), with its own metric.
 
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload (the step does not shard on one grid here: replicas only); the
@@ -41,7 +43,9 @@ from paper_2210_04037_gb300 import workloads as W  # noqa: E402
 METRIC = ("cell-updates/s and % HBM roofline at 1 GB300, FP32-split vs FP64 at stated error")
 L2_BYTES = 129 * 2 ** 20
 DEFAULT_SIZE = {"ring_2d": 512, "cylinder_3d": 256, "spall_1d": 1000, "ensemble_2d": 64,
-                "serve": 24}
+                "serve": 24, "fragments": 256}
+FRAG_METRIC = "fragment labelling at void cut-off 0.5: cells labelled/s at 1 GB300"
+FRAG_CUT = 0.5
 WORKLOAD_TEXT = {
     "ring_2d": "2D expanding ring, {n}x{n} cells, Al-H32 annulus r 20-24 mm at 200 m/s in air, "
                "simple damage, phi0 ~ U(0.9,1.1) on a 0.5 mm lattice",
@@ -55,6 +59,10 @@ WORKLOAD_TEXT = {
     "serve": "served runs: {n} requests with Poisson arrivals (16/s, seeded) mixing 1D spall "
              "(1e3..1e4 cells, 400 steps), 2D ring (256^2..1024^2, 60 steps) and 3D cylinder "
              "(128^3..256^3, 10 steps), FP32-split, memory-based admission, continuous batching",
+    "fragments": "fragment labelling (mm_fragments, void cut-off 0.5) of a 3D thin-cylinder shell "
+                 "at fragmentation, {n}^3 cells: CuBe shell r 18-20 mm, periodic in z, cut by 12 "
+                 "axial and 4 circumferential cracks 1.5 cells wide at D_crit (48 patches), "
+                 "D ~ U(0, 0.9 D_crit) elsewhere",
 }
 
 
@@ -118,7 +126,27 @@ def measured_traffic(workload: str, n: int, precision: str, kernel: str):
     return t
 
 
+def fragment_case(n: int):
+    return W.fractured_cylinder(n, 12, 4, seed=6)
+
+
+def frag_bytes_per_cell(precision: int, member_frac: float) -> dict:
+    """Algorithmic DRAM bytes per cell of each labelling kernel kind.
+    mark: the stored fractions (FP64: the N-1 stored ones; FP32-split: all
+    N), the solid's phi rho and phi rho D read, a parent index (4 B) written,
+    and a mass (8 B) on fragment cells.  union: parents read by the merge and
+    read and written (members) by the root pass.  count: parents read.
+    collect: parents read twice (numbering, sums) and the members' masses."""
+    e = 8 if precision == W.FP64 else 4
+    nfrac = 1 if precision == W.FP64 else 2
+    return {"frag_mark": (nfrac + 2) * e + 4 + 8 * member_frac,
+            "frag_union": 8 + 4 * member_frac,
+            "frag_count": 4, "frag_collect": 8 + 8 * member_frac}
+
+
 def make_case(name: str, n: int):
+    if name == "fragments":
+        return fragment_case(n)
     if name == "ensemble_2d":
         # the oracle's sample of an ensemble: its smallest member
         return ensemble_cases(n)[0]
@@ -249,6 +277,8 @@ def run_reference(args, rank: int, world: int):
     case = make_case(args.workload, n)
     cores = os.cpu_count() or 1
     g = OracleGrid(case, threads=cores)
+    if args.workload == "fragments":
+        return run_reference_fragments(args, world, case, g, n)
     g.step(args.warmup)
     t0 = time.perf_counter()
     g.step(args.steps)
@@ -267,6 +297,146 @@ def run_reference(args, rank: int, world: int):
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_reference_fragments(args, world: int, case, g, n: int):
+    """The oracle's labelling (single-threaded breadth-first search) of the
+    full workload, as many calls as fit in about 20 s (at most --steps)."""
+    g.fragments(FRAG_CUT)
+    t0 = time.perf_counter()
+    calls = 0
+    while calls < max(1, args.steps) and (calls == 0 or time.perf_counter() - t0 < 20.0):
+        g.fragments(FRAG_CUT)
+        calls += 1
+    el = time.perf_counter() - t0
+    value = case.ncell * calls / el
+    sample = f"{calls} labellings of the full {case.ncell}-cell workload after one untimed"
+    line = {"impl": "reference", "metric": FRAG_METRIC, "value": value, "unit": "cells/s",
+            "n_gpus": world, "steps": calls, "warmup": 1, "ms_per_step": 1e3 * el / calls,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["fragments"].format(n=n), "cells": case.ncell,
+                       "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fragments(args, rank: int, world: int):
+    """Device time of mm_fragments calls on a resident fractured state, the
+    per-kernel times, the end-to-end call from host buffers, and the
+    oracle's labelling of the same state beside it."""
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.size or DEFAULT_SIZE["fragments"]
+    case = fragment_case(n)
+    prec = W.FP32_SPLIT if args.precision == "fp32split" else W.FP64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sbytes = state_bytes(case, prec)
+    flush = None
+    if sbytes < 2 * L2_BYTES:
+        flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    g = mmfrac.Grid(case, prec, stream=stream.cuda_stream)
+    for _ in range(max(1, args.warmup)):
+        lab, f = g.fragments(FRAG_CUT, labels=True, max_frags=0)
+    member_frac = float((lab >= 0).mean())
+    nfrag = f["n"]
+    calls = args.steps
+    start = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    stop = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    with ClockSampler(local) as clk:
+        for s in range(calls):
+            if flush is not None:
+                flush.add_(1)
+            l0 = g.launches()
+            start[s].record(stream)
+            g.fragments(FRAG_CUT, labels=False, max_frags=0)
+            stop[s].record(stream)
+            launches += g.launches() - l0
+        torch.cuda.synchronize()
+        # the same calls with events around each kernel kind
+        mmfrac.profile_enable(g.h, True)
+        mmfrac.profile_read(g.h, reset=True)
+        for s in range(calls):
+            if flush is not None:
+                flush.add_(1)
+            g.fragments(FRAG_CUT, labels=False, max_frags=0)
+        prof = mmfrac.profile_read(g.h, reset=True)
+        mmfrac.profile_enable(g.h, False)
+        torch.cuda.synchronize()
+    g.close()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(start, stop)), dist)
+    value = world * case.ncell * calls / (ms * 1e-3)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    per_cell = frag_bytes_per_cell(prec, member_frac)
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    algo = per_cell[dom] * case.ncell
+    peak, peak_kind = read_peaks()
+    achieved = algo / (dom_ms * 1e-3) / 1e9
+    # end to end: the state uploaded from pinned host memory, labelled, the
+    # labels read back (4 B per cell from the device), the grid released
+    prim_pinned = torch.from_numpy(np.ascontiguousarray(case.prim)).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        h = mmfrac.create_grid(case, prec, stream.cuda_stream)
+        mmfrac.set_materials(h, case, prim=prim_pinned.numpy())
+        mmfrac.fragments(h, FRAG_CUT, labels=True, max_frags=nfrag)
+        mmfrac.destroy(h)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    h2d = case.prim.nbytes + (case.phi0.nbytes if case.phi0 is not None else 0)
+    d2h = 4 * case.ncell + 24 * nfrag + 4
+    line = {
+        "metric": FRAG_METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+        "steps": calls, "warmup": args.warmup, "ms_per_step": ms / calls,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == W.FP32_SPLIT else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT["fragments"].format(n=n), "cells": case.ncell,
+                   "precision": args.precision, "fragments": nfrag,
+                   "member_fraction": member_frac,
+                   "l2": "flushed between calls (256 MiB write)" if flush is not None
+                   else "state larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": measured_traffic("fragments", n, args.precision, dom),
+                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": dom_ms},
+        "kernels_ms_per_call": {k: v[0] / calls for k, v in kinds.items()},
+        "e2e": {"value": world * case.ncell * calls / e2e_s, "unit": "cells/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import OracleGrid
+        o = OracleGrid(case)
+        t0 = time.perf_counter()
+        o.fragments(FRAG_CUT)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": case.ncell / el, "unit": "cells/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"one labelling of the full {case.ncell}-cell workload "
+                                          f"({el:.1f} s wall, single-threaded search)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True, x_transport=0):
@@ -492,6 +662,8 @@ def run_gpu(args, rank: int, world: int):
         return run_ensemble(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "fragments":
+        return run_fragments(args, rank, world)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None

@@ -350,12 +350,15 @@ int64_t mm_kernel_launches(const mm_grid* g);
  * grid's stream and accumulates the elapsed device time per kernel kind:
  * MM_K_CFL, MM_K_DT, MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES,
  * MM_K_XTRANSPORT (the X update of MM_X_WENO3_RK3, its four launches and the
- * copy together).
+ * copy together); mm_fragments likewise: MM_K_FRAG_MARK (membership and
+ * masses), MM_K_FRAG_UNION (the union and root passes), MM_K_FRAG_COUNT (the
+ * ordered root count), MM_K_FRAG_COLLECT (numbering and per-fragment sums).
  * mm_profile_read copies min(n, MM_K_COUNT) accumulated milliseconds and
  * launch counts (either pointer may be NULL) and, if reset = 1, zeroes them.
  * Errors: MM_EINVAL, MM_ECUDA. */
 enum { MM_K_CFL = 0, MM_K_DT = 1, MM_K_SWEEP_X = 2, MM_K_SWEEP_Y = 3, MM_K_SWEEP_Z = 4,
-       MM_K_SOURCES = 5, MM_K_XTRANSPORT = 6, MM_K_COUNT = 7 };
+       MM_K_SOURCES = 5, MM_K_XTRANSPORT = 6, MM_K_FRAG_MARK = 7, MM_K_FRAG_UNION = 8,
+       MM_K_FRAG_COUNT = 9, MM_K_FRAG_COLLECT = 10, MM_K_COUNT = 11 };
 mm_status mm_profile_enable(mm_grid* g, int enable);
 mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int reset);
 

@@ -734,9 +734,25 @@ mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_
   a.frag = g->fparent;
   a.fmass = g->fcm;
   a.fcut = theta;
+  a.fthr = 1.0 - theta;
+  a.fthrf = (float)a.fthr;
+  if ((double)a.fthrf > a.fthr) a.fthrf = std::nextafter(a.fthrf, -1.0f);
+  a.fdV = 1.0;
+  for (int k = 0; k < g->dim; ++k) a.fdV *= a.dx[k];
+  for (int l = 0; l < MM_MAXMAT; ++l) {
+    a.fdcrit[l] = l < g->nmat ? a.mat[l].D_crit * (1.0 - 1e-6) : 0.0;
+    a.fdcritf[l] = (float)a.fdcrit[l];
+  }
+  a.fpad = 0.0f;
+  prof_begin(g, MM_K_FRAG_MARK);
   CUDA_TRY(go(g, 8, 0, 0, a));
+  prof_end(g);
+  prof_begin(g, MM_K_FRAG_UNION);
   CUDA_TRY(mm_frag_label(a, g->stream));
+  prof_end(g);
+  prof_begin(g, MM_K_FRAG_COUNT);
   CUDA_TRY(mm_frag_count(a, g->fboff, g->stream));
+  prof_end(g);
   g->launches += 4;
   int nf = 0;
   CUDA_TRY(cudaMemcpyAsync(&nf, g->fboff + nblk, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
@@ -768,7 +784,9 @@ mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_
   if (nf > 0) {
     CUDA_TRY(cudaMemsetAsync(g->fcnt, 0, sizeof(unsigned long long) * nf, g->stream));
     CUDA_TRY(cudaMemsetAsync(g->fmas, 0, sizeof(double) * nf, g->stream));
+    prof_begin(g, MM_K_FRAG_COLLECT);
     CUDA_TRY(mm_frag_collect(a, g->fboff, g->ffid, g->flab, g->fcnt, g->fmas, g->stream));
+    prof_end(g);
     g->launches += 2;
   }
   const size_t k = max_frags < (size_t)nf ? max_frags : (size_t)nf;
@@ -797,6 +815,7 @@ mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_
   if (labels)
     for (long long c = 0; c < g->ncell; ++c) labels[c] = hp[(size_t)c];
   *n_frags = nf;
+  prof_collect(g);
   return MM_OK;
 }
 

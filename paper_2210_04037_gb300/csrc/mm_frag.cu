@@ -83,30 +83,51 @@ struct Geo {
   int dim;
 };
 
+// Joins face neighbours.  Inside a warp's 32 cells the x-runs are linked
+// already (k_frag_mark), so an x-union is needed only from a warp's last
+// lane to the next cell, and across a periodic x face.  Along y and z, two
+// cells i, j = i + stride are joined unless i - 1 and j - 1 are fragment
+// cells as well: those two are joined (or skipped for the same reason, down
+// to the first cell of the overlap), and i - 1 ~ i, j - 1 ~ j along x, so
+// one union per overlap of runs in neighbouring rows covers it.
 __global__ void __launch_bounds__(kThreads) k_frag_merge(int* parent, Geo g, long long ncell,
                                                          DevErr* err) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int sxy = nx * ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     // membership never changes during the labelling, so a plain load decides it
     if (parent[c] < 0) continue;
     const int i = (int)c;
-    int co[3] = {0, 0, 0};
-    long long rest = c;
-    for (int d = 0; d < g.dim; ++d) {
-      co[d] = (int)(rest % g.n[d]);
-      rest /= g.n[d];
+    const int x = i % nx;
+    const int yz = i / nx;
+    bool ok = true;
+    if (x + 1 < nx) {
+      if ((i & 31) == 31 && parent[i + 1] >= 0) ok = unite(parent, i, i + 1);
+    } else if (g.per[0] && nx > 1 && parent[i - (nx - 1)] >= 0) {
+      ok = unite(parent, i, i - (nx - 1));
     }
-    long long stride = 1;
-    for (int d = 0; d < g.dim; ++d) {
-      // the +1 neighbour along d; the last cell of a periodic axis wraps
-      long long j = -1;
-      if (co[d] + 1 < g.n[d])
-        j = c + stride;
-      else if (g.per[d] && g.n[d] > 1)
-        j = c - (long long)(g.n[d] - 1) * stride;
-      if (j >= 0 && parent[j] >= 0 && !unite(parent, i, (int)j)) frag_report(err, MM_ETIMEOUT, c);
-      stride *= g.n[d];
+    if (g.dim > 1) {
+      const int y = yz % ny;
+      int j = -1;
+      if (y + 1 < ny)
+        j = i + nx;
+      else if (g.per[1] && ny > 1)
+        j = i - (ny - 1) * nx;
+      if (j >= 0 && parent[j] >= 0 && !(x > 0 && parent[i - 1] >= 0 && parent[j - 1] >= 0))
+        ok = unite(parent, i, j) && ok;
     }
+    if (g.dim > 2) {
+      const int z = yz / ny;
+      int j = -1;
+      if (z + 1 < nz)
+        j = i + sxy;
+      else if (g.per[2] && nz > 1)
+        j = i - (nz - 1) * sxy;
+      if (j >= 0 && parent[j] >= 0 && !(x > 0 && parent[i - 1] >= 0 && parent[j - 1] >= 0))
+        ok = unite(parent, i, j) && ok;
+    }
+    if (!ok) frag_report(err, MM_ETIMEOUT, c);
   }
 }
 
@@ -197,17 +218,54 @@ __global__ void __launch_bounds__(kThreads) k_frag_ids(const int* parent, long l
   }
 }
 
+// Per-fragment sums.  Neighbouring cells nearly always share a fragment:
+// warps without fragment cells skip, the other lanes of a warp join its
+// first fragment cell's fragment with nothing to add, and a warp whose
+// cells then all name one fragment adds its count and mass with one atomic
+// each; only warps that span two fragments combine lane by lane.  Whole
+// warps run the loop (bound rounded up to the warp) so that every shuffle
+// has all 32 lanes.
 __global__ void __launch_bounds__(kThreads) k_frag_accum(const int* parent, const double* cm,
                                                          long long ncell, const int* fid,
                                                          unsigned long long* fcells,
                                                          double* fmass) {
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int r = parent[c];
-    if (r < 0) continue;
-    const int f = fid[r];
-    atomicAdd(fcells + f, 1ull);
-    atomicAdd(fmass + f, cm[c]);
+  const unsigned full = 0xffffffffu;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long end = (ncell + 31) / 32 * 32;
+  const int lane = threadIdx.x & 31;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < end; c += stride) {
+    const int r = c < ncell ? parent[c] : -1;
+    const unsigned mem = __ballot_sync(full, r >= 0);
+    if (mem == 0) continue;
+    const int lead = __ffs(mem) - 1;
+    const int f = r >= 0 ? fid[r] : -1;
+    const int f0 = __shfl_sync(full, f, lead);
+    const int fe = r >= 0 ? f : f0;
+    double m = r >= 0 ? cm[c] : 0.0;
+    if (__ballot_sync(full, fe == f0) == full) {
+      for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(full, m, o);
+      if (lane == lead) {
+        atomicAdd(fcells + f0, (unsigned long long)__popc(mem));
+        atomicAdd(fmass + f0, m);
+      }
+    } else {
+      double sm = 0.0;
+      unsigned k = 0;
+      int first = 32;
+      for (int src = 0; src < 32; ++src) {
+        const int fs = __shfl_sync(full, fe, src);
+        const double ms = __shfl_sync(full, m, src);
+        if (fs == fe) {
+          sm += ms;
+          k += (mem >> src) & 1u;
+          if (first == 32) first = src;
+        }
+      }
+      if (first == lane) {
+        atomicAdd(fcells + fe, (unsigned long long)k);
+        atomicAdd(fmass + fe, sm);
+      }
+    }
   }
 }
 

@@ -80,6 +80,14 @@ struct KArgs {
   int* frag;           // fragment labelling: per-cell parent index, -1 outside fragments
   double* fmass;       // fragment labelling: per-cell solid mass dV sum (phi rho)_solid
   double fcut;         // fragment labelling: void cut-off theta
+  // fragment labelling constants of the launch (set on the host): 1 - theta,
+  // the largest float not above it, D_crit (1 - 1e-6) per material in FP64
+  // and FP32, the cell volume
+  double fthr, fdV;
+  double fdcrit[MM_MAXMAT];
+  float fthrf;
+  float fdcritf[MM_MAXMAT];
+  float fpad;
 };
 
 static_assert(sizeof(KArgs) % 8 == 0, "KArgs is copied as 8-byte words");

@@ -1556,7 +1556,12 @@ __global__ void __launch_bounds__(256) k_totals(KArgs a) {
 // model a cell is in a fragment when its solid fraction exceeds 1 - theta
 // and no solid in it is critically damaged, D >= D_crit within 1e-6 because
 // D comes back as (phi rho D) / (phi rho)): a.frag[cell] = cell there and
-// -1 elsewhere; a.fmass[cell] = dV sum (phi rho) over the solids.
+// -1 elsewhere; a.fmass[cell] = dV sum (phi rho) over the solids on those
+// cells (left as it is elsewhere).  Each
+// warp also links the runs of fragment cells along x within its 32 cells:
+// a member points at the first member of its run (a run stops at a
+// non-member, at the first cell of a row and at the warp's first lane), so
+// the union pass needs no x-links inside a warp.  Requires ncell < 2^31.
 template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_frag_mark(KArgs a) {
   typedef typename P::R R;
@@ -1566,34 +1571,60 @@ __global__ void __launch_bounds__(256) k_frag_mark(KArgs a) {
   typedef Lay<DIM, NMAT, NH> L;
   constexpr int NX = PH::NX;
   const S* U = (const S*)a.Uin;
-  double dV = 1.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) dV *= a.dx[k];
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < a.ncell;
+  // The cut: the FP64 path compares in FP64 with 1 - theta (a.fthr).  The
+  // FP32-split path compares its FP32 fractions with the largest float not
+  // above 1 - theta (a.fthrf), which for one solid (its fraction one stored
+  // float) decides exactly as the FP64 comparison; the scarce FP64 pipe is
+  // left to the members' masses.  The constants come with the launch.
+  // whole warps run the loop (bound rounded up to the warp) for the ballots
+  const long long end = (a.ncell + 31) / 32 * 32;
+  const int lane = threadIdx.x & 31;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < end;
        cell += (long long)gridDim.x * blockDim.x) {
-    XT cx[NX], phid[NMAT];
-    cx[0] = XT(0);
+    bool in = false;
+    R arho[NMAT];
+    if (cell < a.ncell) {
+      XT cx[NX], phid[NMAT];
+      cx[0] = XT(0);
 #pragma unroll
-    for (int l = 0; l < PH::NPX; ++l) cx[1 + l] = XT(U[phislot<P, DIM, NMAT, NH>(a, l, cell)]);
-    PH::fractions(cx, phid);
-    double phis = 0.0, ms = 0.0;
-    bool crit = false;
+      for (int l = 0; l < PH::NPX; ++l) cx[1 + l] = XT(U[phislot<P, DIM, NMAT, NH>(a, l, cell)]);
+      PH::fractions(cx, phid);
+      XT phis = XT(0);
+      bool crit = false;
 #pragma unroll
-    for (int l = 0; l < NMAT; ++l) {
-      if (a.mat[l].eos != 1) continue;
-      phis += double(phid[l]);
-      const R arho = R(U[(long long)(L::oARHO + l) * a.ncell + cell]);
-      ms += double(arho) * dV;
+      for (int l = 0; l < NMAT; ++l) {
+        arho[l] = R(0);
+        if (a.mat[l].eos != 1) continue;
+        phis += phid[l];
+        arho[l] = R(U[(long long)(L::oARHO + l) * a.ncell + cell]);
 #pragma unroll
-      for (int h = 0; h < NH; ++h)
-        if (h == a.hslot[l] && a.mat[l].damage != 0) {
-          const R D = R(U[(long long)(L::oH + 2 * h + 1) * a.ncell + cell]) / arho;
-          crit = crit || D >= R(a.mat[l].D_crit * (1.0 - 1e-6));
-        }
+        for (int h = 0; h < NH; ++h)
+          if (h == a.hslot[l] && a.mat[l].damage != 0) {
+            const R D = R(U[(long long)(L::oH + 2 * h + 1) * a.ncell + cell]) / arho[l];
+            crit = crit || D >= (P::split ? R(a.fdcritf[l]) : R(a.fdcrit[l]));
+          }
+      }
+      if constexpr (P::split)
+        in = float(phis) > a.fthrf && !crit;
+      else
+        in = double(phis) > a.fthr && !crit;
     }
-    const bool in = phis > 1.0 - a.fcut && !crit;
-    a.frag[cell] = in ? (int)cell : -1;
-    a.fmass[cell] = in ? ms : 0.0;
+    const unsigned mem = __ballot_sync(0xffffffffu, in);
+    const unsigned rows = __ballot_sync(0xffffffffu, cell < a.ncell && (int)cell % a.n[0] == 0);
+    // run starts: members whose left lane is not a member, or that begin a row
+    const unsigned starts = mem & (~(mem << 1) | rows);
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int s = 31 - __clz(starts & upto);
+    if (cell < a.ncell) {
+      a.frag[cell] = in ? (int)(cell - lane + s) : -1;
+      if (in) {  // read for fragment cells only
+        double ms = 0.0;
+#pragma unroll
+        for (int l = 0; l < NMAT; ++l)
+          if (a.mat[l].eos == 1) ms += double(arho[l]) * a.fdV;
+        a.fmass[cell] = ms;
+      }
+    }
   }
 }
 

@@ -89,7 +89,8 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport", "mm_step"
            "mm_batch_step", "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
            "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
            "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy")
-KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources", "xtransport")
+KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources", "xtransport",
+                "frag_mark", "frag_union", "frag_count", "frag_collect")
 X_SWEEP, X_WENO3_RK3 = 0, 1
 
 _lock = threading.Lock()
