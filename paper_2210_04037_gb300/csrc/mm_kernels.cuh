@@ -884,36 +884,56 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
     J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
   }
   double dl = 0.0;
+  R km1 = R(0);  // k - 1 of the return factor k = 1 - 3 G dl / sigma_eq
   if (can_yield && Gm > 0.0) {
-    const double J = series ? sqrt(double(J2))
-                            : sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
-                                   double(h[2]) * double(h[2]));
-    const double str = sqrt(6.0) * Gm * J;
+    // Split path: the equivalent stress, the bracket, the start and the
+    // yield-function inputs come from FP32 quantities and are formed in FP32
+    // (this part's FP64 pipe is narrow); the Newton iterate and residual
+    // stay FP64.
     float phf[NMAT], epf[NMAT], Dmf[NMAT];
+    float inv_dt = 0.f, strf = 0.f;
+    double str;
+    if constexpr (P::split) {
 #pragma unroll
-    for (int l = 0; l < NMAT; ++l) {
-      phf[l] = float(phi[l]);
-      epf[l] = float(eps[l]);
-      Dmf[l] = float(Dm[l]);
+      for (int l = 0; l < NMAT; ++l) {
+        phf[l] = phir[l];
+        epf[l] = Er[l];
+        Dmf[l] = Dr[l];
+      }
+      const float Jf = series ? sqrtf(J2) : sqrtf(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+      strf = 2.4494897f * Gm_r * Jf;  // sqrt(6) G |dev H|
+      str = double(strf);
+      inv_dt = 1.0f / float(dt);
+    } else {
+      const double J = series ? sqrt(double(J2))
+                              : sqrt(double(h[0]) * double(h[0]) + double(h[1]) * double(h[1]) +
+                                     double(h[2]) * double(h[2]));
+      str = sqrt(6.0) * Gm * J;
     }
-    const float inv_dt = float(1.0 / dt);
     float dYf0;
     const double Y0 =
-        P::split ? double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat), inv_dt, 0.f, &dYf0))
+        P::split ? double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat_r), inv_dt, 0.f, &dYf0))
                  : yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, 0.0, nullptr);
     if (str > Y0) {
       // stopping rule at the accuracy of the yield-stress evaluation
       const double gtol = P::split ? 1e-6 : 8.0 * 2.220446049250313e-16;
       const double xtol = P::split ? 1e-7 : 4.0 * 2.220446049250313e-16;
-      const double b0 = str / (3.0 * Gm);
-      double lo = 0.0, hi = b0, x = (str - Y0) / (3.0 * Gm);
+      double b0, x;
+      if constexpr (P::split) {
+        const float g3 = 3.0f * Gm_r;
+        b0 = double(strf / g3);
+        x = double((strf - float(Y0)) / g3);
+      } else {
+        b0 = str / (3.0 * Gm);
+        x = (str - Y0) / (3.0 * Gm);
+      }
+      double lo = 0.0, hi = b0;
       bool conv = false;
       for (int it = 0; it < 200; ++it) {
-        double dY, Y;
+        double dY = 0.0, Y;
+        float dYf = 0.f;
         if (P::split) {
-          float dYf;
-          Y = double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat), inv_dt, float(x), &dYf));
-          dY = double(dYf);
+          Y = double(yield_mix_f32<NMAT>(a, phf, epf, Dmf, float(phihat_r), inv_dt, float(x), &dYf));
         } else {
           Y = yield_mix<NMAT, R>(a, phi, eps, Dm, phihat, dt, x, &dY);
         }
@@ -923,7 +943,7 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
           break;
         }
         if (g > 0.0) lo = x; else hi = x;
-        double nx = P::split ? x - double(float(g) / float(-3.0 * Gm - dY))
+        double nx = P::split ? x - double(float(g) / (-3.0f * Gm_r - dYf))
                              : x - g / (-3.0 * Gm - dY);
         if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
         if (fabs(nx - x) <= xtol * b0) {
@@ -938,19 +958,24 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
         return;
       }
       dl = x;
-      const R k = R((str - 3.0 * Gm * dl) / str);
+      // split path: k - 1 itself in FP32 (k rounded to FP32 would leave
+      // k - 1 with a relative error of 6e-8 / |k - 1|)
+      if constexpr (P::split)
+        km1 = -(3.0f * Gm_r * float(dl)) / strf;
+      else
+        km1 = R((str - 3.0 * Gm * dl) / str) - R(1);
       // Fbar <- S Fbar, S = exp((k-1) dev(H)) (the rotation is kept); in A
       // form A <- (S - I)(I + A) + A
       R Sm[9], Xn[9];
       if (series) {
         R Y[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) Y[q] = (k - R(1)) * devH[q];
+        for (int q = 0; q < 9; ++q) Y[q] = km1 * devH[q];
         expm1_series(Y, Sm);
       } else {
         R m1[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1((k - R(1)) * h[q]) : mexp((k - R(1)) * h[q]);
+        for (int q = 0; q < 3; ++q) m1[q] = P::aform ? mexpm1(km1 * h[q]) : mexp(km1 * h[q]);
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -982,17 +1007,28 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
       report(a.err, ST_ENONFINITE, cell, step);
       return;
     }
-    const double seq = sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2));
+    R seq;
+    if constexpr (P::split)
+      seq = 2.4494897f * mx.Gm * sqrtf(mx.J2);
+    else
+      seq = R(sqrt(6.0) * double(mx.Gm) * sqrt(double(mx.J2)));
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
 #pragma unroll
       for (int hh = 0; hh < NH; ++hh)
         if (a.hslot[l] == hh) {
           const R arho = c[L::oARHO + l];
-          const double Dn = double(damage_rk4<R>(matp<R>(a, l), R(Dm[l]), R(eps[l]), R(dl), R(dt),
-                                                 R(wx2[0]), R(seq), rho[l]));
-          c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
-          c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
+          if constexpr (P::split) {
+            const R Dn = damage_rk4<R>(matp<R>(a, l), Dr[l], Er[l], R(dl), R(dt), R(wx2[0]), seq,
+                                       rho[l]);
+            c[L::oH + 2 * hh] = arho * (Er[l] + R(dl));
+            c[L::oH + 2 * hh + 1] = arho * Dn;
+          } else {
+            const double Dn = double(damage_rk4<R>(matp<R>(a, l), R(Dm[l]), R(eps[l]), R(dl),
+                                                   R(dt), R(wx2[0]), seq, rho[l]));
+            c[L::oH + 2 * hh] = R(double(arho) * (eps[l] + dl));
+            c[L::oH + 2 * hh + 1] = R(double(arho) * Dn);
+          }
         }
     }
   }
