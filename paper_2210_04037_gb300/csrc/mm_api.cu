@@ -33,32 +33,6 @@ mm_status fail(mm_status s, const char* fmt, ...) {
       return fail(MM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
-__device__ __forceinline__ void dt_update(DevInfo* info, DevErr* err, double cfl, double dxmin,
-                                          const double* dx, int dim) {
-  const double smax = __longlong_as_double((long long)info->smax_bits);
-  info->smax_bits = 0ull;
-  info->steps += 1;
-  const double dt = cfl * dxmin / smax;
-  if (!(dt > 0.0) || !isfinite(dt)) {
-    if (atomicCAS(&err->code, 0, MM_EDT) == 0) {
-      err->cell = -1;
-      err->step = info->steps;
-    }
-  }
-  info->dt = dt;
-  info->smax = smax;
-  info->t += dt;
-  // the sweeps' dt / dx, formed once per step instead of once per thread
-  for (int k = 0; k < 3; ++k) info->lam[k] = k < dim ? dt / dx[k] : 0.0;
-}
-
-// dt = cfl dx_min / s_max from the CFL reduction; advances t and the step count.
-__global__ void k_dt(DevInfo* info, DevErr* err, double cfl, double dxmin, double dx0, double dx1,
-                     double dx2, int dim) {
-  const double dx[3] = {dx0, dx1, dx2};
-  dt_update(info, err, cfl, dxmin, dx, dim);
-}
-
 // The same for every member of a batch (one thread per member).
 __global__ void k_dt_batch(const KArgs* args, int M, double cfl) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -486,14 +460,10 @@ mm_status enqueue_one(mm_grid* g, double cfl) {
   {
     KArgs a = args_for(g);
     a.cfl = cfl;
+    // the CFL reduction's last CTA also forms dt (no separate launch)
     prof_begin(g, MM_K_CFL);
     CUDA_TRY(go(g, 2, 0, 0, a));
     prof_end(g);
-    prof_begin(g, MM_K_DT);
-    k_dt<<<1, 1, 0, g->stream>>>(g->info, g->err, cfl, a.dxmin, a.dx[0], a.dx[1], a.dx[2], a.dim);
-    prof_end(g);
-    g->launches += 1;
-    CUDA_TRY(cudaGetLastError());
     if (g->xscheme == MM_X_WENO3_RK3) {
       // X of the step's end from its start (the state the sweeps read)
       prof_begin(g, MM_K_XTRANSPORT);

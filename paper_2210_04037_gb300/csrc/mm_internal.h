@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mmfrac.h"
+
 #define MM_MAXMAT 2
 
 // Material constants as the kernels use them (copied from mm_material, plus
@@ -47,11 +49,35 @@ struct DevErr {
 
 // Device-resident step bookkeeping; dt never leaves the device inside a step.
 struct DevInfo {
-  double t, dt, smax, pad;
+  double t, dt, smax;
+  unsigned int cfl_done;         // CTAs of the CFL reduction finished this step (reset by the last)
+  unsigned int pad;
   long long steps;
   unsigned long long smax_bits;  // running max of the signal speed (bits of a >= 0 double)
   double lam[3];                 // dt / dx_k of the step (0 for an axis the grid lacks)
 };
+
+// dt = cfl dx_min / s_max from the finished CFL reduction; advances t and
+// the step count, forms the sweeps' dt / dx_k, clears the running maximum.
+// The maximum is read past L1 (other CTAs raised it by atomics).
+__device__ __forceinline__ void dt_update(DevInfo* info, DevErr* err, double cfl, double dxmin,
+                                          const double* dx, int dim) {
+  const unsigned long long bits = *(volatile unsigned long long*)&info->smax_bits;
+  const double smax = __longlong_as_double((long long)bits);
+  info->smax_bits = 0ull;
+  info->steps += 1;
+  const double dt = cfl * dxmin / smax;
+  if (!(dt > 0.0) || !isfinite(dt)) {
+    if (atomicCAS(&err->code, 0, MM_EDT) == 0) {
+      err->cell = -1;
+      err->step = info->steps;
+    }
+  }
+  info->dt = dt;
+  info->smax = smax;
+  info->t += dt;
+  for (int k = 0; k < 3; ++k) info->lam[k] = k < dim ? dt / dx[k] : 0.0;
+}
 
 // Everything a kernel needs, passed by value.
 struct KArgs {

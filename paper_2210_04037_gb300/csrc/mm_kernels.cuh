@@ -1315,12 +1315,25 @@ __device__ __forceinline__ void cta_max_to(unsigned long long* dst, double smax)
   }
 }
 
+// The CFL reduction of one grid; the last CTA to finish (counted with an
+// atomic after a fence, no waiting) forms dt for the step.
 template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_cfl(KArgs a) {
   const double smax = cfl_max<P, DIM, NMAT, NH>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                                                 a.ncell, (long long)gridDim.x * blockDim.x,
                                                 a.info->steps);
   cta_max_to(&a.info->smax_bits, smax);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's atomicMax before its count
+    last = atomicAdd(&a.info->cfl_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();  // every other CTA's atomicMax before the read
+    a.info->cfl_done = 0u;
+    dt_update(a.info, a.err, a.cfl, a.dxmin, a.dx, a.dim);
+  }
 }
 
 // Every member of a batch, in chunks of bk.chunk cells.

@@ -10,6 +10,15 @@ namespace mm {
 
 __global__ void k_totals_final(const double* partial, int nblocks, int nq, double dV, double* out);
 
+// Batches of 128 cells each source CTA takes at least: the queue of
+// yielding cells fills across them, so fewer returns run on part-filled
+// warps.  Measured on the 512^2 ring (source kernel): 1 batch 42 us, 2: 42,
+// 4: 36, 8: 50, 16: 75.  Grids of more than 2432 x 4 x 128 cells are capped
+// at 2432 CTAs anyway.
+#ifndef MM_SRC_BATCHES
+#define MM_SRC_BATCHES 4
+#endif
+
 inline int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 16) b = 152LL * 16;
@@ -104,7 +113,7 @@ struct Launch {
         break;
       }
       case 4: {
-        k_sources<P, DIM, NMAT, NH><<<grid_for(a.ncell, 128), 128, 0, s>>>(a);
+        k_sources<P, DIM, NMAT, NH><<<grid_for(a.ncell, 128 * MM_SRC_BATCHES), 128, 0, s>>>(a);
         break;
       }
       case 5: {
