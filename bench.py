@@ -104,9 +104,9 @@ def ensemble_cases(m: int):
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
 # once those differ (profiles/traffic_ring2d_512_fp32split.md).
-TRAFFIC_SRC_SHA256 = "0781f004b0081c8ca9cffd61bb1b07734f90633b6aa7ee289589430e42c1a94b"
-TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892864, "sweep_y": 17898496,
-                                           "sources": 17974784}}
+TRAFFIC_SRC_SHA256 = "ddd3219ec9045e5aa305bc3de7ccf3daadac5ca7677811d61ea1352d57322afc"
+TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17893120, "sweep_y": 17892352,
+                                           "sources": 17975808}}
 
 
 def kernel_src_hash() -> str:

@@ -1233,8 +1233,13 @@ __device__ __forceinline__ void sources_flush(
 
 // One grid: the CTA strides over the cells in batches of 128 (uniform trip
 // count: the barriers are reached by all).
-template <class P, int DIM, int NMAT, int NH>
-__global__ void __launch_bounds__(128) k_sources(KArgs a) {
+// MINB: CTAs per SM the registers must allow (launch bound).  The launcher
+// takes 5 for FP32-split grids large enough to fill 2432 CTAs (96 instead
+// of 104 registers, 5 CTAs per SM instead of 4: 2048^2 ring 235 -> 213 us,
+// 256^3 cylinder 1.53 -> 1.48 ms) and 1 below (512^2 ring 36.6 us against
+// 37.6 with the bound).
+template <class P, int DIM, int NMAT, int NH, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_sources(KArgs a) {
   static_assert(SrcQueue<P, DIM, NMAT, NH>::NT == 128, "queue batch = CTA size");
   __shared__ typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type qs;
   const double dt = a.info->dt;
@@ -1251,8 +1256,10 @@ __global__ void __launch_bounds__(128) k_sources(KArgs a) {
 
 // Every member of a batch: units are chunks of bk.chunk cells (a multiple of
 // 128) of one member; the queue is drained at the end of each chunk.
+// FP32-split: 5 CTAs per SM (96 registers): the 64-ring ensemble's batched
+// sources 1.056 -> 0.951 ms per step.
 template <class P, int DIM, int NMAT, int NH>
-__global__ void __launch_bounds__(128) k_sources_batch(BatchK bk) {
+__global__ void __launch_bounds__(128, P::split ? 5 : 1) k_sources_batch(BatchK bk) {
   __shared__ typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type qs;
   __shared__ KArgs ka;
   __shared__ long long s_unit;
@@ -1317,8 +1324,13 @@ __device__ __forceinline__ void cta_max_to(unsigned long long* dst, double smax)
 
 // The CFL reduction of one grid; the last CTA to finish (counted with an
 // atomic after a fence, no waiting) forms dt for the step.
+// FP32-split: four 256-thread CTAs per SM (64 registers, 16 bytes spilled);
+// the FP64 recovery would spill 260 bytes under that cap, so it has none.
+// Launched as one wave of resident CTAs that stride over the cells.
+// Measured on the 512^2 ring: 29.8 us with 3 CTAs per SM over 2.25 waves,
+// 24.0 with the cap, 22.9 in one wave, 19.7 with both.
 template <class P, int DIM, int NMAT, int NH>
-__global__ void __launch_bounds__(256) k_cfl(KArgs a) {
+__global__ void __launch_bounds__(256, P::split ? 4 : 1) k_cfl(KArgs a) {
   const double smax = cfl_max<P, DIM, NMAT, NH>(a, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                                                 a.ncell, (long long)gridDim.x * blockDim.x,
                                                 a.info->steps);

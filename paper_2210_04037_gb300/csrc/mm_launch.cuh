@@ -95,7 +95,16 @@ struct Launch {
         break;
       }
       case 2: {
-        k_cfl<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a);
+        // one wave of resident CTAs (the grid strides over the cells)
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cfl<P, DIM, NMAT, NH>, 256, 0);
+        if (e != cudaSuccess) return e;
+        const int wave = sms * (per > 0 ? per : 1);
+        const int need = grid_for(a.ncell, 256);
+        k_cfl<P, DIM, NMAT, NH><<<need < wave ? need : wave, 256, 0, s>>>(a);
         break;
       }
       case 3:
@@ -113,7 +122,15 @@ struct Launch {
         break;
       }
       case 4: {
-        k_sources<P, DIM, NMAT, NH><<<grid_for(a.ncell, 128 * MM_SRC_BATCHES), 128, 0, s>>>(a);
+        const int g = grid_for(a.ncell, 128 * MM_SRC_BATCHES);
+        bool bounded = false;
+        if constexpr (P::split) {
+          if (a.ncell >= 152LL * 16 * 128 * MM_SRC_BATCHES) {
+            k_sources<P, DIM, NMAT, NH, 5><<<g, 128, 0, s>>>(a);
+            bounded = true;
+          }
+        }
+        if (!bounded) k_sources<P, DIM, NMAT, NH, 1><<<g, 128, 0, s>>>(a);
         break;
       }
       case 5: {
