@@ -348,7 +348,8 @@ int64_t mm_kernel_launches(const mm_grid* g);
 /* Kernel timing (tracing aid, no counterpart in the paper).  With enable = 1
  * every later mm_step brackets each of its launches with CUDA events on the
  * grid's stream and accumulates the elapsed device time per kernel kind:
- * MM_K_CFL, MM_K_DT, MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES,
+ * MM_K_CFL (on a single grid it also forms dt), MM_K_DT (batches only: the
+ * per-member dt launch), MM_K_SWEEP_X, MM_K_SWEEP_Y, MM_K_SWEEP_Z, MM_K_SOURCES,
  * MM_K_XTRANSPORT (the X update of MM_X_WENO3_RK3, its four launches and the
  * copy together); mm_fragments likewise: MM_K_FRAG_MARK (membership and
  * masses), MM_K_FRAG_UNION (the union and root passes), MM_K_FRAG_COUNT (the
