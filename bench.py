@@ -104,9 +104,9 @@ def ensemble_cases(m: int):
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
 # once those differ (profiles/traffic_ring2d_512_fp32split.md).
-TRAFFIC_SRC_SHA256 = "ae873f0faebfeaa1b0bb54bed5cc2bf00261a79e32c927c0dbd3d6e21cc7b9a4"
-TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892864, "sweep_y": 17892864,
-                                           "sources": 17984256}}
+TRAFFIC_SRC_SHA256 = "d1301c09f9d06f8dac2299cc2b3bdef3454478a9a583a53d1843eca2fd7f092b"
+TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892608, "sweep_y": 17892608,
+                                           "sources": 17976064}}
 
 
 def kernel_src_hash() -> str:

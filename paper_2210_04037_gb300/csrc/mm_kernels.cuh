@@ -185,7 +185,7 @@ template <> struct Tile<P64, 3, 2> { static constexpr int TL = 12, TW = 4, NT = 
 // FP32-split: 128-thread CTAs, transverse width 8 (32-byte sectors of x).
 template <> struct Tile<P32, 1, 0> { static constexpr int TL = 124, TW = 1, NT = 128; };
 template <> struct Tile<P32, 2, 0> { static constexpr int TL = 60, TW = 2, NT = 128; };
-template <> struct Tile<P32, 2, 1> { static constexpr int TL = 12, TW = 8, NT = 128; };
+template <> struct Tile<P32, 2, 1> { static constexpr int TL = 28, TW = 8, NT = 256; };
 template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
 template <> struct Tile<P32, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
 template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
