@@ -104,15 +104,20 @@ def ensemble_cases(m: int):
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
 # once those differ (profiles/traffic_ring2d_512_fp32split.md).
-TRAFFIC_SRC_SHA256 = "d1301c09f9d06f8dac2299cc2b3bdef3454478a9a583a53d1843eca2fd7f092b"
+TRAFFIC_SRC_SHA256 = "02d9816d76c400538692bb22cc8863360673f61cd53ec29a15d858d25af821dd"
 TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892608, "sweep_y": 17892608,
                                            "sources": 17976064}}
 
 
 def kernel_src_hash() -> str:
+    """SHA-256 of what the single-grid step kernels are built from: the
+    kernel headers, the per-precision single-grid units and build.py (not
+    the host API, the batch units or fragment labelling)."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2210_04037_gb300", "csrc")
-    for f in sorted(os.listdir(cs)) + ["../build.py"]:
+    step = [f for f in sorted(os.listdir(cs))
+            if f.endswith((".cuh", ".h")) or (f.startswith("mm_fp") and "_batch" not in f)]
+    for f in step + ["../build.py"]:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())

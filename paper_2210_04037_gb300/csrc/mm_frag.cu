@@ -35,12 +35,19 @@ __device__ __forceinline__ void frag_report(DevErr* e, int code, long long cell)
   }
 }
 
-// Root of i.  Loads bypass L1 (ld.global.cg): links made by other blocks
-// during the same launch must be seen.  Path halving: each visited cell is
-// pointed at its grandparent, an ancestor, which keeps the invariant.
+// Steps of one walk to a root.  The walk ends by the invariant (indices
+// strictly decrease); the cap makes that independent of it: a walk that
+// reaches it returns -1 and the caller reports MM_ETIMEOUT.
+constexpr int kWalkSteps = 1 << 26;
+
+// Root of i (-1 past the cap).  Loads bypass L1 (ld.global.cg): links made
+// by other blocks during the same launch must be seen.  Path halving: each
+// visited cell is pointed at its grandparent, an ancestor, which keeps the
+// invariant.
 __device__ __forceinline__ int find_root(int* parent, int i) {
   int p = __ldcg(parent + i);
-  while (p != i) {
+  for (int k = 0; p != i; ++k) {
+    if (k == kWalkSteps) return -1;
     const int gp = __ldcg(parent + p);
     if (gp != p) parent[i] = gp;
     i = p;
@@ -49,12 +56,14 @@ __device__ __forceinline__ int find_root(int* parent, int i) {
   return i;
 }
 
-// Root of i without writes.  The pass that stores every cell's root uses
-// it: a halving store from another thread, of an ancestor read before the
-// owner stored the root, could otherwise land last and leave a non-root.
+// Root of i without writes (-1 past the cap).  The pass that stores every
+// cell's root uses it: a halving store from another thread, of an ancestor
+// read before the owner stored the root, could otherwise land last and
+// leave a non-root.
 __device__ __forceinline__ int find_root_ro(const int* parent, int i) {
   int p = __ldcg(parent + i);
-  while (p != i) {
+  for (int k = 0; p != i; ++k) {
+    if (k == kWalkSteps) return -1;
     i = p;
     p = __ldcg(parent + i);
   }
@@ -65,6 +74,7 @@ __device__ __forceinline__ bool unite(int* parent, int a, int b) {
   for (int it = 0; it < kUniteRetries; ++it) {
     a = find_root(parent, a);
     b = find_root(parent, b);
+    if (a < 0 || b < 0) return false;
     if (a == b) return true;
     if (a > b) {
       const int t = a;
@@ -131,10 +141,17 @@ __global__ void __launch_bounds__(kThreads) k_frag_merge(int* parent, Geo g, lon
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_frag_compress(int* parent, long long ncell) {
+__global__ void __launch_bounds__(kThreads) k_frag_compress(int* parent, long long ncell,
+                                                            DevErr* err) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x)
-    if (parent[c] >= 0) parent[c] = find_root_ro(parent, (int)c);
+    if (parent[c] >= 0) {
+      const int r = find_root_ro(parent, (int)c);
+      if (r < 0)
+        frag_report(err, MM_ETIMEOUT, c);
+      else
+        parent[c] = r;
+    }
 }
 
 // Roots in each block of MM_FRAG_CELLS cells (thread t takes cells
@@ -282,7 +299,7 @@ cudaError_t mm_frag_label(const KArgs& a, cudaStream_t s) {
   k_frag_merge<<<nb, kThreads, 0, s>>>(a.frag, g, a.ncell, a.err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_frag_compress<<<nb, kThreads, 0, s>>>(a.frag, a.ncell);
+  k_frag_compress<<<nb, kThreads, 0, s>>>(a.frag, a.ncell, a.err);
   return cudaGetLastError();
 }
 
