@@ -9,14 +9,16 @@
  * 2.1.2), the damage laws (Sec. 2.1.1, Sec. 4.3), the perturbation field
  * (Sec. 2.1.3, 3.2) and RK4 for damage (Sec. 3.1), and defers the hyperbolic
  * solver, the mixture rules and the plastic update to earlier papers (start
- * of Sec. 3).  The readings used for those (R1..R26) are written out beside
- * each routine; every step is done plainly, one cell or one face at a time,
- * in the order the method takes them:
+ * of Sec. 3).  The readings used for those are written out beside each
+ * routine; every step is done plainly, one cell or one face at a time, in
+ * the order the method takes them:
  *
  *   one time step = dt from the CFL rule (R-CFL)
  *                   -> sweep x -> sweep y -> sweep z  (dimensional split, R8)
  *                   -> per-cell sources: phi0(X) lookup, plastic return,
  *                      RK4 damage (Godunov split, R12)
+ *   fragments     = membership at a void cut-off -> components under face
+ *                   adjacency in cell order -> masses (Sec. 4.2, 4.3)
  *   one sweep     = primitive recovery -> van Leer slopes on primitives (R9)
  *                   -> MUSCL-Hancock half step (first order where a face
  *                      state is inadmissible or a phase density leaves the
