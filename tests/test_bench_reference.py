@@ -25,6 +25,7 @@ def reference_line(workload, size):
 
 @pytest.mark.parametrize("workload,size,unit", [("ring_2d", 32, "cell-updates/s"),
                                                 ("spall_1d", 200, "cell-updates/s"),
+                                                ("ensemble_2d", 2, "cell-updates/s"),
                                                 ("fragments", 24, "cells/s")])
 def test_reference_arm_json_contract(workload, size, unit):
     d = reference_line(workload, size)
