@@ -243,7 +243,14 @@ mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** 
     }
     g->own_stream = true;
   }
-  g->tot_blocks = 1024;
+  // totals: at least 8 cells per thread, at most 1024 blocks of 256.  Each
+  // warp's FP64 reduction of the N + 4 sums costs about as much as a thread
+  // accumulating 8 cells on this part's narrow FP64 pipe, so one cell per
+  // thread (1024 blocks on a 512^2 grid) spent most of the time reducing.
+  {
+    long long nb = ncell / (256LL * 8);
+    g->tot_blocks = (int)(nb < 1 ? 1 : (nb > 1024 ? 1024 : nb));
+  }
   if (cudaMalloc(&g->info, sizeof(DevInfo)) != cudaSuccess ||
       cudaMalloc(&g->err, sizeof(DevErr)) != cudaSuccess ||
       cudaMalloc(&g->partial, sizeof(double) * g->tot_blocks * (MM_MAXMAT + 4)) != cudaSuccess ||
