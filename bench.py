@@ -7,7 +7,7 @@ headline) beside the FP64 path, with the HBM roofline fraction of the
 dominant kernel.
 
     python bench.py [--gpus N --steps K --warmup W]
-                    [--workload ring_2d|cylinder_3d|spall_1d|ensemble_2d|serve|fragments]
+                    [--workload cylinder_3d|ring_2d|spall_1d|ensemble_2d|serve|fragments]
                     [--precision fp32split|fp64] [--impl mmfrac|reference]
 
 ``--workload ensemble_2d`` times a batch of seeded 2D rings of uneven size
@@ -103,7 +103,7 @@ def ensemble_cases(m: int):
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, cold L2) per
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
-# once those differ (profiles/traffic_ring2d_512_fp32split.md).
+# once those differ.
 TRAFFIC_SRC_SHA256 = "02d9816d76c400538692bb22cc8863360673f61cd53ec29a15d858d25af821dd"
 TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892608, "sweep_y": 17892608,
                                            "sources": 17976064}}
@@ -175,6 +175,17 @@ def max_over_ranks(value: float, dist=None, device: str = "cuda") -> float:
 def aggregate_rate(cells_per_rank: int, steps: int, ms_max: float, world: int) -> float:
     """Whole-job cell-updates/s: every rank advances its own replica."""
     return world * cells_per_rank * steps / (ms_max * 1e-3)
+
+
+def algo_bytes_per_pass(case, precision: int) -> int:
+    """Algorithmic bytes per cell of one split pass: one read and one write
+    of the S stored fields of the method's state (S = 21 in 3D, 15 in 2D, 11
+    in 1D for two materials with one plastic one).  FP64: 8 bytes a field;
+    FP32-split: rho E in 8 bytes and the other S - 1 fields in 4.  A full
+    step moves `dim` times this.  The build's own layout (`state_bytes`)
+    carries the last volume fraction too and is reported beside it."""
+    s = case.layout.nfield
+    return 2 * 8 * s if precision == W.FP64 else 2 * (8 + 4 * (s - 1))
 
 
 def state_bytes(case, precision: int) -> int:
@@ -284,21 +295,31 @@ def run_reference(args, rank: int, world: int):
     g = OracleGrid(case, threads=cores)
     if args.workload == "fragments":
         return run_reference_fragments(args, world, case, g, n)
-    g.step(args.warmup)
+    # a bounded sample: the warm-up and the timed steps each stop after about
+    # a minute of host time (the 256^3 cylinder takes seconds per step)
     t0 = time.perf_counter()
-    g.step(args.steps)
+    warm = 0
+    while warm < args.warmup and (warm == 0 or time.perf_counter() - t0 < 30.0):
+        g.step(1)
+        warm += 1
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < args.steps and (steps == 0 or time.perf_counter() - t0 < 60.0):
+        g.step(1)
+        steps += 1
     el = time.perf_counter() - t0
-    value = case.ncell * args.steps / el
+    value = case.ncell * steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "n_gpus": world, "steps": steps, "warmup": warm,
+            "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload].format(n=n), "cells": case.ncell,
                        "precision": "fp64 (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
                              "kind": "oracle",
-                             "sample": f"{args.steps} timed FP64 steps of the full workload "
-                                       f"after {args.warmup} warm-up steps"},
+                             "sample": f"{steps} timed FP64 steps of the full workload "
+                                       f"after {warm} warm-up steps (at most {args.steps} and "
+                                       f"{args.warmup}, each run capped near a minute)"},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -707,8 +728,15 @@ def run_gpu(args, rank: int, world: int):
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms = kinds[dom][0] / kinds[dom][1]
-    algo = 2 * sbytes if dom.startswith("sweep") or dom == "sources" else sbytes
+    per_pass = algo_bytes_per_pass(case, prec)
+    # a sweep and the source step each read and write the state once; the
+    # CFL reduction and the totals read it once
+    algo = per_pass * case.ncell if dom.startswith("sweep") or dom == "sources" \
+        else per_pass * case.ncell // 2
+    layout = 2 * sbytes if dom.startswith("sweep") or dom == "sources" else sbytes
     achieved = algo / (dom_ms * 1e-3) / 1e9
+    step_bytes = per_pass * case.layout.dim * case.ncell
+    step_achieved = step_bytes * args.steps / (ms * 1e-3) / 1e9
     fp32_state = g.read()
     g.close()
     # FP64 beside it (same workload, same steps) and the FP32-split error
@@ -763,7 +791,12 @@ def run_gpu(args, rank: int, world: int):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": measured_traffic(args.workload, n, args.precision, dom),
-                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": dom_ms},
+                     "algorithmic_bytes_per_launch": algo,
+                     "algorithmic_bytes_per_cell": algo / case.ncell,
+                     "layout_bytes_per_launch": layout, "avg_launch_ms": dom_ms},
+        "step_roofline": {"bytes_per_update": per_pass * case.layout.dim,
+                          "achieved": step_achieved, "peak": peak, "unit": "GB/s",
+                          "frac": step_achieved / peak},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
         "ms_per_step_with_kernel_events": ms_k / args.steps,
         "e2e": {"value": world * case.ncell * args.steps / e2e_s, "unit": "cell-updates/s",
@@ -788,10 +821,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mmfrac", choices=["mmfrac", "reference"])
-    ap.add_argument("--workload", default="ring_2d", choices=list(DEFAULT_SIZE))
+    ap.add_argument("--workload", default="cylinder_3d", choices=list(DEFAULT_SIZE))
     ap.add_argument("--precision", default="fp32split", choices=["fp32split", "fp64"])
     ap.add_argument("--size", type=int, default=0)
-    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--x-transport", default="sweep", choices=["sweep", "weno3rk3"],

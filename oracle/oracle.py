@@ -21,17 +21,23 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_oracle(src: str, out: str) -> str:
+    """gcc, FP64, no FMA contraction, OpenMP loops; `src` must sit beside
+    oracle.h (or find it on the include path given by its directory)."""
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-fopenmp", "-I", HERE, src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc: FP64, no FMA contraction, OpenMP loops."""
+    """Compile the oracle in place (liboracle.so beside the source)."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-fopenmp", SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    return compile_oracle(SRC, LIB)
 
 
 class Material(ctypes.Structure):
@@ -56,44 +62,54 @@ def material_struct(m) -> Material:
 
 
 def load():
+    """The oracle library (built on first use)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
         build()
-        lib = ctypes.CDLL(LIB)
-        P = ctypes.POINTER
-        d, i, L = ctypes.c_double, ctypes.c_int, ctypes.c_long
-        lib.or_create.restype = ctypes.c_void_p
-        lib.or_create.argtypes = [i, P(L), P(d), P(d), P(i), i, P(Material), P(d),
-                                  P(ctypes.c_float), P(L), P(d), P(d), P(i)]
-        lib.or_destroy.argtypes = [ctypes.c_void_p]
-        lib.or_nfield.argtypes = [ctypes.c_void_p]
-        lib.or_ncell.argtypes = [ctypes.c_void_p]
-        lib.or_ncell.restype = L
-        lib.or_step.argtypes = [ctypes.c_void_p, i, d, d, P(d)]
-        lib.or_cfl_dt.argtypes = [ctypes.c_void_p, d, P(d), P(d)]
-        lib.or_read.argtypes = [ctypes.c_void_p, i, P(d)]
-        lib.or_write_conserved.argtypes = [ctypes.c_void_p, P(d)]
-        lib.or_totals.argtypes = [ctypes.c_void_p, P(d)]
-        lib.or_set_threads.argtypes = [i]
-        lib.or_set_x_scheme.argtypes = [ctypes.c_void_p, i]
-        lib.or_fragments.restype = L
-        lib.or_fragments.argtypes = [ctypes.c_void_p, d, P(L), P(L), P(L), P(d), L]
-        lib.or_thermo.argtypes = [P(Material), d, d, d, P(d)]
-        lib.or_hencky.argtypes = [P(d), P(d), P(d), P(d)]
-        lib.or_lookup.restype = d
-        lib.or_lookup.argtypes = [i, P(ctypes.c_float), P(L), P(d), P(d), P(d)]
-        lib.or_eps_thresh.restype = d
-        lib.or_eps_thresh.argtypes = [d, d, d, d]
-        lib.or_Rt.restype = d
-        lib.or_Rt.argtypes = [d, d, d, d, d]
-        lib.or_damage_rk4.restype = d
-        lib.or_damage_rk4.argtypes = [P(Material), d, d, d, d, d, d, d]
-        lib.or_plastic_return_cell.argtypes = [P(Material), i, P(d), P(d), P(d), P(d),
-                                               d, d, P(d), P(d)]
-        _lib = lib
-        return lib
+        _lib = _bind(ctypes.CDLL(LIB))
+        return _lib
+
+
+def load_from(path: str):
+    """Another build of the oracle source (the tests compile copies with a
+    planted mistake to show that the pins catch it)."""
+    return _bind(ctypes.CDLL(os.path.abspath(path)))
+
+
+def _bind(lib):
+    P = ctypes.POINTER
+    d, i, L = ctypes.c_double, ctypes.c_int, ctypes.c_long
+    lib.or_create.restype = ctypes.c_void_p
+    lib.or_create.argtypes = [i, P(L), P(d), P(d), P(i), i, P(Material), P(d),
+                              P(ctypes.c_float), P(L), P(d), P(d), P(i)]
+    lib.or_destroy.argtypes = [ctypes.c_void_p]
+    lib.or_nfield.argtypes = [ctypes.c_void_p]
+    lib.or_ncell.argtypes = [ctypes.c_void_p]
+    lib.or_ncell.restype = L
+    lib.or_step.argtypes = [ctypes.c_void_p, i, d, d, P(d)]
+    lib.or_cfl_dt.argtypes = [ctypes.c_void_p, d, P(d), P(d)]
+    lib.or_read.argtypes = [ctypes.c_void_p, i, P(d)]
+    lib.or_write_conserved.argtypes = [ctypes.c_void_p, P(d)]
+    lib.or_totals.argtypes = [ctypes.c_void_p, P(d)]
+    lib.or_set_threads.argtypes = [i]
+    lib.or_set_x_scheme.argtypes = [ctypes.c_void_p, i]
+    lib.or_fragments.restype = L
+    lib.or_fragments.argtypes = [ctypes.c_void_p, d, P(L), P(L), P(L), P(d), L]
+    lib.or_thermo.argtypes = [P(Material), d, d, d, P(d)]
+    lib.or_hencky.argtypes = [P(d), P(d), P(d), P(d)]
+    lib.or_lookup.restype = d
+    lib.or_lookup.argtypes = [i, P(ctypes.c_float), P(L), P(d), P(d), P(d)]
+    lib.or_eps_thresh.restype = d
+    lib.or_eps_thresh.argtypes = [d, d, d, d]
+    lib.or_Rt.restype = d
+    lib.or_Rt.argtypes = [d, d, d, d, d]
+    lib.or_damage_rk4.restype = d
+    lib.or_damage_rk4.argtypes = [P(Material), d, d, d, d, d, d, d]
+    lib.or_plastic_return_cell.argtypes = [P(Material), i, P(d), P(d), P(d), P(d),
+                                           d, d, P(d), P(d)]
+    return lib
 
 
 def _dp(a: np.ndarray):
@@ -103,8 +119,8 @@ def _dp(a: np.ndarray):
 class OracleGrid:
     """One oracle grid built from a ``workloads.Case``."""
 
-    def __init__(self, case, threads: int = 0):
-        lib = load()
+    def __init__(self, case, threads: int = 0, lib=None):
+        lib = load() if lib is None else lib
         self.lib = lib
         self.case = case
         if threads:
