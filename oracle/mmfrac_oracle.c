@@ -380,30 +380,20 @@ static void phys_flux(const or_grid* g, int d, const double* u,
 /* continuous.  With G = 0 it is the HLLC solver.                           */
 /* ------------------------------------------------------------------------ */
 
-static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
-                    const double* UR, const aux_t* aR, double* Fo,
-                    double* uface, double Frow[3]) {
+/* Flux through the face from the star side K (left = 1: the left star
+ * region holds the face) of the subsonic Riemann fan: F_K + S_K (U*_K - U_K)
+ * plus the jump across K's shear wave; the face velocity and the row d of
+ * Fbar of that star region. */
+static void star_side_flux(const or_grid* g, int d, int left, const double* UL,
+                           const aux_t* aL, const double* UR, const aux_t* aR,
+                           double SL, double SR, double Ss, double* Fo,
+                           double* uface, double Frow[3]) {
   const double uL = aL->u[d], uR = aR->u[d];
-  const double a1 = uL - aL->cL, a2 = uR - aR->cL;
-  const double b1 = uL + aL->cL, b2 = uR + aR->cL;
-  const double SL = a1 < a2 ? a1 : a2;
-  const double SR = b1 > b2 ? b1 : b2;
-  const double sL = aL->sig[3 * d + d], sR = aR->sig[3 * d + d];
   const double rL = aL->rho, rR = aR->rho;
-  const double Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
-                    (rL * (SL - uL) - rR * (SR - uR));
-  double FK[MAXF];
-  if (SL >= 0.0 || SR <= 0.0) {
-    const aux_t* aK = SL >= 0.0 ? aL : aR;
-    phys_flux(g, d, SL >= 0.0 ? UL : UR, aK, Fo);
-    *uface = aK->u[d];
-    for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
-    return;
-  }
-  const int left = Ss >= 0.0;
   const double* UK = left ? UL : UR;
   const aux_t* aK = left ? aL : aR;
   const double SK = left ? SL : SR;
+  double FK[MAXF];
   phys_flux(g, d, UK, aK, FK);
   const double uK = aK->u[d];
   for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
@@ -456,6 +446,45 @@ static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
   }
   const double SSK = left ? Ss - csL : Ss + csR;
   for (int k = 0; k < g->nfield; ++k) Fo[k] += SSK * (Uss[k] - Us[k]);
+}
+
+static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
+                    const double* UR, const aux_t* aR, double* Fo,
+                    double* uface, double Frow[3]) {
+  const double uL = aL->u[d], uR = aR->u[d];
+  const double a1 = uL - aL->cL, a2 = uR - aR->cL;
+  const double b1 = uL + aL->cL, b2 = uR + aR->cL;
+  const double SL = a1 < a2 ? a1 : a2;
+  const double SR = b1 > b2 ? b1 : b2;
+  const double sL = aL->sig[3 * d + d], sR = aR->sig[3 * d + d];
+  const double rL = aL->rho, rR = aR->rho;
+  const double Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+                    (rL * (SL - uL) - rR * (SR - uR));
+  if (SL >= 0.0 || SR <= 0.0) {
+    const aux_t* aK = SL >= 0.0 ? aL : aR;
+    phys_flux(g, d, SL >= 0.0 ? UL : UR, aK, Fo);
+    *uface = aK->u[d];
+    for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
+    return;
+  }
+  /* A contact at rest (S* zero to within the rounding of the wave speeds, as
+   * at a reflective wall or on any symmetry plane) lies on the face itself:
+   * the face takes the mean of what the two star sides give (R31).  The two
+   * agree in the conserved fields; in the tangential rows of Fbar, the row d
+   * and the face velocity they differ, and the mean makes the face
+   * independent of the sign of a rounded zero.  At a wall it gives the
+   * kinematics of a free-slip wall: no flux of the tangential rows, row d
+   * without tangential entries. */
+  if (fabs(Ss) <= 16.0 * DBL_EPSILON * (SR - SL)) {
+    double FL[MAXF], FR[MAXF], ufL, ufR, rowL[3], rowR[3];
+    star_side_flux(g, d, 1, UL, aL, UR, aR, SL, SR, Ss, FL, &ufL, rowL);
+    star_side_flux(g, d, 0, UL, aL, UR, aR, SL, SR, Ss, FR, &ufR, rowR);
+    for (int k = 0; k < g->nfield; ++k) Fo[k] = 0.5 * (FL[k] + FR[k]);
+    *uface = 0.5 * (ufL + ufR);
+    for (int j = 0; j < 3; ++j) Frow[j] = 0.5 * (rowL[j] + rowR[j]);
+    return;
+  }
+  star_side_flux(g, d, Ss >= 0.0, UL, aL, UR, aR, SL, SR, Ss, Fo, uface, Frow);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,90 @@
+"""The pins have teeth: copies of the oracle with one plausible mistake
+planted (a sign, a side, an index, a skipped term in the shear-wave branch
+of the Riemann solver, the reflective ghosts, the 3D tangential loop, the
+totals' cell volume, the rule for a contact at rest) are each caught by at
+least one check of tests/pins_waves.py.  Each copy is compiled to a
+temporary library and checked in a child process.  CPU only."""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+sys.path.insert(0, ROOT)
+from oracle import oracle as O  # noqa: E402
+
+# (name, text in mmfrac_oracle.c, replacement): each text occurs exactly once
+MUTANTS = [
+    ("shear_row_sign",
+     "Us[g->o_F + c] + sgn * aK->F[3 * d + j] * du / csK",
+     "Us[g->o_F + c] - sgn * aK->F[3 * d + j] * du / csK"),
+    ("shear_star_density_side",
+     "const double rsK = left ? rsL : rsR;",
+     "const double rsK = left ? rsR : rsL;"),
+    ("shear_energy_sign",
+     "Uss[g->o_E] += sgn * (tss * uss - tauK * uKt) / csK;",
+     "Uss[g->o_E] -= sgn * (tss * uss - tauK * uKt) / csK;"),
+    ("shear_impedance_swap",
+     "const double uss = (tauR - tauL + ZL * uLt + ZR * uRt) / (ZL + ZR);",
+     "const double uss = (tauR - tauL + ZR * uLt + ZL * uRt) / (ZL + ZR);"),
+    ("shear_tangential_z_skipped",
+     "for (int t = 0; t < g->dim; ++t) {\n    if (t == d) continue;",
+     "for (int t = 0; t < 2 && t < g->dim; ++t) {\n    if (t == d) continue;"),
+    ("mirror_flips_diagonal_too",
+     "if ((i == d) != (j == d)) u[g->o_F + c] = -u[g->o_F + c];",
+     "if ((i == d) || (j == d)) u[g->o_F + c] = -u[g->o_F + c];"),
+    ("mirror_keeps_normal_velocity",
+     "u[g->o_mom + d] = -u[g->o_mom + d];",
+     "u[g->o_mom + d] = u[g->o_mom + d];"),
+    ("mirror_keeps_X",
+     "u[g->o_X + d] = 2.0 * wall - u[g->o_X + d];",
+     "u[g->o_X + d] = u[g->o_X + d];"),
+    ("reflective_ghost_order",
+     "src = side == 0 ? m : n - 1 - m;",
+     "src = side == 0 ? 1 - m : n - 2 + m;"),
+    ("totals_cubic_cells",
+     "double dV = 1.0;\n  for (int k = 0; k < g->dim; ++k) dV *= g->dx[k];\n  const int nq",
+     "double dV = 1.0;\n  for (int k = 0; k < g->dim; ++k) dV *= g->dx[0];\n  const int nq"),
+    ("contact_at_rest_takes_one_side",
+     "if (fabs(Ss) <= 16.0 * DBL_EPSILON * (SR - SL)) {",
+     "if (0) {"),
+]
+
+
+def _build(name, old, new, tmp):
+    src = open(O.SRC).read()
+    assert src.count(old) == 1, f"{name}: pattern occurs {src.count(old)} times"
+    path = os.path.join(tmp, f"{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    return O.compile_oracle(path, os.path.join(tmp, f"lib{name}.so"))
+
+
+def _check(lib):
+    r = subprocess.run([sys.executable, os.path.join(HERE, "pins_waves.py"), lib, "all"],
+                       capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, OMP_NUM_THREADS="2"))
+    return r.returncode, (r.stdout + r.stderr)[-400:]
+
+
+def test_every_planted_mistake_is_caught():
+    with tempfile.TemporaryDirectory() as tmp:
+        libs = {name: _build(name, old, new, tmp) for name, old, new in MUTANTS}
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            res = dict(zip(libs, ex.map(_check, libs.values())))
+    survived = {k: v[1] for k, v in res.items() if v[0] == 0}
+    assert not survived, f"mistakes no pin catches: {survived}"
+    for k, (rc, out) in res.items():
+        print(k, rc, out.strip().splitlines()[-1] if out.strip() else "")
+
+
+def test_unplanted_copy_passes():
+    # the same build route with nothing changed passes every check
+    with tempfile.TemporaryDirectory() as tmp:
+        lib = _build("unchanged", "#include <float.h>", "#include <float.h>", tmp)
+        rc, out = _check(lib)
+    assert rc == 0, out
