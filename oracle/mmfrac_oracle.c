@@ -425,6 +425,9 @@ static void star_side_flux(const or_grid* g, int d, int left, const double* UL,
   const double csK = left ? csL : csR;
   if (!(ZL + ZR > 0.0)) return;
   if (left ? !(Ss - csL < 0.0) : !(Ss + csR > 0.0)) return;
+  /* a side without shear stiffness has no shear wave (it would coincide
+   * with the contact; reachable at a contact at rest) */
+  if (!(csK > 0.0)) return;
   double Uss[MAXF];
   for (int k = 0; k < g->nfield; ++k) Uss[k] = Us[k];
   const double sgn = left ? 1.0 : -1.0;
@@ -1048,10 +1051,10 @@ int or_plastic_return_cell(const or_material* mats, int nmat,
   const int can_yield = mix_shear(mats, nmat, phi, rho, D, &Gm);
   const double dt3 = cbrt(det3(F));
   for (int k = 0; k < 9; ++k) F[k] /= dt3;
-  double devH[9], h[3], Q[9], lam[3];
-  if (hencky_eig(F, devH, h, Q, lam) != 0) return OR_ENONFINITE;
   *dEps = 0.0;
   if (!can_yield || !(Gm > 0.0)) return OR_OK;
+  double devH[9], h[3], Q[9], lam[3];
+  if (hencky_eig(F, devH, h, Q, lam) != 0) return OR_ENONFINITE;
   const double J = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
   const double str = sqrt(6.0) * Gm * J;
   double dl;
