@@ -171,6 +171,37 @@ __device__ __forceinline__ void store_sources(const KArgs& a, long long idx,
   }
 }
 
+// Still state: zero velocity, and every field but X equal to the reference
+// state (exact comparisons; -0 equals +0).  A line of cells in such states
+// keeps them through a sweep bit for bit, up to the sign of a zero: every
+// slope but those of X is zero, both face states are the cell's, the
+// Riemann problems between them are contacts at rest with equal sides, and
+// the update adds lam (F - F + 0) = 0 to each field (X moves with u = 0).
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ bool same_state(const typename P::R* c, const typename P::X* cx,
+                                           double e, const typename P::R* cr,
+                                           const typename P::X* cxr, double er) {
+  typedef Lay<DIM, NMAT, NH> L;
+  constexpr int NX = Phys<P, DIM, NMAT, NH>::NX;
+  bool s = e == er;
+#pragma unroll
+  for (int f = 0; f < L::oX; ++f) s = s && c[f] == cr[f];
+#pragma unroll
+  for (int k = 0; k < NX; ++k) s = s && cx[k] == cxr[k];
+  return s;
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ bool same_still(const typename P::R* c, const typename P::X* cx,
+                                           double e, const typename P::R* cr,
+                                           const typename P::X* cxr, double er) {
+  typedef Lay<DIM, NMAT, NH> L;
+  bool s = true;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) s = s && c[L::oMOM + k] == 0;
+  return s && same_state<P, DIM, NMAT, NH>(c, cx, e, cr, cxr, er);
+}
+
 // ------------------------------------------------------------------ sweep ----
 template <class P, int DIM, int AX, int V = 0> struct Tile;
 // The halo-extended tile (TL + 4) x TW equals the CTA, so each phase is one
@@ -238,8 +269,13 @@ struct SweepShape {
 // (carried), so each phase computes only the tile's new items.  carry: move
 // those records to the front for tile ta + 1 at the end.  All threads of the
 // CTA call it together.
+//
+// Still tiles: when every cell of the halo-extended tile holds one still
+// state (same_still against the tile's first cell), the sweep leaves the
+// tile's cells as they are; they are copied to Uout and nothing is
+// computed.  Returns false then (no records to carry), true otherwise.
 template <class P, int DIM, int NMAT, int NH, int AX, int V>
-__device__ __forceinline__ void sweep_tile(const KArgs& a, int ta, int tw, int rr, bool first,
+__device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int rr, bool first,
                                            bool carry, unsigned char* smem, unsigned char* ok1,
                                            unsigned char* ok2) {
   typedef typename P::R R;
@@ -262,6 +298,47 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, int ta, int tw, int r
   const int a0 = ta * TL, w0 = tw * TW;
   const long long step = a.info->steps;
   const R lam = R(a.info->lam[AX]);  // dt / dx_AX of the step
+
+  // 0. still tile?  The reference is the tile's first cell (read by every
+  // thread, one broadcast); each thread tests its cells, velocity first.
+  {
+    R cr[NF];
+    XT cxr[NX];
+    double er;
+    load_cell<P, DIM, NMAT, NH, AX>(a, a0 - 2, w0, rr, cr, cxr, &er);
+    bool still = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) still = still && cr[L::oMOM + k] == R(0);
+    if (still) {
+      for (int it0 = threadIdx.x; it0 < (TL + 4) * TW && still; it0 += NT) {
+        int p, w;
+        SH::pos(it0, TL + 4, p, w);
+        const int gi = a0 - 2 + p;
+        if (w0 + w < ntw && gi >= -2 && gi < na + 2) {
+          R c[NF];
+          XT cx[NX];
+          double eE;
+          load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
+          still = same_still<P, DIM, NMAT, NH>(c, cx, eE, cr, cxr, er);
+        }
+      }
+    }
+    if (__syncthreads_and(still)) {
+      for (int it = threadIdx.x; it < N4; it += NT) {
+        int p4, w;
+        SH::pos(it, TL, p4, w);
+        const int gi = a0 + p4;
+        if (w0 + w < ntw && gi < na) {
+          R c[NF];
+          XT cx[NX];
+          double eE;
+          const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
+          store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
+        }
+      }
+      return false;
+    }
+  }
 
   // 1. primitive recovery of every tile cell, halo of two included
   // (positions 0..3 carried when the tile follows one of the same CTA)
@@ -566,6 +643,7 @@ __device__ __forceinline__ void sweep_tile(const KArgs& a, int ta, int tw, int r
     }
     __syncthreads();
   }
+  return true;
 }
 
 // Tile coordinates of tile index b of a sweep (along AX fastest, then
@@ -608,8 +686,11 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep_col(KArgs a, int
   b /= nch;
   const int tw = int(b % ntt), rr = int(b / ntt);
   const int t0 = ch * K, t1 = t0 + K < nta ? t0 + K : nta;
+  // a tile after a still one starts afresh (nothing was carried)
+  bool first = true;
   for (int ta = t0; ta < t1; ++ta)
-    sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, ta, tw, rr, ta == t0, ta + 1 < t1, smem, ok1, ok2);
+    first = !sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, ta, tw, rr, first, ta + 1 < t1, smem, ok1,
+                                                 ok2);
 }
 
 // ------------------------------------------------------------ batches ----
@@ -862,30 +943,34 @@ __device__ __noinline__ void source_full(const KArgs& a, long long cell, typenam
   }
   // dev(H), |dev(H)|, and (for the return) either eigen-pairs or the
   // series form of exp((k-1) dev(H)) - I
+  // (only a cell that can yield and carries shear needs them)
+  const bool yieldable = can_yield && Gm > 0.0;
   R devH[9], h[3], V[9];
   R J2 = R(0);
   bool series = false;
-  if constexpr (P::split) {
-    // series form while the stretch is small (|dev(H)|_F <= 0.05), else
-    // the eigen-pairs are taken below
-    R dH[9], j2;
-    if (hencky_fast(X, dH, j2) && j2 <= R(2.5e-3)) {
+  if (yieldable) {
+    if constexpr (P::split) {
+      // series form while the stretch is small (|dev(H)|_F <= 0.05), else
+      // the eigen-pairs are taken below
+      R dH[9], j2;
+      if (hencky_fast(X, dH, j2) && j2 <= R(2.5e-3)) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) devH[q] = dH[q];
-      J2 = j2;
-      series = true;
+        for (int q = 0; q < 9; ++q) devH[q] = dH[q];
+        J2 = j2;
+        series = true;
+      }
     }
-  }
-  if (!series) {
-    if (!hencky<P::aform>(X, devH, h, V)) {
-      report(a.err, ST_ENONFINITE, cell, step);
-      return;
+    if (!series) {
+      if (!hencky<P::aform>(X, devH, h, V)) {
+        report(a.err, ST_ENONFINITE, cell, step);
+        return;
+      }
+      J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
     }
-    J2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
   }
   double dl = 0.0;
   R km1 = R(0);  // k - 1 of the return factor k = 1 - 3 G dl / sigma_eq
-  if (can_yield && Gm > 0.0) {
+  if (yieldable) {
     // Split path: the equivalent stress, the bracket, the start and the
     // yield-function inputs come from FP32 quantities and are formed in FP32
     // (this part's FP64 pipe is narrow); the Newton iterate and residual
@@ -1102,6 +1187,16 @@ __device__ __forceinline__ void sources_cells(
       XT cx[NX], wx[NX];
       double eE;
       load_at<P, DIM, NMAT, NH>(a, cell, c, cx, &eE);
+      {
+        // Fbar = I exactly (A = 0 in the split form): det Fbar = 1 and
+        // dev(H) = 0, so no trial stress, no plastic increment and no
+        // damage; the source step leaves the cell as it is
+        bool ident = true;
+#pragma unroll
+        for (int k = 0; k < L::NFC; ++k)
+          ident = ident && c[L::oF + k] == ((!P::aform && FC<DIM>::idx(k) % 4 == 0) ? R(1) : R(0));
+        if (ident) break;
+      }
       Aux<R> ax;
       typename PH::Mix mx0;
       if (!PH::template u2w<0>(a, c, cx, w, wx, ax, &eE, &mx0)) {

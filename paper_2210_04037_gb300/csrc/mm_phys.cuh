@@ -64,8 +64,14 @@ __device__ __forceinline__ bool mfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool mfinite(float x) { return isfinite(x); }
 
 template <class R> struct Eps;
-template <> struct Eps<double> { static constexpr double jacobi = 1e-32; };
-template <> struct Eps<float> { static constexpr float jacobi = 1e-14f; };
+template <> struct Eps<double> {
+  static constexpr double jacobi = 1e-32;
+  static constexpr double unit = 2.220446049250313e-16;  // 2^-52
+};
+template <> struct Eps<float> {
+  static constexpr float jacobi = 1e-14f;
+  static constexpr float unit = 1.1920929e-07f;  // 2^-23
+};
 
 // -------------------------------------------------------------- layout ----
 template <int DIM> struct FC;
@@ -751,38 +757,23 @@ struct Phys {
     }
   }
 
-  // HLLD-type Riemann solver for the elastic mixture: outer waves S_L, S_R
-  // (Davis), contact S*, shear waves S* -/+ c_s inside the star regions.
-  // Jumps from the Rankine-Hugoniot conditions of each wave; with G = 0 it
-  // is the HLLC solver.  Outputs the flux, the normal velocity at the face
-  // and the row d of Fbar on the upwind side of the contact.
+  // Flux through the face from star side K (lft: the left star region
+  // holds the face) of the subsonic fan: F_K + S_K (U*_K - U_K) plus the
+  // jump across K's shear wave; the face velocity and the row d of Fbar of
+  // that star region.
   template <int AX>
-  __device__ static void riemann(const R* cL_, const XT* xL, const Aux<R>& aL, const R* cR_,
-                                 const XT* xR, const Aux<R>& aR, R* fo, XT* fox, R& uface,
-                                 R frowo[3]) {
+  __device__ static __forceinline__ void star_side(bool lft, const R* cL_, const XT* xL,
+                                                   const Aux<R>& aL, const R* cR_, const XT* xR,
+                                                   const Aux<R>& aR, R SL, R SR, R Ss, R* fo,
+                                                   XT* fox, R& uface, R frowo[3]) {
     const R uL = aL.u[AX], uR = aR.u[AX];
-    const R a1 = uL - aL.cL, a2 = uR - aR.cL;
-    const R b1 = uL + aL.cL, b2 = uR + aR.cL;
-    const R SL = a1 < a2 ? a1 : a2;
-    const R SR = b1 > b2 ? b1 : b2;
-    const R sL = aL.sd[AX], sR = aR.sd[AX];
     const R rL = aL.rho, rR = aR.rho;
-    const R Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
-                 (rL * (SL - uL) - rR * (SR - uR));
-    // one upwind state: supersonic -> the state on the upwind side of both
-    // waves, subsonic -> the state on the side of the contact holding the face
-    const bool sup = SL >= R(0) || SR <= R(0);
-    const bool lft = sup ? SL >= R(0) : Ss >= R(0);
     const R* cK = lft ? cL_ : cR_;
     const XT* xK = lft ? xL : xR;
     const Aux<R>& aK = lft ? aL : aR;
     flux<AX>(cK, xK, aK, fo, fox);
     frow<AX>(cK, frowo);
     const R uK = aK.u[AX];
-    if (sup) {
-      uface = uK;
-      return;
-    }
     const R SK = lft ? SL : SR;
     const R chi = (SK - uK) / (SK - Ss);
     const R rK = aK.rho;
@@ -829,6 +820,9 @@ struct Phys {
     if (!(ZL + ZR > R(0))) return;
     if (lft ? !(Ss - csL < R(0)) : !(Ss + csR > R(0))) return;
     const R csK = lft ? csL : csR;
+    // a side without shear stiffness has no shear wave (it would coincide
+    // with the contact; reached at a contact at rest)
+    if (!(csK > R(0))) return;
     const R rsK = lft ? rsL : rsR;
     const R sgn = lft ? R(1) : R(-1);
     const R SSK = lft ? Ss - csL : Ss + csR;
@@ -854,6 +848,76 @@ struct Phys {
       ess += XT(sgn) * (XT(tss) * XT(uss) - XT(tauK) * XT(uKt)) / XT(csK);
     }
     fox[0] = fox[0] + XT(SSK) * (ess - Es);
+  }
+
+  // HLLD-type Riemann solver for the elastic mixture: outer waves S_L, S_R
+  // (Davis), contact S*, shear waves S* -/+ c_s inside the star regions.
+  // Jumps from the Rankine-Hugoniot conditions of each wave; with G = 0 it
+  // is the HLLC solver.  Outputs the flux, the normal velocity at the face
+  // and the row d of Fbar of the star region holding the face.  A contact
+  // at rest (S* zero to within the rounding of the wave speeds: a reflective
+  // wall, a symmetry plane, still gas) lies on the face itself, which then
+  // takes the mean of what the two star sides give: it does not depend on
+  // the sign of a rounded zero, and at a wall the tangential rows of Fbar
+  // have no flux.
+  template <int AX>
+  __device__ static void riemann(const R* cL_, const XT* xL, const Aux<R>& aL, const R* cR_,
+                                 const XT* xR, const Aux<R>& aR, R* fo, XT* fox, R& uface,
+                                 R frowo[3]) {
+    const R uL = aL.u[AX], uR = aR.u[AX];
+    const R a1 = uL - aL.cL, a2 = uR - aR.cL;
+    const R b1 = uL + aL.cL, b2 = uR + aR.cL;
+    const R SL = a1 < a2 ? a1 : a2;
+    const R SR = b1 > b2 ? b1 : b2;
+    const R sL = aL.sd[AX], sR = aR.sd[AX];
+    const R rL = aL.rho, rR = aR.rho;
+    R Ss;
+    if constexpr (P::split) {
+      // separately rounded products (no contraction): the numerator is then
+      // exactly odd under the mirror of the face, and exactly zero where the
+      // two sides are mirror images (a wall, a symmetry plane) in every
+      // kernel, whatever the compiler fuses elsewhere
+      const float X = __fmul_rn(__fmul_rn(rL, uL), __fsub_rn(SL, uL));
+      const float Y = __fmul_rn(__fmul_rn(rR, uR), __fsub_rn(SR, uR));
+      const float num = __fadd_rn(__fsub_rn(sL, sR), __fsub_rn(X, Y));
+      const float den = __fsub_rn(__fmul_rn(rL, __fsub_rn(SL, uL)), __fmul_rn(rR, __fsub_rn(SR, uR)));
+      Ss = num / den;
+    } else {
+      Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
+           (rL * (SL - uL) - rR * (SR - uR));
+    }
+    if (SL >= R(0) || SR <= R(0)) {
+      // supersonic: the state on the upwind side of both waves
+      const bool lft = SL >= R(0);
+      const Aux<R>& aK = lft ? aL : aR;
+      flux<AX>(lft ? cL_ : cR_, lft ? xL : xR, aK, fo, fox);
+      frow<AX>(lft ? cL_ : cR_, frowo);
+      uface = aK.u[AX];
+      return;
+    }
+    // at rest: |S*| <= 16 eps (S_R - S_L) with eps = 2^-52 in both
+    // precisions (the FP32 path takes it as the exact zero of a wall or a
+    // symmetry plane; an FP32-rounding threshold would average the sides
+    // of slowly moving contacts)
+    const bool rest = mabs(Ss) <= R(16.0 * Eps<double>::unit) * (SR - SL);
+    // one star side, or both (weights 1/2 each, exact) for a contact at rest;
+    // one code copy for either
+#pragma unroll 1
+    for (int side = 0; side < (rest ? 2 : 1); ++side) {
+      const bool lft = rest ? side == 0 : Ss >= R(0);
+      R f[NF], row[3], uf;
+      XT fx[NX];
+      star_side<AX>(lft, cL_, xL, aL, cR_, xR, aR, SL, SR, Ss, f, fx, uf, row);
+      const R wg = rest ? R(0.5) : R(1);
+      const XT wgx = rest ? XT(0.5) : XT(1);
+#pragma unroll
+      for (int k = 0; k < NF; ++k) fo[k] = (side == 0 ? R(0) : fo[k]) + wg * f[k];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) fox[k] = (side == 0 ? XT(0) : fox[k]) + wgx * fx[k];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) frowo[j] = (side == 0 ? R(0) : frowo[j]) + wg * row[j];
+      uface = (side == 0 ? R(0) : uface) + wg * uf;
+    }
   }
 };
 

@@ -128,9 +128,10 @@ def periodic_mix_3d(n, seed=6, shear=0.03, p0=5e8, dp=5e7, rho_gas=700.0, vel=5.
     return c
 
 
-def shear_bar_2d(n, length, uy_of_x, left=None, right=None, x0=None, bc=(0, 0)):
-    """A bar along x on an n x 2 grid, periodic in y, at rest in x with a
-    transverse velocity u_y(x) and Fbar = I, p = 1e5 Pa, elastic (no
+def shear_bar_2d(n, length, uy_of_x, left=None, right=None, x0=None, bc=(0, 0), ux=0.0):
+    """A bar along x on an n x 2 grid, periodic in y, moving at ux along x
+    (default at rest) with a transverse velocity u_y(x) and Fbar = I,
+    p = 1e5 Pa, elastic (no
     plasticity, no damage).  One material (CuBe) by default; with `right`
     given, two materials: `left` for x < x0 and `right` beyond, each at its
     reference density (a bimaterial interface, volume fractions 1 - 1e-6 /
@@ -148,6 +149,7 @@ def shear_bar_2d(n, length, uy_of_x, left=None, right=None, x0=None, bc=(0, 0)):
     else:
         W.fill_two_phase(c, np.where(x < x0, 1.0, 0.0), left["rho0"], right["rho0"], 1e5,
                          [0 * x, 0 * x])
+    c.prim[lay.o_u] = ux
     c.prim[lay.o_u + 1] = uy_of_x(x)
     c.prim[lay.o_p] = 1e5
     c.prim[lay.o_X] = x

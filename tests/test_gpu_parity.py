@@ -51,7 +51,33 @@ PARITY_CASES = {
     # large enough that the 3D y and z sweeps run chunks of 9 consecutive
     # tiles per CTA, reusing each tile's overlap with the next
     "cylinder_3d_128_tile_chunks": (lambda: W.cylinder_3d(128), 3),
+    # shear waves across a CuBe / Al-H32 interface moving at 2 m/s (the
+    # oracle pin's case, boosted so that the normal velocity is not a
+    # second-order field measured against its own tiny norm)
+    "shear_bimaterial_2d": (lambda: _pin_shear_bimaterial(), 100),
+    # reflective walls at both ends of one axis, the others periodic
+    "reflective_walls_gas_1d": (lambda: _pin_reflective("gas_1d"), 60),
+    "reflective_walls_solid_1d": (lambda: _pin_reflective("solid_1d"), 100),
+    "reflective_walls_x_2d": (lambda: _pin_reflective("mix_2d_x"), 60),
+    "reflective_walls_y_2d": (lambda: _pin_reflective("mix_2d_y"), 60),
+    "reflective_walls_z_3d": (lambda: _pin_reflective("mix_3d_z"), 40),
+    # the 2D mixture with shear laid in the y-z plane of a 3D grid (two
+    # cells along x): the z sweep carries the in-plane shear
+    "mix_2d_in_yz_plane_3d": (lambda: cases.embed_3d(cases.periodic_mix_2d(14, seed=3, shear=0.03),
+                                                     (1, 2))[0], 60),
 }
+
+
+def _pin_shear_bimaterial():
+    import pins_waves as P
+    L = 4e-3
+    return cases.shear_bar_2d(600, L, lambda x: np.where(x < L / 2, -4.0, 12.0), left=P.CUBE,
+                              right=P.AL, x0=L / 2, ux=2.0)
+
+
+def _pin_reflective(kind):
+    import pins_waves as P
+    return P.reflective_case(kind)[0]
 
 
 @pytest.mark.parametrize("name", list(PARITY_CASES))
