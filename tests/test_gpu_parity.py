@@ -42,6 +42,12 @@ PARITY_CASES = {
     "spall_1d_1000": (lambda: W.spall_1d(1000), 100),
     "ring_2d_90": (lambda: W.ring_2d(90), 60),
     "cylinder_3d_28x28x20": (lambda: W.cylinder_3d(28, nz=20, width=0.048), 30),
+    # the largest sizes the oracle steps within a test's budget, over the
+    # horizon on which the oracle started from a 1e-15 perturbation of the
+    # same state still agrees with itself to 1e-10 (256^2: 3.3e-11 at 40
+    # steps, 1.3e-4 at 60; 64^3: 3.8e-11 at 30, 6.6e-10 at 40)
+    "ring_2d_256": (lambda: W.ring_2d(256), 40),
+    "cylinder_3d_64": (lambda: W.cylinder_3d(64), 30),
     "periodic_mix_2d_50": (lambda: cases.periodic_mix_2d(50, shear=0.03), 100),
     "reflective_mix_2d_36": (lambda: cases.periodic_mix_2d(36, shear=0.03, bc=2), 100),
     "periodic_mix_3d_18x20x14": (lambda: cases.periodic_mix_3d(18, nz=14), 100),
