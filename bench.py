@@ -512,16 +512,18 @@ def time_alone(cases, precision, steps, stream):
     return total
 
 
-def run_ensemble(args, rank: int, world: int):
+def run_ensemble(args, rank: int, world: int, nested: bool = False, dist=None):
+    """The batched ensemble's line; nested: inside another workload's run
+    (process group and device already set up, nothing printed, the line
+    returned)."""
     import torch
     from paper_2210_04037_gb300 import mmfrac
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
+    if world > 1 and not nested:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    m = args.size or DEFAULT_SIZE["ensemble_2d"]
+    m = (args.size if not nested else 0) or DEFAULT_SIZE["ensemble_2d"]
     members = ensemble_cases(m)
     ncell = sum(c.ncell for c in members)
     prec = W.FP32_SPLIT if args.precision == "fp32split" else W.FP64
@@ -606,6 +608,8 @@ def run_ensemble(args, rank: int, world: int):
         "clocks": clk.summary(),
         "gpu_launches": args.steps * (3 + 2),
     }
+    if nested:
+        return line
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline("ensemble_2d", m)
     if rank == 0:
@@ -615,12 +619,13 @@ def run_ensemble(args, rank: int, world: int):
         dist.destroy_process_group()
 
 
-def run_serve(args, rank: int, world: int):
+def run_serve(args, rank: int, world: int, nested: bool = False):
+    """The served-runs line; nested: returned instead of printed."""
     import torch
     from paper_2210_04037_gb300 import mmfrac
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    count = args.size or DEFAULT_SIZE["serve"]
+    count = (args.size if not nested else 0) or DEFAULT_SIZE["serve"]
     reqs = serve_requests(count, seed=7 + rank)
     cases = [serve_case(k, n, 200 + i) for i, (k, n, _, _) in enumerate(reqs)]
     work = [c.ncell * st for c, (_, _, st, _) in zip(cases, reqs)]
@@ -677,6 +682,8 @@ def run_serve(args, rank: int, world: int):
         "roofline": None,
         "clocks": clk.summary(),
     }
+    if nested:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -808,6 +815,12 @@ def run_gpu(args, rank: int, world: int):
         line["fp64"] = fp64
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload, n)
+    if args.workload == "cylinder_3d" and not args.no_extra:
+        # the batched ensemble and the served runs, measured in the same run
+        # (each rank its own replica of them), so that their numbers are
+        # taken beside the headline
+        line["ensemble_2d"] = run_ensemble(args, rank, world, nested=True, dist=dist)
+        line["serve"] = run_serve(args, rank, world, nested=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -827,6 +840,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="cylinder workload: skip the nested ensemble and served-runs lines")
     ap.add_argument("--x-transport", default="sweep", choices=["sweep", "weno3rk3"],
                     help="transport of the Lagrangian coordinates (default: with the sweeps)")
     args = ap.parse_args()
