@@ -45,6 +45,7 @@ struct or_grid {
   int bc[3][2];
   or_material mat[OR_MAXMAT];
   int hslot[OR_MAXMAT]; /* history slot of material l, or -1 */
+  int void_l;           /* index of the void material (eos 2), or -1 */
   int Fidx[9];          /* row-major index (3i+j) of each stored Fbar comp */
   int o_phi, o_arho, o_mom, o_E, o_F, o_hist, o_X;
   double *U, *V; /* conserved state and sweep output, [nfield][ncell] */
@@ -92,6 +93,11 @@ void or_thermo(const or_material* m, double rho, double psi, double J2,
     out[2] = 0.0;
     out[3] = 0.0;
     out[4] = m->gamma_gas - 1.0;
+    return;
+  }
+  if (m->eos == 2) {  /* void: no energy, no pressure, no shear */
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    out[4] = 1.0;
     return;
   }
   const double a = m->alpha;
@@ -200,6 +206,12 @@ int or_hencky(const double F[9], double devH[9], double lam[3], double Q[9]) {
 
 static int is_damaged(const or_material* m) { return m->damage != 0; }
 
+/* The void volume fraction nu (Sec. 2.1) is carried as a material of its
+ * own (eos 2): its fraction is advected like the others, it has no mass, no
+ * energy and no stress, and it takes no part in the pressure equilibrium of
+ * the materials (R33). */
+static int is_void(const or_material* m) { return m->eos == 2; }
+
 /* Full local views of a stored state vector (inactive components: 0 / I). */
 static void full_F(const or_grid* g, const double* w, double F[9]) {
   for (int k = 0; k < 9; ++k) F[k] = (k % 4 == 0) ? 1.0 : 0.0;
@@ -235,6 +247,7 @@ static int mixture(const or_grid* g, const double* phi, const double* rho_l,
   for (int l = 0; l < g->nmat; ++l) {
     const double psi = is_damaged(&g->mat[l]) ? 1.0 - Dl[l] : 1.0;
     or_thermo(&g->mat[l], rho_l[l], psi, mx->J2, mx->th[l]);
+    if (is_void(&g->mat[l])) continue;
     mx->xi += phi[l] / mx->th[l][4];
     mx->Gmix += phi[l] * mx->th[l][3];
   }
@@ -244,13 +257,18 @@ static int mixture(const or_grid* g, const double* phi, const double* rho_l,
 /* Stress sigma = -p I + 2 G dev(H) (R5) and longitudinal sound speed (R6). */
 static int finish_aux(const or_grid* g, const double* phi, const double* rho_l,
                       const double* arho, const mix_t* mx, aux_t* ax) {
+  /* with void in the cell the materials fill 1 - nu of it and the pressure
+   * part of the stress is theirs times that fraction (the void carries
+   * none); the shear part is already weighted by the fractions (R33) */
+  const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
       ax->sig[3 * i + j] =
-          (i == j ? -ax->p : 0.0) + 2.0 * mx->Gmix * mx->devH[3 * i + j];
+          (i == j ? -pm : 0.0) + 2.0 * mx->Gmix * mx->devH[3 * i + j];
   /* frozen mixture sound speed: xi c^2 = sum_l y_l xi_l c_l^2 */
   double s = 0.0;
   for (int l = 0; l < g->nmat; ++l) {
+    if (is_void(&g->mat[l])) continue;
     const double Gam = mx->th[l][4];
     const double cl2 = mx->th[l][2] + (Gam + 1.0) * (ax->p - mx->th[l][1]) /
                                           rho_l[l];
@@ -271,6 +289,14 @@ static int w2u(const or_grid* g, const double* w, double* u, aux_t* ax) {
   vol_fracs(g, w, phi);
   ax->rho = 0.0;
   for (int l = 0; l < g->nmat; ++l) {
+    Dl[l] = 0.0;
+    if (is_void(&g->mat[l])) {
+      /* no mass; the fraction may be zero */
+      if (!(phi[l] >= 0.0)) return -1;
+      rho_l[l] = 0.0;
+      arho[l] = 0.0;
+      continue;
+    }
     if (!(phi[l] > 0.0)) return -1;
     rho_l[l] = w[g->o_arho + l];
     if (!(rho_l[l] > 0.0)) return -1;
@@ -311,6 +337,11 @@ static int u2w(const or_grid* g, const double* u, double* w, aux_t* ax) {
   ax->rho = 0.0;
   for (int l = 0; l < g->nmat; ++l) {
     arho[l] = u[g->o_arho + l];
+    if (is_void(&g->mat[l])) {
+      if (!(phi[l] >= 0.0)) return -1;
+      rho_l[l] = 0.0;
+      continue;
+    }
     if (!(phi[l] > 0.0) || !(arho[l] > 0.0)) return -1;
     rho_l[l] = arho[l] / phi[l];
     ax->rho += arho[l];
@@ -451,9 +482,9 @@ static void star_side_flux(const or_grid* g, int d, int left, const double* UL,
   for (int k = 0; k < g->nfield; ++k) Fo[k] += SSK * (Uss[k] - Us[k]);
 }
 
-static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
-                    const double* UR, const aux_t* aR, double* Fo,
-                    double* uface, double Frow[3]) {
+static void riemann_contact(const or_grid* g, int d, const double* UL, const aux_t* aL,
+                            const double* UR, const aux_t* aR, double* Fo,
+                            double* uface, double Frow[3]) {
   const double uL = aL->u[d], uR = aR->u[d];
   const double a1 = uL - aL->cL, a2 = uR - aR->cL;
   const double b1 = uL + aL->cL, b2 = uR + aR->cL;
@@ -488,6 +519,149 @@ static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
     return;
   }
   star_side_flux(g, d, Ss >= 0.0, UL, aL, UR, aR, SL, SR, Ss, Fo, uface, Frow);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Void opening (Sec. 3.1: the void-opening flux modifier applied where     */
+/* either face state is critically damaged and the two are in tension along */
+/* the sweep, x^T (sigma_L + sigma_R) x > 0).  The modifier itself is in a  */
+/* paper not available; reading R33: each side meets a traction-free        */
+/* surface (the Riemann problem of a material against void), and where the  */
+/* two surfaces separate, the gap between them is void.                     */
+/* ------------------------------------------------------------------------ */
+
+/* A damaged solid at D >= D_crit (within 1e-6: D comes back as the ratio
+ * (phi rho D) / (phi rho), so a capped cell can read one rounding below). */
+static int critical_state(const or_grid* g, const double* U) {
+  for (int l = 0; l < g->nmat; ++l) {
+    const int h = g->hslot[l];
+    if (h < 0 || !is_damaged(&g->mat[l])) continue;
+    const double arho = U[g->o_arho + l];
+    if (!(arho > 0.0)) continue;
+    if (U[g->o_hist + 2 * h + 1] / arho >= g->mat[l].D_crit * (1.0 - 1e-6)) return 1;
+  }
+  return 0;
+}
+
+/* Speed of side K's traction-free surface: across K's longitudinal wave
+ * S_K = u_K -/+ c_L,K the normal stress drops to zero,
+ * 0 = sigma_K - rho_K (S_K - u_K)(S_f - u_K)  (HLLC jump relation). */
+static double free_surface_speed(int d, int left, const aux_t* a) {
+  const double SK = left ? a->u[d] - a->cL : a->u[d] + a->cL;
+  return a->u[d] + a->sig[3 * d + d] / (a->rho * (SK - a->u[d]));
+}
+
+/* Flux of side K's fan against a traction-free surface: waves S_K, the
+ * shear wave S_f -/+ c_s and the surface S_f; in the star regions the
+ * normal stress and then the tangential tractions are zero.  at_face: the
+ * region holding x/t = 0; otherwise the region just inside the surface.
+ * Fo, uface, Frow as in the contact solver. */
+static void free_surface_flux(const or_grid* g, int d, int left, const double* UK,
+                              const aux_t* aK, int at_face, double* Fo, double* uface,
+                              double Frow[3]) {
+  const double uK = aK->u[d];
+  const double SK = left ? uK - aK->cL : uK + aK->cL;
+  const double Sf = free_surface_speed(d, left, aK);
+  for (int j = 0; j < 3; ++j) Frow[j] = aK->F[3 * d + j];
+  phys_flux(g, d, UK, aK, Fo);
+  *uface = uK;
+  if (at_face && (left ? SK >= 0.0 : SK <= 0.0)) return; /* region K */
+  const double chi = (SK - uK) / (SK - Sf);
+  const double rK = aK->rho;
+  double Us[MAXF];
+  for (int l = 0; l + 1 < g->nmat; ++l) Us[g->o_phi + l] = UK[g->o_phi + l] * chi;
+  for (int l = 0; l < g->nmat; ++l) Us[g->o_arho + l] = UK[g->o_arho + l] * chi;
+  for (int k = 0; k < g->dim; ++k)
+    Us[g->o_mom + k] = (k == d) ? rK * chi * Sf : UK[g->o_mom + k] * chi;
+  Us[g->o_E] = chi * (UK[g->o_E] + rK * Sf * (Sf - uK) -
+                      aK->sig[3 * d + d] * (Sf - uK) / (SK - uK));
+  for (int c = 0; c < g->nF; ++c) {
+    const int i = g->Fidx[c] / 3;
+    Us[g->o_F + c] = (i == d) ? UK[g->o_F + c] : UK[g->o_F + c] * chi;
+  }
+  for (int k = 0; k < 2 * g->nhist; ++k) Us[g->o_hist + k] = UK[g->o_hist + k] * chi;
+  for (int k = 0; k < g->dim; ++k) Us[g->o_X + k] = UK[g->o_X + k] * chi;
+  for (int k = 0; k < g->nfield; ++k) Fo[k] += SK * (Us[k] - UK[k]);
+  *uface = uK + SK * (chi - 1.0);
+  /* the shear wave: speed from the star density, kept between S_K and S_f */
+  const double rs = rK * ((SK - uK) / (SK - Sf));
+  double cs = sqrt(aK->G / rs);
+  if (cs > fabs(Sf - SK)) cs = fabs(Sf - SK);
+  if (!(cs > 0.0)) return;
+  const double SSK = left ? Sf - cs : Sf + cs;
+  if (at_face && (left ? SSK >= 0.0 : SSK <= 0.0)) return; /* region K* */
+  const double Z = rs * cs, sgn = left ? 1.0 : -1.0;
+  double Uss[MAXF];
+  for (int k = 0; k < g->nfield; ++k) Uss[k] = Us[k];
+  for (int t = 0; t < g->dim; ++t) {
+    if (t == d) continue;
+    const double tau = aK->sig[3 * t + d], ut = aK->u[t];
+    /* zero traction behind the shear wave: tau + sgn Z (uss - ut) = 0 */
+    const double uss = ut - sgn * tau / Z;
+    const double du = uss - ut;
+    Uss[g->o_mom + t] = rs * uss;
+    for (int c = 0; c < g->nF; ++c) {
+      const int i = g->Fidx[c] / 3, j = g->Fidx[c] % 3;
+      if (i == t) Uss[g->o_F + c] = Us[g->o_F + c] + sgn * aK->F[3 * d + j] * du / cs;
+    }
+    Uss[g->o_E] += sgn * (0.0 * uss - tau * ut) / cs;
+  }
+  for (int k = 0; k < g->nfield; ++k) Fo[k] += SSK * (Uss[k] - Us[k]);
+}
+
+/* Riemann problem at a face: the face records of its left cell (FoL, ufL,
+ * FrL: what the cell left of the face sees) and of its right cell.  They
+ * are the same record (the contact solver) unless the void opens.  Where it
+ * opens, each side's traction-free surface S_f,K sets that side's face
+ * velocity, its Fbar and X transport; the conserved fields and the
+ * material fractions take what crosses the face (nothing when the gap
+ * holds the face; the fan of the side whose surface has passed it
+ * otherwise), and the void fraction takes the rest, so that every side's
+ * fractions stay summing to one: a side that receives the gap gets void at
+ * the rate S_f,own - u_crossing. */
+static void riemann(const or_grid* g, int d, const double* UL, const aux_t* aL,
+                    const double* UR, const aux_t* aR, double* FoL, double* ufL,
+                    double FrL[3], double* FoR, double* ufR, double FrR[3]) {
+  const int nf = g->nfield;
+  if (g->void_l >= 0 && (critical_state(g, UL) || critical_state(g, UR)) &&
+      aL->sig[3 * d + d] + aR->sig[3 * d + d] > 0.0) {
+    const double SfL = free_surface_speed(d, 1, aL), SfR = free_surface_speed(d, 0, aR);
+    if (SfL < SfR) {
+      double Fs[2][MAXF], ufs[2], rows[2][3], Fc[MAXF], ufc = 0.0, rowc[3];
+      free_surface_flux(g, d, 1, UL, aL, 0, Fs[0], &ufs[0], rows[0]);
+      free_surface_flux(g, d, 0, UR, aR, 0, Fs[1], &ufs[1], rows[1]);
+      int cross = -1; /* the side whose fan holds the face, or none */
+      for (int k = 0; k < nf; ++k) Fc[k] = 0.0;
+      if (SfL > 0.0) {
+        cross = 0;
+        free_surface_flux(g, d, 1, UL, aL, 1, Fc, &ufc, rowc);
+      } else if (SfR < 0.0) {
+        cross = 1;
+        free_surface_flux(g, d, 0, UR, aR, 1, Fc, &ufc, rowc);
+      }
+      for (int side = 0; side < 2; ++side) {
+        double* Fo = side == 0 ? FoL : FoR;
+        double* uf = side == 0 ? ufL : ufR;
+        double* Fr = side == 0 ? FrL : FrR;
+        for (int j = 0; j < 3; ++j) Fr[j] = rows[side][j];
+        if (cross == side) {
+          for (int k = 0; k < nf; ++k) Fo[k] = Fc[k];
+          *uf = ufc;
+          continue;
+        }
+        for (int k = 0; k < nf; ++k) Fo[k] = Fc[k];
+        for (int c = 0; c < g->nF; ++c) Fo[g->o_F + c] = Fs[side][g->o_F + c];
+        for (int k = 0; k < g->dim; ++k) Fo[g->o_X + k] = Fs[side][g->o_X + k];
+        Fo[g->o_phi + g->void_l] += ufs[side] - ufc;
+        *uf = ufs[side];
+      }
+      return;
+    }
+  }
+  riemann_contact(g, d, UL, aL, UR, aR, FoL, ufL, FrL);
+  for (int k = 0; k < nf; ++k) FoR[k] = FoL[k];
+  *ufR = *ufL;
+  for (int j = 0; j < 3; ++j) FrR[j] = FrL[j];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -647,9 +821,14 @@ static int sweep_line(const or_grid* g, int d, double dt, long line,
   aux_t* A = malloc(sizeof(aux_t) * ne);
   double* FS = malloc(sizeof(double) * ne * 2 * nf); /* face states per cell */
   aux_t* FA = malloc(sizeof(aux_t) * ne * 2);
-  double* FX = malloc(sizeof(double) * ne * nf);     /* face fluxes */
-  double* UF = malloc(sizeof(double) * ne);          /* face velocity */
-  double* FR = malloc(sizeof(double) * ne * 3);      /* face Fbar row d */
+  /* face records as the cell left of the face sees them, then as the cell
+   * right of it sees them (the two differ only where the void opens) */
+  double* FX = malloc(sizeof(double) * ne * nf * 2); /* face fluxes */
+  double* UF = malloc(sizeof(double) * ne * 2);      /* face velocity */
+  double* FR = malloc(sizeof(double) * ne * 6);      /* face Fbar row d */
+  double* FXr = FX + ne * nf;
+  double* UFr = UF + ne;
+  double* FRr = FR + ne * 3;
   int rc = OR_OK;
   for (long c = 0; c < n; ++c)
     for (int k = 0; k < nf; ++k)
@@ -675,19 +854,29 @@ static int sweep_line(const or_grid* g, int d, double dt, long line,
   /* 3. HLLC on faces between ext e and e+1, e = 1 .. n+1 */
   for (size_t e = 1; e <= (size_t)n + 1; ++e) {
     riemann(g, d, FS + (2 * e + 1) * nf, &FA[2 * e + 1], FS + (2 * (e + 1)) * nf,
-         &FA[2 * (e + 1)], FX + e * nf, &UF[e], FR + 3 * e);
+            &FA[2 * (e + 1)], FX + e * nf, &UF[e], FR + 3 * e, FXr + e * nf, &UFr[e],
+            FRr + 3 * e);
   }
-  /* 4. update of cells 0 .. n-1 (ext 2 .. n+1): face e-1 is left, e right */
+  /* 4. update of cells 0 .. n-1 (ext 2 .. n+1): face e-1 is left, e right;
+   * the cell takes the right-cell record of its left face and the
+   * left-cell record of its right face */
   for (size_t e = 2; e <= (size_t)n + 1; ++e) {
     const double* uc = ext + e * nf;
-    const double du = UF[e] - UF[e - 1];
+    const double du = UF[e] - UFr[e - 1];
     double dF[3], nc[MAXF];
-    for (int j = 0; j < 3; ++j) dF[j] = FR[3 * e + j] - FR[3 * (e - 1) + j];
+    for (int j = 0; j < 3; ++j) dF[j] = FR[3 * e + j] - FRr[3 * (e - 1) + j];
     noncons(g, d, W + e * nf, &A[e], du, dF, nc);
     const long cell = base + ((long)e - 2) * stride;
     for (int k = 0; k < nf; ++k)
       g->V[(size_t)k * g->ncell + cell] =
-          uc[k] + lam * ((FX[(e - 1) * nf + k] - FX[e * nf + k]) + nc[k]);
+          uc[k] + lam * ((FXr[(e - 1) * nf + k] - FX[e * nf + k]) + nc[k]);
+    /* the void fraction is created only where the void opens; its transport
+     * of traces (ahead of an opening crack it falls off to 1e-300 and
+     * below) can leave it a rounding below zero, which is taken as zero */
+    if (g->void_l >= 0) {
+      double* nu = &g->V[(size_t)(g->o_phi + g->void_l) * g->ncell + cell];
+      if (*nu < 0.0) *nu = 0.0;
+    }
   }
 done:
   free(ext); free(W); free(A); free(FS); free(FA); free(FX); free(UF); free(FR);
@@ -1208,9 +1397,19 @@ or_grid* or_create(int dim, const long n[3], const double lo[3],
     if (k < dim && g->n[k] < 2) { free(g); return NULL; }
   }
   g->nhist = 0;
+  g->void_l = -1;
   for (int l = 0; l < nmat; ++l) {
     g->mat[l] = mats[l];
     g->hslot[l] = mats[l].plasticity == 1 ? g->nhist++ : -1;
+    if (mats[l].eos == 2) {
+      /* one void at most, never the last material (whose fraction is
+       * formed as one minus the others), with no strength or damage model */
+      if (g->void_l >= 0 || l == nmat - 1 || mats[l].plasticity != 0 || mats[l].damage != 0) {
+        free(g);
+        return NULL;
+      }
+      g->void_l = l;
+    }
   }
   static const int F1[] = {0, 4, 8};
   static const int F2[] = {0, 1, 3, 4, 8};

@@ -48,7 +48,8 @@ extern "C" {
 #define OR_ENOCONV (-5)
 
 typedef struct {
-  int eos;                /* 0 ideal gas, 1 Romenskii solid */
+  int eos;                /* 0 ideal gas, 1 Romenskii solid, 2 void (massless,
+                             stress-free; at most one, never the last material) */
   double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
   int plasticity;         /* 0 none, 1 Johnson-Cook (no thermal term) */
   double c1, c2, c3, n_hard, edot0;

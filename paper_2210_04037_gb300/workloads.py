@@ -80,6 +80,13 @@ def al_h32(damage: str = "simple", plastic: bool = True) -> Dict[str, float]:
     return m
 
 
+def void() -> Dict[str, float]:
+    """The void volume fraction nu of Sec. 2.1, carried as a material of its
+    own (eos 2): no mass, no energy, no stress; it takes the volume a
+    void-opening face creates (Sec. 3.1).  Never the last material."""
+    return material(eos=2, rho0=0.0)
+
+
 def steel_304l_disk() -> Dict[str, float]:
     """304L: Romenskii row, Johnson-Cook hardening/rate (thermal term not
     modelled), Bonora row of the expanding-disk test."""

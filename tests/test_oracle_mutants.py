@@ -1,8 +1,10 @@
 """The pins have teeth: copies of the oracle with one plausible mistake
 planted (a sign, a side, an index, a skipped term in the shear-wave branch
 of the Riemann solver, the reflective ghosts, the 3D tangential loop, the
-totals' cell volume, the rule for a contact at rest) are each caught by at
-least one check of tests/pins_waves.py.  Each copy is compiled to a
+totals' cell volume, the rule for a contact at rest, the void-opening
+modifier's tension test, critical-damage test, surface speed, gap volume,
+mass flux and the void's share of the stress) are each caught by at least
+one check of tests/pins_void.py or tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
 import concurrent.futures as cf
 import os
@@ -32,8 +34,8 @@ MUTANTS = [
      "const double uss = (tauR - tauL + ZL * uLt + ZR * uRt) / (ZL + ZR);",
      "const double uss = (tauR - tauL + ZR * uLt + ZL * uRt) / (ZL + ZR);"),
     ("shear_tangential_z_skipped",
-     "for (int t = 0; t < g->dim; ++t) {\n    if (t == d) continue;",
-     "for (int t = 0; t < 2 && t < g->dim; ++t) {\n    if (t == d) continue;"),
+     "for (int t = 0; t < g->dim; ++t) {\n    if (t == d) continue;\n    const double uLt",
+     "for (int t = 0; t < 2 && t < g->dim; ++t) {\n    if (t == d) continue;\n    const double uLt"),
     ("mirror_flips_diagonal_too",
      "if ((i == d) != (j == d)) u[g->o_F + c] = -u[g->o_F + c];",
      "if ((i == d) || (j == d)) u[g->o_F + c] = -u[g->o_F + c];"),
@@ -52,6 +54,24 @@ MUTANTS = [
     ("contact_at_rest_takes_one_side",
      "if (fabs(Ss) <= 16.0 * DBL_EPSILON * (SR - SL)) {",
      "if (0) {"),
+    ("void_opens_in_compression",
+     "aL->sig[3 * d + d] + aR->sig[3 * d + d] > 0.0) {",
+     "aL->sig[3 * d + d] + aR->sig[3 * d + d] < 0.0) {"),
+    ("void_opens_without_critical_damage",
+     "if (U[g->o_hist + 2 * h + 1] / arho >= g->mat[l].D_crit * (1.0 - 1e-6)) return 1;",
+     "if (U[g->o_hist + 2 * h + 1] / arho >= 0.9 * g->mat[l].D_crit) return 1;"),
+    ("free_surface_speed_sign",
+     "return a->u[d] + a->sig[3 * d + d] / (a->rho * (SK - a->u[d]));",
+     "return a->u[d] - a->sig[3 * d + d] / (a->rho * (SK - a->u[d]));"),
+    ("gap_void_sign",
+     "Fo[g->o_phi + g->void_l] += ufs[side] - ufc;",
+     "Fo[g->o_phi + g->void_l] -= ufs[side] - ufc;"),
+    ("gap_side_takes_own_mass_flux",
+     "        for (int k = 0; k < nf; ++k) Fo[k] = Fc[k];\n        for (int c = 0; c < g->nF; ++c)",
+     "        for (int k = 0; k < nf; ++k) Fo[k] = Fs[side][k];\n        for (int c = 0; c < g->nF; ++c)"),
+    ("void_stress_not_scaled",
+     "const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;",
+     "const double pm = ax->p;"),
 ]
 
 
@@ -65,10 +85,17 @@ def _build(name, old, new, tmp):
 
 
 def _check(lib):
-    r = subprocess.run([sys.executable, os.path.join(HERE, "pins_waves.py"), lib, "all"],
-                       capture_output=True, text=True, timeout=900,
-                       env=dict(os.environ, OMP_NUM_THREADS="2"))
-    return r.returncode, (r.stdout + r.stderr)[-400:]
+    # the void checks first (a second or so), then the shear, wall, 3D and
+    # totals checks
+    out = ""
+    for mod in ("pins_void.py", "pins_waves.py"):
+        r = subprocess.run([sys.executable, os.path.join(HERE, mod), lib, "all"],
+                           capture_output=True, text=True, timeout=900,
+                           env=dict(os.environ, OMP_NUM_THREADS="2"))
+        out = (r.stdout + r.stderr)[-400:]
+        if r.returncode != 0:
+            return r.returncode, out
+    return 0, out
 
 
 def test_every_planted_mistake_is_caught():
