@@ -206,6 +206,17 @@ int or_hencky(const double F[9], double devH[9], double lam[3], double Q[9]) {
 
 static int is_damaged(const or_material* m) { return m->damage != 0; }
 
+/* Critical damage (Sec. 3.1): D >= D_crit within 1e-4 (R34).  D comes back
+ * as the ratio (phi rho D) / (phi rho) of two transported quantities, so a
+ * cell the RK4 capped at D_crit reads below it after advection, by rounding
+ * (in FP32 storage about 1e-7 a step) or by a trace of undamaged material
+ * mixed in; the yield stress and the void-opening test both count a cell
+ * within the band as critical, and a cell diluted further as healed (the
+ * artificial healing of Sec. 3.1). */
+static int is_critical(const or_material* m, double D) {
+  return is_damaged(m) && D >= m->D_crit * (1.0 - 1e-4);
+}
+
 /* The void volume fraction nu (Sec. 2.1) is carried as a material of its
  * own (eos 2): its fraction is advected like the others, it has no mass, no
  * energy and no stress, and it takes no part in the pressure equilibrium of
@@ -311,8 +322,10 @@ static int w2u(const or_grid* g, const double* w, double* u, aux_t* ax) {
   if (mixture(g, phi, rho_l, Dl, ax->F, &mx) != 0) return -1;
   /* rho e = sum_l phi_l rho_l e_l with p = p_ref,l + rho_l Gamma_l (e_l - e_ref,l) */
   double rhoe = 0.0;
-  for (int l = 0; l < g->nmat; ++l)
+  for (int l = 0; l < g->nmat; ++l) {
+    if (is_void(&g->mat[l])) continue; /* no energy, no part in the closure */
     rhoe += arho[l] * mx.th[l][0] + phi[l] * (ax->p - mx.th[l][1]) / mx.th[l][4];
+  }
   const double ke = 0.5 * ax->rho *
                     (ax->u[0] * ax->u[0] + ax->u[1] * ax->u[1] + ax->u[2] * ax->u[2]);
   for (int l = 0; l + 1 < g->nmat; ++l) u[g->o_phi + l] = phi[l];
@@ -530,15 +543,14 @@ static void riemann_contact(const or_grid* g, int d, const double* UL, const aux
 /* two surfaces separate, the gap between them is void.                     */
 /* ------------------------------------------------------------------------ */
 
-/* A damaged solid at D >= D_crit (within 1e-6: D comes back as the ratio
- * (phi rho D) / (phi rho), so a capped cell can read one rounding below). */
+/* A damaged solid at critical damage (R34). */
 static int critical_state(const or_grid* g, const double* U) {
   for (int l = 0; l < g->nmat; ++l) {
     const int h = g->hslot[l];
     if (h < 0 || !is_damaged(&g->mat[l])) continue;
     const double arho = U[g->o_arho + l];
     if (!(arho > 0.0)) continue;
-    if (U[g->o_hist + 2 * h + 1] / arho >= g->mat[l].D_crit * (1.0 - 1e-6)) return 1;
+    if (is_critical(&g->mat[l], U[g->o_hist + 2 * h + 1] / arho)) return 1;
   }
   return 0;
 }
@@ -719,6 +731,13 @@ static int face_states(const or_grid* g, int d, double lam, const double* wm,
     wL[k] = wc[k] - 0.5 * s;
     wR[k] = wc[k] + 0.5 * s;
   }
+  /* the limited slope keeps a face value between the neighbours' values up
+   * to rounding; a void fraction next to a zero one can come out a rounding
+   * below zero, which is zero (R33) */
+  if (g->void_l >= 0) {
+    if (wL[g->o_phi + g->void_l] < 0.0) wL[g->o_phi + g->void_l] = 0.0;
+    if (wR[g->o_phi + g->void_l] < 0.0) wR[g->o_phi + g->void_l] = 0.0;
+  }
   double uL0[MAXF], uR0[MAXF];
   aux_t xL, xR;
   int ok = w2u(g, wL, uL0, &xL) == 0 && w2u(g, wR, uR0, &xR) == 0;
@@ -733,6 +752,12 @@ static int face_states(const or_grid* g, int d, double lam, const double* wm,
       const double inc = 0.5 * lam * ((FL[k] - FR[k]) + nc[k]);
       uL1[k] = uL0[k] + inc;
       uR1[k] = uR0[k] + inc;
+    }
+    /* the void fraction's trace transport can leave it a rounding below
+     * zero in the half step too: zero, as in the update (R33) */
+    if (g->void_l >= 0) {
+      if (uL1[g->o_phi + g->void_l] < 0.0) uL1[g->o_phi + g->void_l] = 0.0;
+      if (uR1[g->o_phi + g->void_l] < 0.0) uR1[g->o_phi + g->void_l] = 0.0;
     }
     ok = u2w(g, uL1, wL1, aL) == 0 && u2w(g, uR1, wR1, aR) == 0;
     if (ok && !(phase_density_in_bound(g, wL, wL1) && phase_density_in_bound(g, wR, wR1))) {
@@ -1130,7 +1155,7 @@ static double yield_mix(const or_material* mats, int nmat, const double* phi,
   for (int l = 0; l < nmat; ++l) {
     const or_material* m = &mats[l];
     if (m->plasticity != 1) continue;
-    if (is_damaged(m) && D[l] >= m->D_crit) continue;
+    if (is_critical(m, D[l])) continue;
     const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;
     /* advection can leave a rounding-level negative plastic strain; the
      * hardening law sees it as zero (R27) */
@@ -1566,9 +1591,8 @@ int or_totals(const or_grid* g, double* out) {
 /* phi_s > 1 - theta and no solid at D >= D_crit.  Fragments are the        */
 /* components of such cells under face adjacency (periodic faces wrap);     */
 /* a fragment's mass is the sum of dV (phi rho)_l over its cells and solid  */
-/* materials.  Labels: the smallest cell index of the component.  D comes   */
-/* back as (phi rho D) / (phi rho), so a cell capped at D_crit can read one  */
-/* rounding below it: critical means D >= D_crit (1 - 1e-6).                 */
+/* materials.  Labels: the smallest cell index of the component.  Critical  */
+/* means D >= D_crit (1 - 1e-4), as in the yield stress (R34).               */
 /* ------------------------------------------------------------------------ */
 
 static int in_fragment(const or_grid* g, double theta, long c) {
@@ -1583,8 +1607,7 @@ static int in_fragment(const or_grid* g, double theta, long c) {
     const int h = g->hslot[l];
     if (is_damaged(&g->mat[l]) && h >= 0) {
       const double arho = U[(size_t)(g->o_arho + l) * n + c];
-      const double D = U[(size_t)(g->o_hist + 2 * h + 1) * n + c] / arho;
-      if (D >= g->mat[l].D_crit * (1.0 - 1e-6)) return 0;
+      if (is_critical(&g->mat[l], U[(size_t)(g->o_hist + 2 * h + 1) * n + c] / arho)) return 0;
     }
   }
   return phis > 1.0 - theta;

@@ -291,3 +291,41 @@ def unembed_3d(case, c3, full, U3, src):
     for h in range(2 * lay.nhist):
         out[lay.o_hist + h] = Q[l3.o_hist + h]
     return out
+
+
+def cracked_block(dim, n, p=-2e8, vel=5.0, seed=0, with_void=True, bc=0):
+    """A CuBe block in hydrostatic tension p (negative) with one plane of
+    critically damaged cells (D = D_crit) across the middle of each axis (a
+    cross in 2D, three planes in 3D), so that void opens across faces of
+    every axis; a smooth seeded velocity perturbation of amplitude `vel`;
+    with `with_void` a void material (fraction 0, density 0) as material 0
+    before the CuBe.  Transmissive (bc=0) or periodic (bc=1) on every side."""
+    rng = np.random.default_rng(seed)
+    cube = W.cube("bonora")
+    mats = [W.void(), cube] if with_void else [cube]
+    L = 1e-3
+    n3 = [n if k < dim else 1 for k in range(3)]
+    hi = [L if k < dim else 1.0 for k in range(3)]
+    c = W.Case("cracked", dim, n3, [0, 0, 0], hi, [bc] * (2 * dim), mats, None, cfl=0.6)
+    lay = c.layout
+    c.prim = W.blank_prim(lay, c.ncell)
+    cen = c.centres()
+    k = 1 if with_void else 0
+    if with_void:
+        c.prim[lay.o_phi] = 0.0
+        c.prim[lay.o_rho] = 0.0
+    c.prim[lay.o_rho + k] = cube["rho0"]
+    kk = 2 * np.pi / L
+    a = rng.uniform(0.0, 2 * np.pi, 2 * dim)
+    for d in range(dim):
+        other = cen[(d + 1) % dim]
+        c.prim[lay.o_u + d] = vel * np.sin(kk * cen[d] + a[d]) * np.cos(kk * other + a[dim + d])
+    c.prim[lay.o_p] = p
+    crack = np.zeros(c.ncell, dtype=bool)
+    dx = L / n
+    for d in range(dim):
+        crack |= np.abs(cen[d] - (0.5 * L + 0.5 * dx)) < 0.5 * dx
+    c.prim[lay.o_hist + 1] = np.where(crack, cube["D_crit"], 0.0)
+    for d in range(dim):
+        c.prim[lay.o_X + d] = cen[d]
+    return c

@@ -164,19 +164,60 @@ def check_no_opening_without_critical_damage(lib=None):
     _same_as_without_void(c1, c2, 80, lib)
 
 
+def check_opening_at_capped_damage(lib=None):
+    """A crack at D = D_crit (1 - 1e-5), as a capped D reads back after
+    advection, is critical (R34): the void opens as at D = D_crit (opened
+    volume within 1e-4 after 40 steps; the damaged cell's moduli differ by
+    (1 - D) between the two)."""
+    gaps = []
+    for D in (CUBE["D_crit"], CUBE["D_crit"] * (1 - 1e-5)):
+        c = bar()
+        c.prim[c.layout.o_hist + 1][N // 2] = D
+        g = OracleGrid(c, lib=lib)
+        g.step(40)
+        gaps.append(g.read()[c.layout.o_phi].sum())
+    assert gaps[0] > 0.01 and abs(gaps[1] / gaps[0] - 1) < 1e-4, gaps
+
+
+def porous_bar(nu=0.5, p=1e8):
+    """The bar without a crack: CuBe at pressure p on the left half, the same
+    CuBe with void fraction nu at p / (1 - nu) on the right half."""
+    c = bar(p=p, crack=())
+    lay = c.layout
+    right = c.centres()[0] > L / 2
+    c.prim[lay.o_phi] = np.where(right, nu, 0.0)
+    c.prim[lay.o_p] = np.where(right, p / (1 - nu), p)
+    return c
+
+
+def check_porous_stress_equilibrium(lib=None):
+    """The void carries no stress (R33: the mixture's pressure is (1 - nu) p):
+    the CuBe at p = 1e8 Pa beside the same CuBe with void fraction 0.5 at
+    p = 2e8 Pa, at rest and unsheared, has the same normal stress on both
+    sides, so it stays at rest (|u| below 1e-9 of p / (rho0 c_L) after 50
+    steps) and the porosity jump stays where it is."""
+    c = porous_bar()
+    lay = c.layout
+    g = OracleGrid(c, lib=lib)
+    g.step(50)
+    w = g.read()
+    assert np.abs(w[lay.o_u]).max() < 1e-9 * 1e8 / (CUBE["rho0"] * CL), np.abs(w[lay.o_u]).max()
+    assert np.array_equal(w[lay.o_phi], c.prim[lay.o_phi])
+
+
 def check_void_opening_mirror(lib=None):
     """An off-centre crack in a bar in tension with a smooth velocity
     perturbation, mirrored about the mid-plane, runs into the mirror image
-    of its own run (1e-11 of each field's scale)."""
+    of its own run over 100 steps (1e-11 of each field's scale): the
+    decisions of the void opening (critical damage, tension, the clamps of
+    a void fraction a rounding below zero) take the same branch on both."""
     pert = lambda x: 5.0 * np.sin(2 * np.pi * x / L)
     c = bar(crack=(N // 2 + 37,), u=pert)
     m = bar(crack=(N - 1 - (N // 2 + 37),), u=lambda x: -pert(L - x))
     m.prim[m.layout.o_X] = c.centres()[0]
-    # (20 steps: later, at the opened surfaces the stress is near zero and
-    # the tension test flips on rounding-level differences)
     g1, g2 = OracleGrid(c, lib=lib), OracleGrid(m, lib=lib)
-    g1.step(20)
-    g2.step(20)
+    g1.step(100)
+    g2.step(100)
     a, b = g1.read(False), g2.read(False)
     lay = c.layout
     back = b[:, ::-1].copy()
@@ -210,6 +251,8 @@ CHECKS = {
     "no_opening_in_compression": check_no_opening_in_compression,
     "no_opening_without_critical_damage": check_no_opening_without_critical_damage,
     "release_from_a_crack": check_release_from_a_crack,
+    "opening_at_capped_damage": check_opening_at_capped_damage,
+    "porous_stress_equilibrium": check_porous_stress_equilibrium,
     "void_opening_mirror": check_void_opening_mirror,
     "void_opening_galilean": check_void_opening_galilean,
 }

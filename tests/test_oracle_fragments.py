@@ -15,11 +15,11 @@ from paper_2210_04037_gb300 import workloads as W
 
 def members_from_prim(case, theta):
     """Membership written out from the primitive fields the case was made
-    from (solid = material 0; critical = D >= D_crit within 1e-6)."""
+    from (solid = material 0; critical = D >= D_crit within 1e-4)."""
     lay = case.layout
     phi = case.prim[lay.o_phi]
     Dc = case.materials[0]["D_crit"]
-    crit = case.prim[lay.o_hist + 1] >= Dc * (1.0 - 1e-6)
+    crit = case.prim[lay.o_hist + 1] >= Dc * (1.0 - 1e-4)
     return (phi > 1.0 - theta) & ~crit
 
 

@@ -58,8 +58,11 @@ MUTANTS = [
      "aL->sig[3 * d + d] + aR->sig[3 * d + d] > 0.0) {",
      "aL->sig[3 * d + d] + aR->sig[3 * d + d] < 0.0) {"),
     ("void_opens_without_critical_damage",
-     "if (U[g->o_hist + 2 * h + 1] / arho >= g->mat[l].D_crit * (1.0 - 1e-6)) return 1;",
-     "if (U[g->o_hist + 2 * h + 1] / arho >= 0.9 * g->mat[l].D_crit) return 1;"),
+     "return is_damaged(m) && D >= m->D_crit * (1.0 - 1e-4);",
+     "return is_damaged(m) && D >= 0.9 * m->D_crit;"),
+    ("critical_damage_without_rounding_margin",
+     "return is_damaged(m) && D >= m->D_crit * (1.0 - 1e-4);",
+     "return is_damaged(m) && D >= m->D_crit;"),
     ("free_surface_speed_sign",
      "return a->u[d] + a->sig[3 * d + d] / (a->rho * (SK - a->u[d]));",
      "return a->u[d] - a->sig[3 * d + d] / (a->rho * (SK - a->u[d]));"),
@@ -69,6 +72,9 @@ MUTANTS = [
     ("gap_side_takes_own_mass_flux",
      "        for (int k = 0; k < nf; ++k) Fo[k] = Fc[k];\n        for (int c = 0; c < g->nF; ++c)",
      "        for (int k = 0; k < nf; ++k) Fo[k] = Fs[side][k];\n        for (int c = 0; c < g->nF; ++c)"),
+    ("void_energy_in_closure",
+     "    if (is_void(&g->mat[l])) continue; /* no energy, no part in the closure */\n",
+     ""),
     ("void_stress_not_scaled",
      "const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;",
      "const double pm = ax->p;"),

@@ -186,8 +186,20 @@ def test_elastic_state_is_unchanged_and_critical_damage_removes_strength():
     assert de == 0.0 and np.allclose(Fn, F, rtol=0, atol=1e-16)
     # D >= D_crit: zero yield stress, the return removes all deviatoric strain
     F[0, 1] = 3e-2
+    F0 = F.copy()
     Fn, de = _return([m], [1.0], [m["rho0"]], [0.0], [m["D_crit"]], 1.0, 1e-9, F)
     assert _seq(Fn, m["G0"]) < 1e-6 * m["c1"]
+    # a capped D read back a rounding below D_crit is still critical (R34),
+    # while D_crit (1 - 1e-3) keeps the strength (1 - D) c1 of Sec. 2.1.1
+    # (dt = 1 s floors the rate factor at 1; the return overwrites F, so
+    # each call takes a copy)
+    Dlow = np.nextafter(m["D_crit"], 0.0)
+    Fn, de = _return([m], [1.0], [m["rho0"]], [0.0], [Dlow], 1.0, 1.0, F0.copy())
+    assert de > 0 and _seq(Fn, m["G0"]) < 1e-6 * m["c1"]
+    Dout = m["D_crit"] * (1 - 1e-3)
+    G = (1 - Dout) * m["G0"]
+    Fn, de = _return([m], [1.0], [m["rho0"]], [0.0], [Dout], 1.0, 1.0, F0.copy())
+    assert de > 0 and _seq(Fn, G) == pytest.approx((1 - Dout) * m["c1"], rel=1e-9)
 
 
 def test_rate_dependent_return_satisfies_yield_condition():
