@@ -51,14 +51,15 @@ typedef enum {
 
 enum { MM_BC_TRANSMISSIVE = 0, MM_BC_PERIODIC = 1, MM_BC_REFLECTIVE = 2 };
 enum { MM_FP64 = 0, MM_FP32_SPLIT = 1 };
-enum { MM_EOS_IDEAL_GAS = 0, MM_EOS_ROMENSKII = 1 };
+enum { MM_EOS_IDEAL_GAS = 0, MM_EOS_ROMENSKII = 1, MM_EOS_VOID = 2 };
 enum { MM_PL_NONE = 0, MM_PL_JOHNSON_COOK = 1 };
 enum { MM_DMG_NONE = 0, MM_DMG_BONORA = 1, MM_DMG_SIMPLE = 2 };
 
 /* Grid: dim in {1,2,3}; n[k] cells on [lo[k], hi[k]] for k < dim (n[k] >= 2);
  * bc[k][side] one of MM_BC_*; precision MM_FP64 (every step in FP64) or
  * MM_FP32_SPLIT (reconstruction and fluxes in FP32, total energy, energy
- * recovery, plastic return iteration and totals in FP64); n_materials 1..2. */
+ * recovery, plastic return iteration and totals in FP64); n_materials 1..2,
+ * or 3 when one of them is void (MM_EOS_VOID). */
 typedef struct {
   int dim;
   int64_t n[3];
@@ -70,7 +71,17 @@ typedef struct {
 
 /* Material (Sec. 2.1.1-2.1.2 and the parameter tables): Romenskii cold
  * energy K0, rho0, alpha; shear modulus G0 (rho/rho0)^(beta+1); Grueneisen
- * Gamma0; ideal gas gamma_gas.  Johnson-Cook yield (c1 + c2 eps^n_hard)
+ * Gamma0; ideal gas gamma_gas.  MM_EOS_VOID: the void volume fraction nu of
+ * Sec. 2.1 as a material of its own (no mass, energy or stress; its
+ * primitive density field is 0; other parameters unused): at most one, not
+ * the last material, with no plasticity or damage model, beside exactly one
+ * plastic material; its fraction may be 0.  Where either face state is
+ * critically damaged (D >= D_crit (1 - 1e-4), the threshold at which the
+ * yield stress is zero too) and the two are in tension
+ * along the sweep, x^T (sigma_L + sigma_R) x > 0, such a grid opens void
+ * (Sec. 3.1): each side meets a traction-free surface and the gap between
+ * them becomes void.  Grids with void run on single grids only (not in
+ * batches or on the server).  Johnson-Cook yield (c1 + c2 eps^n_hard)
  * max(1, 1 + c3 ln(epsdot/edot0)).  Damage: Bonora (D_crit, eps_t = the
  * threshold strain, eps_c = the critical strain, alpha_D, poisson) or the
  * simple law Ddot = Ddot0 (1-D) epsdot (Sec. 4.3).  SI units. */
@@ -155,12 +166,14 @@ mm_status mm_set_x_transport(mm_grid* g, int scheme);
 
 /* Fragments of the present state (Sec. 4.2, 4.3 demarcate fragments by the
  * contour nu = theta of the void volume fraction, theta = 0.25, 0.5, 0.75,
- * and report fragment masses).  This model carries gas in place of void and
- * a crack is critically damaged solid (Sec. 3.1), so a cell belongs to a
- * fragment when the summed volume fraction of its solid (Romenskii)
- * materials exceeds 1 - theta and no damaged solid in it has
- * D >= D_crit (1 - 1e-6) (D comes back as (phi rho D)/(phi rho), one rounding
- * below a cap at D_crit).  Fragments are the components of such cells under
+ * and report fragment masses).  A crack is critically damaged solid
+ * (Sec. 3.1) and the space around the pieces holds gas, or void on grids
+ * with a void material, so a cell belongs to a fragment when the summed
+ * volume fraction of its solid (Romenskii) materials exceeds 1 - theta
+ * (on a grid of solid and void alone: nu < theta) and no damaged solid in
+ * it has D >= D_crit (1 - 1e-4), the threshold of the yield stress (D comes
+ * back as (phi rho D)/(phi rho), below a cap at D_crit by rounding or a
+ * trace mixed in).  Fragments are the components of such cells under
  * face adjacency; periodic faces wrap.  A fragment's label is its smallest
  * linear cell index (x fastest), its mass sum dV (phi rho) over its cells
  * and solids (FP64; summed in no fixed order).

@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "libmmfrac.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {"mm_api.cu": [], "mm_noalloc.cu": [], "mm_server.cu": [], "mm_frag.cu": []}
 for _d in (1, 2, 3):
-    for _b in ("", "_batch"):
+    for _b in ("", "_batch", "_void"):
         UNITS[f"mm_fp64_d{_d}{_b}.cu"] = ["--fmad=false"]
         UNITS[f"mm_fp32_d{_d}{_b}.cu"] = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
 

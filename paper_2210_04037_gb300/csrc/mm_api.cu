@@ -134,10 +134,12 @@ cudaError_t go(mm_grid* g, int what, int axis, int flag, const KArgs& a, double*
                int nblocks = 0) {
   g->launches += (what == 5) ? 2 : 1;
   typedef cudaError_t (*launcher)(int, int, int, const KArgs&, double*, int, cudaStream_t);
-  static const launcher table[2][3] = {{mm_p64_d1, mm_p64_d2, mm_p64_d3},
-                                       {mm_p32_d1, mm_p32_d2, mm_p32_d3}};
-  return table[g->prec == MM_FP64 ? 0 : 1][g->dim - 1](what, axis, flag, a, out, nblocks,
-                                                        g->stream);
+  static const launcher table[2][2][3] = {
+      {{mm_p64_d1, mm_p64_d2, mm_p64_d3}, {mm_p32_d1, mm_p32_d2, mm_p32_d3}},
+      {{mm_p64_d1_void, mm_p64_d2_void, mm_p64_d3_void},
+       {mm_p32_d1_void, mm_p32_d2_void, mm_p32_d3_void}}};
+  return table[a.void_l >= 0 ? 1 : 0][g->prec == MM_FP64 ? 0 : 1][g->dim - 1](
+      what, axis, flag, a, out, nblocks, g->stream);
 }
 
 mm_status check_device_error(mm_grid* g, const char* where) {
@@ -262,6 +264,7 @@ mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** 
   cudaMemsetAsync(g->err, 0, sizeof(DevErr), g->stream);
   KArgs& a = g->base;
   memset(&a, 0, sizeof a);
+  a.void_l = -1;
   a.dim = g->dim;
   a.nmat = g->nmat;
   a.ncell = ncell;
@@ -285,14 +288,21 @@ mm_status mm_create_grid(const mm_grid_desc* desc, void* cuda_stream, mm_grid** 
 mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_init* init) {
   if (!g || !mats || !init || !init->prim) return fail(MM_EINVAL, "mm_set_materials: null argument");
   if (n != g->nmat) return fail(MM_EINVAL, "expected %d materials, got %d", g->nmat, n);
-  int nhist = 0;
-  int hslot[MM_MAXMAT] = {-1, -1};
+  int nhist = 0, void_l = -1;
+  int hslot[MM_MAXMAT] = {-1, -1, -1};
   MatK mk[MM_MAXMAT];
   memset(mk, 0, sizeof mk);
   for (int l = 0; l < n; ++l) {
     const mm_material& m = mats[l];
-    if (m.eos != MM_EOS_IDEAL_GAS && m.eos != MM_EOS_ROMENSKII)
+    if (m.eos != MM_EOS_IDEAL_GAS && m.eos != MM_EOS_ROMENSKII && m.eos != MM_EOS_VOID)
       return fail(MM_EINVAL, "material %d: unknown eos", l);
+    if (m.eos == MM_EOS_VOID) {
+      if (void_l >= 0 || l == n - 1 || m.plasticity != MM_PL_NONE || m.damage != MM_DMG_NONE)
+        return fail(MM_EINVAL,
+                    "material %d: one void at most, not the last material, without plasticity "
+                    "or damage", l);
+      void_l = l;
+    }
     if (m.eos == MM_EOS_IDEAL_GAS && !(m.gamma_gas > 1.0))
       return fail(MM_EINVAL, "material %d: gamma_gas must exceed 1", l);
     if (m.eos == MM_EOS_ROMENSKII &&
@@ -329,13 +339,16 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     k.n_hard = m.n_hard;
     k.edot0 = m.edot0;
     k.D_crit = m.D_crit;
+    k.D_cut = m.D_crit * (1.0 - 1e-4);
     k.eps_t = m.eps_t;
     k.eps_c = m.eps_c;
     k.alpha_D = m.alpha_D;
     k.poisson = m.poisson;
     k.Ddot0 = m.Ddot0;
-    k.Gamma = m.eos == MM_EOS_IDEAL_GAS ? m.gamma_gas - 1.0 : m.Gamma0;
-    k.xi = 1.0 / k.Gamma;
+    k.Gamma = m.eos == MM_EOS_IDEAL_GAS ? m.gamma_gas - 1.0
+              : m.eos == MM_EOS_VOID     ? 1.0
+                                         : m.Gamma0;
+    k.xi = m.eos == MM_EOS_VOID ? 0.0 : 1.0 / k.Gamma;
     if (m.damage == MM_DMG_BONORA) {
       k.bon_k = m.alpha_D * pow(m.D_crit, 1.0 / m.alpha_D) / log(m.eps_c / m.eps_t);
       k.bon_ec2n = pow(m.eps_c, 2.0 * m.n_hard);
@@ -344,6 +357,10 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     if (m.plasticity == MM_PL_JOHNSON_COOK) hslot[l] = nhist++;
   }
   if (nhist > 1) return fail(MM_EINVAL, "at most one plastic material is supported");
+  if (void_l >= 0 && nhist != 1)
+    return fail(MM_EINVAL, "a grid with void needs exactly one plastic material");
+  if (n == 3 && void_l < 0)
+    return fail(MM_EINVAL, "three materials are supported with one of them void");
   const int nF = g->dim == 1 ? 3 : (g->dim == 2 ? 5 : 9);
   const int nfield = (g->nmat - 1) + g->nmat + g->dim + 1 + nF + 2 * nhist + g->dim;
   if (init->phi0) {
@@ -381,6 +398,7 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   KArgs& a = g->base;
   a.nhist = nhist;
   a.nfield = nfield;
+  a.void_l = void_l;
   for (int l = 0; l < MM_MAXMAT; ++l) {
     const MatK& k = mk[l];
     a.mat[l] = k;
@@ -403,6 +421,7 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     f.n_hard = float(k.n_hard);
     f.edot0 = float(k.edot0);
     f.D_crit = float(k.D_crit);
+    f.D_cut = float(k.D_cut);
     f.eps_t = float(k.eps_t);
     f.eps_c = float(k.eps_c);
     f.alpha_D = float(k.alpha_D);
@@ -717,8 +736,8 @@ mm_status mm_fragments(mm_grid* g, double theta, int64_t* labels, size_t labels_
   a.fdV = 1.0;
   for (int k = 0; k < g->dim; ++k) a.fdV *= a.dx[k];
   for (int l = 0; l < MM_MAXMAT; ++l) {
-    a.fdcrit[l] = l < g->nmat ? a.mat[l].D_crit * (1.0 - 1e-6) : 0.0;
-    a.fdcritf[l] = (float)a.fdcrit[l];
+    a.fdcrit[l] = l < g->nmat ? a.mat[l].D_cut : 0.0;
+    a.fdcritf[l] = l < g->nmat ? a.matf[l].D_cut : 0.0f;
   }
   a.fpad = 0.0f;
   prof_begin(g, MM_K_FRAG_MARK);
@@ -970,6 +989,9 @@ mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_ba
   }
   if (g0->nmat != 2)
     return fail(MM_EINVAL, "mm_batch_create: batches are built for two materials");
+  for (int i = 0; i < n; ++i)
+    if (grids[i]->base.void_l >= 0)
+      return fail(MM_EINVAL, "mm_batch_create: member %d holds void; void grids run alone", i);
   for (int i = 0; i < n; ++i)
     if (grids[i]->xscheme != MM_X_SWEEP)
       return fail(MM_EINVAL, "mm_batch_create: member %d transports X by WENO3 + RK3; batches "

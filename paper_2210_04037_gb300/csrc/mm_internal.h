@@ -7,7 +7,7 @@
 
 #include "mmfrac.h"
 
-#define MM_MAXMAT 2
+#define MM_MAXMAT 3
 
 // Material constants as the kernels use them (copied from mm_material, plus
 // derived values computed once on the host).
@@ -21,6 +21,11 @@ struct MatK {
   // Bonora constants: alpha_D D_c^(1/alpha_D) / ln(eps_c/eps_t), and
   // eps_c^(2n), eps_t^(2n) of the threshold law (n the hardening exponent)
   double bon_k, bon_ec2n, bon_et2n;
+  // critical damage threshold D_crit (1 - 1e-4): D comes back as the ratio
+  // (phi rho D) / (phi rho) of two transported quantities, so a capped
+  // state reads below D_crit by rounding (FP32 storage: about 1e-7 a step)
+  // or by a trace of undamaged material mixed in
+  double D_cut;
 };
 
 // The same constants in FP32 for the FP32-split kernels, which read them as
@@ -37,6 +42,7 @@ struct MatKf {
   float K0_2a2;    // K0 / (2 alpha^2)
   float K0_arho0;  // K0 / (alpha rho0)
   float c2n;       // c2 n_hard
+  float D_cut;     // the FP64 threshold rounded to FP32
 };
 
 // First failure seen on the device (sticky until the host clears it).
@@ -87,6 +93,8 @@ struct KArgs {
   double dx[3], lo[3], hi[3];
   int bc[3][2];
   int hslot[MM_MAXMAT];
+  int void_l;          // index of the void material (eos 2), or -1
+  int pad_void;
   MatK mat[MM_MAXMAT];
   MatKf matf[MM_MAXMAT];
   const void* Uin;     // conserved fields [nfield][ncell] (double or float)
@@ -107,7 +115,7 @@ struct KArgs {
   double* fmass;       // fragment labelling: per-cell solid mass dV sum (phi rho)_solid
   double fcut;         // fragment labelling: void cut-off theta
   // fragment labelling constants of the launch (set on the host): 1 - theta,
-  // the largest float not above it, D_crit (1 - 1e-6) per material in FP64
+  // the largest float not above it, D_crit (1 - 1e-4) per material in FP64
   // and FP32, the cell volume
   double fthr, fdV;
   double fdcrit[MM_MAXMAT];
@@ -163,6 +171,14 @@ MM_DECLARE_LAUNCHER(mm_p64_d3)
 MM_DECLARE_LAUNCHER(mm_p32_d1)
 MM_DECLARE_LAUNCHER(mm_p32_d2)
 MM_DECLARE_LAUNCHER(mm_p32_d3)
+// grids with a void material (mm_fp{64,32}_d{1,2,3}_void.cu): two or three
+// materials, one of them plastic
+MM_DECLARE_LAUNCHER(mm_p64_d1_void)
+MM_DECLARE_LAUNCHER(mm_p64_d2_void)
+MM_DECLARE_LAUNCHER(mm_p64_d3_void)
+MM_DECLARE_LAUNCHER(mm_p32_d1_void)
+MM_DECLARE_LAUNCHER(mm_p32_d2_void)
+MM_DECLARE_LAUNCHER(mm_p32_d3_void)
 #undef MM_DECLARE_LAUNCHER
 
 // Batched launchers (mm_fp{64,32}_d{1,2,3}_batch.cu): what 0 CFL, 1 sweep

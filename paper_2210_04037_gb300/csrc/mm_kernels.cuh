@@ -224,6 +224,9 @@ template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 
 // (the cell arithmetic does not depend on the tile, so either gives the same
 // bits): longer tiles along the sweep, narrower across it.
 template <class P, int DIM, int AX> struct Tile<P, DIM, AX, 1> : Tile<P, DIM, AX, 0> {};
+// grids that can open void take the single-grid tiles of their precision
+template <int DIM, int AX> struct Tile<P64V, DIM, AX, 0> : Tile<P64, DIM, AX, 0> {};
+template <int DIM, int AX> struct Tile<P32V, DIM, AX, 0> : Tile<P32, DIM, AX, 0> {};
 template <> struct Tile<P32, 1, 0, 1> { static constexpr int TL = 60, TW = 1, NT = 64; };
 template <> struct Tile<P32, 2, 0, 1> { static constexpr int TL = 60, TW = 2, NT = 128; };
 template <> struct Tile<P32, 2, 1, 1> { static constexpr int TL = 28, TW = 4, NT = 128; };
@@ -240,8 +243,11 @@ struct SweepShape {
   static constexpr int C1 = NF + AuxRec<P>::N, C2 = NF + AuxRec<P>::N, C3 = NF + 4;
   static constexpr int N1 = (TL + 4) * TW, N2 = (TL + 2) * TW, N3 = (TL + 1) * TW, N4 = TL * TW;
   static constexpr int NX = Phys<P, DIM, NMAT, NH>::NX;
-  static constexpr size_t smem = sizeof(typename P::X) * NX * (size_t(N1) + 2 * size_t(N2) + size_t(N3)) +
-                                 sizeof(R) * (size_t(N1) * C1 + 2 * size_t(N2) * C2 + size_t(N3) * C3);
+  // face records per face: one, or (grids that can open void) the record
+  // the cell left of the face takes and the one the cell right of it takes
+  static constexpr int NR = Voidable<P>::value ? 2 : 1;
+  static constexpr size_t smem = sizeof(typename P::X) * NX * (size_t(N1) + 2 * size_t(N2) + NR * size_t(N3)) +
+                                 sizeof(R) * (size_t(N1) * C1 + 2 * size_t(N2) * C2 + NR * size_t(N3) * C3);
   __device__ static __forceinline__ int idx(int p, int w, int len) {
     return AX == 0 ? w * len + p : p * TW + w;
   }
@@ -284,13 +290,13 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
   typedef SweepShape<P, DIM, NMAT, NH, AX, V> SH;
   typedef typename P::X XT;
   constexpr int NF = L::NF, NX = SH::NX, TL = SH::TL, TW = SH::TW, NT = SH::NT;
-  constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3;
+  constexpr int C1 = SH::C1, C2 = SH::C2, C3 = SH::C3, NR = SH::NR;
   constexpr int N1 = SH::N1, N2 = SH::N2, N3 = SH::N3, N4 = SH::N4;
   constexpr int TD = (AX == 0) ? 1 : 0;
   XT* x1 = reinterpret_cast<XT*>(smem);  // N1 * NX
   XT* x2 = x1 + N1 * NX;                  // 2 * N2 * NX
-  XT* x3 = x2 + 2 * N2 * NX;              // N3 * NX
-  R* r1 = reinterpret_cast<R*>(x3 + N3 * NX);
+  XT* x3 = x2 + 2 * N2 * NX;              // NR * N3 * NX
+  R* r1 = reinterpret_cast<R*>(x3 + NR * N3 * NX);
   R* r2 = r1 + N1 * C1;
   R* r3 = r2 + 2 * N2 * C2;
 
@@ -460,6 +466,13 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
           for (int k = 0; k < NF; ++k) wv[k] = wc[k] + hs * sl[k];
 #pragma unroll
           for (int k = 0; k < NX; ++k) wxv[k] = xc[k] + XT(hs) * slx[k];
+          if constexpr (NR == 2) {
+            // the limited slope keeps a face value between the neighbours'
+            // up to rounding: a void fraction a rounding below zero is zero
+#pragma unroll
+            for (int l = 0; l < PH::NPX; ++l)
+              if (l == a.void_l && wxv[1 + l] < XT(0)) wxv[1 + l] = XT(0);
+          }
           Aux<R> xs;
           if (!PH::template w2u<AX>(a, wv, wxv, cs, cxs, xs)) {
             good = false;
@@ -494,6 +507,12 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
             for (int k = 0; k < NF; ++k) cs[k] = q[k] + R(0.5) * lam * (dfl[k] + nc[k]);
 #pragma unroll
             for (int k = 0; k < NX; ++k) cxs[k] = qx[k] + XT(0.5) * XT(lam) * (dfx[k] + ncx[k]);
+            if constexpr (NR == 2) {
+              // a void fraction a rounding below zero is zero, as in the update
+#pragma unroll
+              for (int l = 0; l < PH::NPX; ++l)
+                if (l == a.void_l && cxs[1 + l] < XT(0)) cxs[1 + l] = XT(0);
+            }
             Aux<R> xs;
             if (!PH::template u2w<AX>(a, cs, cxs, tmp, tmpx, xs)) {
               good = false;
@@ -567,9 +586,22 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       }
       R fo[NF], row[3], uf;
       XT fox[NX];
-      PH::template riemann<AX>(ql, x2 + (2 * il + 1) * NX, xl, qr, x2 + (2 * ir) * NX, xr, fo,
-                               fox, uf, row);
-      R* q3 = r3 + it * C3;
+      if constexpr (NR == 2) {
+        // the record the right cell takes goes to slot 1 first, then the
+        // left cell's to slot 0
+        R* q3 = r3 + (2 * it + 1) * C3;
+        R uf1, row1[3];
+        PH::template riemann2<AX>(a, ql, x2 + (2 * il + 1) * NX, xl, qr, x2 + (2 * ir) * NX, xr,
+                                  fo, fox, uf, row, q3, x3 + (2 * it + 1) * NX, uf1, row1);
+        q3[NF] = uf1;
+        q3[NF + 1] = row1[0];
+        q3[NF + 2] = row1[1];
+        q3[NF + 3] = row1[2];
+      } else {
+        PH::template riemann<AX>(ql, x2 + (2 * il + 1) * NX, xl, qr, x2 + (2 * ir) * NX, xr, fo,
+                                 fox, uf, row);
+      }
+      R* q3 = r3 + NR * it * C3;
 #pragma unroll
       for (int k = 0; k < NF; ++k) q3[k] = fo[k];
       q3[NF] = uf;
@@ -577,7 +609,7 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       q3[NF + 2] = row[1];
       q3[NF + 3] = row[2];
 #pragma unroll
-      for (int k = 0; k < NX; ++k) x3[it * NX + k] = fox[k];
+      for (int k = 0; k < NX; ++k) x3[NR * it * NX + k] = fox[k];
     }
   }
   __syncthreads();
@@ -597,8 +629,12 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
       const R* wc = r1 + ic * C1;
       const XT* xc = x1 + ic * NX;
-      const R* ql = r3 + fl * C3;
-      const R* qr = r3 + fr * C3;
+      // the left face's record as a right cell takes it, the right face's as
+      // a left cell does (one record each where the void cannot open)
+      const R* ql = r3 + (NR * fl + NR - 1) * C3;
+      const R* qr = r3 + NR * fr * C3;
+      const XT* xql = x3 + (NR * fl + NR - 1) * NX;
+      const XT* xqr = x3 + NR * fr * NX;
       R uc[3], dF[3], nc[NF];
       XT ncx[NX];
 #pragma unroll
@@ -609,12 +645,18 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
 #pragma unroll
       for (int k = 0; k < NF; ++k) c[k] = c[k] + lam * ((ql[k] - qr[k]) + nc[k]);
 #pragma unroll
-      for (int k = 1; k < NX; ++k)
-        cx[k] = cx[k] + XT(lam) * ((x3[fl * NX + k] - x3[fr * NX + k]) + ncx[k]);
+      for (int k = 1; k < NX; ++k) cx[k] = cx[k] + XT(lam) * ((xql[k] - xqr[k]) + ncx[k]);
+      if constexpr (NR == 2) {
+        // the void fraction is created only where the void opens; its
+        // transport of traces can leave it a rounding below zero: zero
+#pragma unroll
+        for (int l = 0; l < PH::NPX; ++l)
+          if (l == a.void_l && cx[1 + l] < XT(0)) cx[1 + l] = XT(0);
+      }
       // total energy updated in FP64 (the stored state)
       // (the face fluxes differenced in FP64 telescope exactly over the
       // cells, which keeps the total energy conserved to FP64 rounding)
-      eE = eE + double(lam) * ((double(x3[fl * NX]) - double(x3[fr * NX])) + double(ncx[0]));
+      eE = eE + double(lam) * ((double(xql[0]) - double(xqr[0])) + double(ncx[0]));
       store_cell<P, DIM, NMAT, NH>(a, idx, c, cx, eE);
     }
   }
@@ -637,8 +679,8 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
         ok2[d] = ok2[sidx];
       } else {
         const int d = SH::idx(0, w, TL + 1), sidx = SH::idx(TL, w, TL + 1);
-        for (int k = 0; k < C3; ++k) r3[d * C3 + k] = r3[sidx * C3 + k];
-        for (int k = 0; k < NX; ++k) x3[d * NX + k] = x3[sidx * NX + k];
+        for (int k = 0; k < NR * C3; ++k) r3[NR * d * C3 + k] = r3[NR * sidx * C3 + k];
+        for (int k = 0; k < NR * NX; ++k) x3[NR * d * NX + k] = x3[NR * sidx * NX + k];
       }
     }
     __syncthreads();
@@ -776,7 +818,8 @@ __device__ __forceinline__ T lookup(const KArgs& a, const T X[3]) {
 }
 
 // Mixture yield stress sum_l phi_l phi (1-D_l) sigma_Y,l (Johnson-Cook, rate
-// factor floored at 1, zero at critical damage) and its derivative in dl.
+// factor floored at 1, zero at critical damage D >= D_cut) and its
+// derivative in dl.
 // The Johnson-Cook powers and logarithm are evaluated in T (FP64 on the FP64
 // path, FP32 on the split path); the sums are FP64.
 template <int NMAT, class T>
@@ -788,7 +831,9 @@ __device__ __forceinline__ double yield_mix(const KArgs& a, const double* phi, c
   for (int l = 0; l < NMAT; ++l) {
     const MatK& m = a.mat[l];
     if (m.plasticity != 1) continue;
-    if (m.damage != 0 && D[l] >= m.D_crit) continue;
+    // critical damage at the threshold in the path's precision
+    const double dcut = sizeof(T) == sizeof(float) ? double(a.matf[l].D_cut) : m.D_cut;
+    if (m.damage != 0 && D[l] >= dcut) continue;
     const double psi = m.damage != 0 ? 1.0 - D[l] : 1.0;
     const double e = (eps[l] > 0.0 ? eps[l] : 0.0) + dl;
     double hard = m.c1, dhard = 0.0;
@@ -824,7 +869,7 @@ __device__ __forceinline__ float yield_mix_f32(const KArgs& a, const float* phi,
   for (int l = 0; l < NMAT; ++l) {
     const MatKf& m = a.matf[l];
     if (m.plasticity != 1) continue;
-    if (m.damage != 0 && D[l] >= m.D_crit) continue;
+    if (m.damage != 0 && D[l] >= m.D_cut) continue;
     const float psi = m.damage != 0 ? 1.f - D[l] : 1.f;
     const float e = (eps[l] > 0.f ? eps[l] : 0.f) + dl;
     float hard = m.c1, dhard = 0.f;
@@ -1249,7 +1294,7 @@ __device__ __forceinline__ void sources_cells(
 #pragma unroll
         for (int l = 0; l < NMAT; ++l) {
           const auto& m = matp<R>(a, l);
-          if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_crit))) continue;
+          if (m.plasticity != 1 || (m.damage != 0 && Dr[l] >= R(m.D_cut))) continue;
           const R e = Er[l] > R(0) ? Er[l] : R(0);
           R hard = R(m.c1);
           if (m.c2 != 0) hard += R(m.c2) * mpow(e, R(m.n_hard));
@@ -1710,8 +1755,8 @@ __global__ void __launch_bounds__(256) k_totals(KArgs a) {
 // Marks the cells of fragments at void cut-off a.fcut (Sec. 4.2, 4.3
 // demarcate fragments by a contour of the void fraction; in this gas-filled
 // model a cell is in a fragment when its solid fraction exceeds 1 - theta
-// and no solid in it is critically damaged, D >= D_crit within 1e-6 because
-// D comes back as (phi rho D) / (phi rho)): a.frag[cell] = cell there and
+// and no solid in it is critically damaged, D >= D_crit (1 - 1e-4) as in
+// the yield stress): a.frag[cell] = cell there and
 // -1 elsewhere; a.fmass[cell] = dV sum (phi rho) over the solids on those
 // cells (left as it is elsewhere).  Each
 // warp also links the runs of fragment cells along x within its 32 cells:

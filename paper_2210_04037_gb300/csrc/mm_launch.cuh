@@ -218,6 +218,15 @@ struct Launch {
     return (long long)((n[axis] + TL - 1) / TL) * ((n[TD] + TW - 1) / TW) * n[RD];
   }
 
+  // grids with a void material: two or three materials, one plastic
+  template <int DIM>
+  static cudaError_t by_mat_void(int what, int axis, int flag, KArgs a, double* out,
+                                 int nblocks, cudaStream_t s) {
+    if (a.nmat == 2 && a.nhist == 1) return run<DIM, 2, 1>(what, axis, flag, a, out, nblocks, s);
+    if (a.nmat == 3 && a.nhist == 1) return run<DIM, 3, 1>(what, axis, flag, a, out, nblocks, s);
+    return cudaErrorInvalidValue;
+  }
+
   template <int DIM>
   static cudaError_t by_mat(int what, int axis, int flag, KArgs a, double* out, int nblocks,
                             cudaStream_t s) {

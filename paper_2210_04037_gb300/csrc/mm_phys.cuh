@@ -40,6 +40,21 @@ struct P32 {
   static constexpr bool aform = true;
   static constexpr bool allphi = true;
 };
+// The same for grids holding a void material (eos 2: the void volume
+// fraction of Sec. 2.1): the closures leave it out of the mass, the energy
+// and the pressure equilibrium, and the sweeps open void at critically
+// damaged faces in tension (Sec. 3.1).  Grids without void keep the plain
+// policies (voidable false), whose kernels carry none of this.
+struct P64V : P64 {
+  static constexpr bool voidable = true;
+};
+struct P32V : P32 {
+  static constexpr bool voidable = true;
+};
+template <class P, class = void> struct Voidable { static constexpr bool value = false; };
+template <class P> struct Voidable<P, decltype((void)P::voidable)> {
+  static constexpr bool value = P::voidable;
+};
 
 // ---------------------------------------------------------------- math ----
 __device__ __forceinline__ double mlog(double x) { return log(x); }
@@ -114,7 +129,7 @@ struct Lay {
 template <class R>
 __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, R& p,
                                        R& dp, R& G) {
-  if (m.eos == 0) {
+  if (m.eos != 1) {  // ideal gas or void
     e = R(0); p = R(0); dp = R(0); G = R(0);
     return;
   }
@@ -137,7 +152,7 @@ __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, 
 // K0/(alpha rho0) in place of divisions.
 __device__ __forceinline__ void thermo(const MatKf& m, float rho, float psi, float J2, float& e,
                                        float& p, float& dp, float& G) {
-  if (m.eos == 0) {
+  if (m.eos != 1) {  // ideal gas or void
     e = 0.f; p = 0.f; dp = 0.f; G = 0.f;
     return;
   }
@@ -421,6 +436,12 @@ struct Phys {
   static constexpr int NPX = P::allphi ? NMAT : L::NPHI;  // fractions in the X block
   static constexpr int NX = 1 + NPX;
   static constexpr bool AF = P::aform;
+  static constexpr bool VD = Voidable<P>::value;
+
+  // Material l is the void (grids with a void material only).
+  __device__ static __forceinline__ bool isvoid(const KArgs& a, int l) {
+    return VD && l == a.void_l;
+  }
 
   // Full 3x3 stored tensor (Fbar, or A = Fbar - I): inactive comps are 0 off
   // the diagonal (and the diagonal is always stored).
@@ -487,6 +508,7 @@ struct Phys {
       const R psi = m.damage != 0 ? R(1) - D[l] : R(1);
       R G;
       thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G);
+      if (isvoid(a, l)) continue;  // no part in the pressure equilibrium
       if constexpr (P::split)
         mx.xi += phi[l] * m.xi;
       else
@@ -501,15 +523,21 @@ struct Phys {
   // c_l^2 = dp_ref,l + (Gamma_l + 1)(p - p_ref,l)/rho_l.
   template <int AX>
   __device__ static __forceinline__ bool finish(const KArgs& a, R p, const R rho[NMAT],
-                                                const R arho[NMAT], const Mix& mx, Aux<R>& ax) {
+                                                const R arho[NMAT], const Mix& mx, Aux<R>& ax,
+                                                R nu = R(0)) {
+    // with void in the cell the materials fill 1 - nu of it: the pressure
+    // part of the stress is theirs times that (the shear part is weighted by
+    // the fractions already)
+    const R pm = VD ? p * (R(1) - nu) : p;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ax.sd[k] = (k == AX ? -p : R(0)) + R(2) * mx.Gm * mx.devH[3 * k + AX];
-      ax.sr[k] = (k == AX ? -p : R(0)) + R(2) * mx.Gm * mx.devH[3 * AX + k];
+      ax.sd[k] = (k == AX ? -pm : R(0)) + R(2) * mx.Gm * mx.devH[3 * k + AX];
+      ax.sr[k] = (k == AX ? -pm : R(0)) + R(2) * mx.Gm * mx.devH[3 * AX + k];
     }
     R s = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
+      if (isvoid(a, l)) continue;
       const R Gam = R(matp<R>(a, l).Gamma);
       const R cl2 = mx.dp[l] + (Gam + R(1)) * (p - mx.p[l]) / rho[l];
       if constexpr (P::split)
@@ -536,6 +564,14 @@ struct Phys {
     ax.rho = R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
+      if (isvoid(a, l)) {  // no mass; its fraction may be zero
+        if (!(phid[l] >= XT(0))) return false;
+        phi[l] = R(phid[l]);
+        rho[l] = R(0);
+        arho[l] = R(0);
+        D[l] = R(0);
+        continue;
+      }
       if (!(phid[l] > XT(0))) return false;
       phi[l] = R(phid[l]);
       rho[l] = w[L::oARHO + l];
@@ -559,7 +595,8 @@ struct Phys {
       // FP32: the face states need float accuracy only
       R re = R(0);
 #pragma unroll
-      for (int l = 0; l < NMAT; ++l) re += arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * (p - mx.p[l]);
+      for (int l = 0; l < NMAT; ++l)
+        if (!isvoid(a, l)) re += arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * (p - mx.p[l]);
       const R kef = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
       // the FP32 sum equals the FP64 sum rounded to FP32 (double rounding is
       // exact for one addition); the FP64 total is formed only when asked for
@@ -571,7 +608,8 @@ struct Phys {
     } else {
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
-        rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
+        if (!isvoid(a, l))
+          rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
       ke = 0.5 * E(ax.rho) *
            (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
     }
@@ -591,6 +629,7 @@ struct Phys {
     if (rhoE_out) *rhoE_out = rhoe + ke;
 #pragma unroll
     for (int k = 0; k < L::NFC; ++k) c[L::oF + k] = w[L::oF + k];
+    const R nu = VD && a.void_l >= 0 ? phi[VD ? a.void_l : 0] : R(0);
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
 #pragma unroll
@@ -602,7 +641,7 @@ struct Phys {
     }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) c[L::oX + k] = w[L::oX + k];
-    return finish<AX>(a, p, rho, arho, mx, ax);
+    return finish<AX>(a, p, rho, arho, mx, ax, nu);
   }
 
   // conserved (c, cx) -> primitive (w, wx), with
@@ -619,6 +658,12 @@ struct Phys {
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       arho[l] = c[L::oARHO + l];
+      if (isvoid(a, l)) {
+        if (!(phid[l] >= XT(0))) return false;
+        phi[l] = R(phid[l]);
+        rho[l] = R(0);
+        continue;
+      }
       if (!(phid[l] > XT(0)) || !(arho[l] > R(0))) return false;
       phi[l] = R(phid[l]);
       if constexpr (P::split)
@@ -652,7 +697,8 @@ struct Phys {
       const R ke = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
       R num = rhoE_d ? R(*rhoE_d - E(ke)) : R(cx[0]) - ke;
 #pragma unroll
-      for (int l = 0; l < NMAT; ++l) num += -arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * mx.p[l];
+      for (int l = 0; l < NMAT; ++l)
+        if (!isvoid(a, l)) num += -arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * mx.p[l];
       pE = E(num / mx.xi);
     } else {
       const E ke = 0.5 * E(ax.rho) *
@@ -660,7 +706,7 @@ struct Phys {
       E num = (rhoE_d ? *rhoE_d : E(cx[0])) - ke;
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
-        num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
+        if (!isvoid(a, l)) num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
       pE = num / E(mx.xi);
     }
 #pragma unroll
@@ -688,7 +734,8 @@ struct Phys {
     for (int k = 0; k < NX; ++k) sx += cx[k] + wx[k];
     if (!(ok && mfinite(sw) && mfinite(sx))) return false;
     if (mxo) *mxo = mx;
-    return finish<AX>(a, R(pE), rho, arho, mx, ax);
+    const R nu = VD && a.void_l >= 0 ? phi[VD ? a.void_l : 0] : R(0);
+    return finish<AX>(a, R(pE), rho, arho, mx, ax, nu);
   }
 
   // Row AX of Fbar of a state vector.
@@ -848,6 +895,189 @@ struct Phys {
       ess += XT(sgn) * (XT(tss) * XT(uss) - XT(tauK) * XT(uKt)) / XT(csK);
     }
     fox[0] = fox[0] + XT(SSK) * (ess - Es);
+  }
+
+  // ---- void opening (void grids): Sec. 3.1 opens void where either face
+  // state is critically damaged and the two are in tension along the sweep,
+  // x^T (sigma_L + sigma_R) x > 0.  Each side meets a traction-free surface;
+  // where the surfaces separate the gap between them is void.
+
+  // A damaged solid at D >= D_cut = D_crit (1 - 1e-4), as in the yield
+  // stress.
+  __device__ static __forceinline__ bool critical(const KArgs& a, const R* c) {
+    bool crit = false;
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) {
+      const auto& m = matp<R>(a, l);
+#pragma unroll
+      for (int h = 0; h < NH; ++h)
+        if (a.hslot[l] == h && m.damage != 0) {
+          const R ar = c[L::oARHO + l];
+          if (ar > R(0)) crit = crit || c[L::oH + 2 * h + 1] / ar >= R(m.D_cut);
+        }
+    }
+    return crit;
+  }
+
+  // Speed of side K's traction-free surface: across K's longitudinal wave
+  // S_K = u_K -/+ c_L,K the normal stress drops to zero (HLLC jump relation
+  // 0 = sigma_K - rho_K (S_K - u_K)(S_f - u_K)).
+  template <int AX>
+  __device__ static __forceinline__ R free_surface_speed(bool lft, const Aux<R>& ax) {
+    const R SK = lft ? ax.u[AX] - ax.cL : ax.u[AX] + ax.cL;
+    return ax.u[AX] + ax.sd[AX] / (ax.rho * (SK - ax.u[AX]));
+  }
+
+  // Flux of side K's fan against a traction-free surface: waves S_K, the
+  // shear wave S_f -/+ c_s and the surface S_f; the normal stress and then
+  // the tangential tractions are zero behind them.  at_face: the region
+  // holding x/t = 0; otherwise the region just inside the surface.
+  template <int AX>
+  __device__ static void free_surface_flux(bool lft, const R* cK, const XT* xK, const Aux<R>& aK,
+                                           bool at_face, R* fo, XT* fox, R& uface,
+                                           R frowo[3]) {
+    const R uK = aK.u[AX];
+    const R SK = lft ? uK - aK.cL : uK + aK.cL;
+    const R Sf = free_surface_speed<AX>(lft, aK);
+    flux<AX>(cK, xK, aK, fo, fox);
+    frow<AX>(cK, frowo);
+    uface = uK;
+    if (at_face && (lft ? SK >= R(0) : SK <= R(0))) return;  // region K
+    const R chi = (SK - uK) / (SK - Sf);
+    const R rK = aK.rho;
+    R us[NF];
+#pragma unroll
+    for (int l = 0; l < NMAT - 1; ++l) us[L::oPHI + l] = R(0);
+#pragma unroll
+    for (int l = 0; l < NPX; ++l) fox[1 + l] = fox[1 + l] + XT(SK) * (xK[1 + l] * XT(chi) - xK[1 + l]);
+#pragma unroll
+    for (int l = 0; l < NMAT; ++l) us[L::oARHO + l] = cK[L::oARHO + l] * chi;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) us[L::oMOM + k] = (k == AX) ? rK * chi * Sf : cK[L::oMOM + k] * chi;
+    us[L::oE] = R(0);
+    const XT Es = XT(chi) * (xK[0] + XT(rK) * XT(Sf) * (XT(Sf) - XT(uK)) -
+                             XT(aK.sd[AX]) * (XT(Sf) - XT(uK)) / (XT(SK) - XT(uK)));
+#pragma unroll
+    for (int k = 0; k < L::NFC; ++k) {
+      const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+      if (i == AX)
+        us[L::oF + k] = cK[L::oF + k];
+      else
+        us[L::oF + k] = AF ? Fv(i, j, cK[L::oF + k]) * chi - (i == j ? R(1) : R(0))
+                           : cK[L::oF + k] * chi;
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NH; ++k) us[L::oH + k] = cK[L::oH + k] * chi;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) us[L::oX + k] = cK[L::oX + k] * chi;
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+      if (k != L::oE && (k < L::oPHI || k >= L::oPHI + L::NPHI)) fo[k] = fo[k] + SK * (us[k] - cK[k]);
+    fox[0] = fox[0] + XT(SK) * (Es - xK[0]);
+    uface = uK + SK * (chi - R(1));
+    if (DIM == 1) return;
+    // the shear wave: speed from the star density, kept between S_K and S_f
+    const R rs = rK * ((SK - uK) / (SK - Sf));
+    R cs = msqrt(aK.G / rs);
+    if (cs > mabs(Sf - SK)) cs = mabs(Sf - SK);
+    if (!(cs > R(0))) return;
+    const R SSK = lft ? Sf - cs : Sf + cs;
+    if (at_face && (lft ? SSK >= R(0) : SSK <= R(0))) return;  // region K*
+    const R Z = rs * cs, sgn = lft ? R(1) : R(-1);
+    XT ess = Es;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == AX) continue;
+      const R tau = aK.sd[t], ut = aK.u[t];
+      // zero traction behind the shear wave: tau + sgn Z (uss - ut) = 0
+      const R uss = ut - sgn * tau / Z;
+      const R du = uss - ut;
+      fo[L::oMOM + t] = fo[L::oMOM + t] + SSK * (rs * uss - us[L::oMOM + t]);
+#pragma unroll
+      for (int k = 0; k < L::NFC; ++k) {
+        const int i = FC<DIM>::idx(k) / 3, j = FC<DIM>::idx(k) % 3;
+        if (i == t) {
+          const R uss_f = us[L::oF + k] + sgn * frowo[j] * du / cs;
+          fo[L::oF + k] = fo[L::oF + k] + SSK * (uss_f - us[L::oF + k]);
+        }
+      }
+      ess += XT(sgn) * (XT(0) * XT(uss) - XT(tau) * XT(ut)) / XT(cs);
+    }
+    fox[0] = fox[0] + XT(SSK) * (ess - Es);
+  }
+
+  // The face's two records, as the cell left of it sees it (fL, fxL, ufL,
+  // rowL) and as the cell right of it does.  Both are the contact solver's
+  // unless the void opens.  Where it opens, each side's surface sets that
+  // side's face velocity, Fbar and X transport; the conserved fields and
+  // the material fractions take what crosses the face (nothing when the gap
+  // holds it, else the fan of the side whose surface has passed it), and
+  // the void fraction takes the rest: a side receiving the gap gets void at
+  // the rate S_f,own - u_crossing, so its fractions keep summing to one.
+  template <int AX>
+  __device__ static void riemann2(const KArgs& a, const R* cL_, const XT* xL, const Aux<R>& aL,
+                                  const R* cR_, const XT* xR, const Aux<R>& aR, R* fL, XT* fxL,
+                                  R& ufL, R rowL[3], R* fR, XT* fxR, R& ufR, R rowR[3]) {
+    if (a.void_l >= 0 && (critical(a, cL_) || critical(a, cR_)) && aL.sd[AX] + aR.sd[AX] > R(0)) {
+      const R SfL = free_surface_speed<AX>(true, aL), SfR = free_surface_speed<AX>(false, aR);
+      if (SfL < SfR) {
+        // the crossing side's fan at the face (nothing if the gap holds it)
+        R fc[NF], ufc = R(0), rowc[3];
+        XT fxc[NX];
+        int cross = -1;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) fc[k] = R(0);
+#pragma unroll
+        for (int k = 0; k < NX; ++k) fxc[k] = XT(0);
+        if (SfL > R(0)) {
+          cross = 0;
+          free_surface_flux<AX>(true, cL_, xL, aL, true, fc, fxc, ufc, rowc);
+        } else if (SfR < R(0)) {
+          cross = 1;
+          free_surface_flux<AX>(false, cR_, xR, aR, true, fc, fxc, ufc, rowc);
+        }
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          const bool lft = side == 0;
+          R* fo = lft ? fL : fR;
+          XT* fox = lft ? fxL : fxR;
+          R& uf = lft ? ufL : ufR;
+          R* row = lft ? rowL : rowR;
+          R fs[NF], ufs, rows[3];
+          XT fxs[NX];
+          free_surface_flux<AX>(lft, lft ? cL_ : cR_, lft ? xL : xR, lft ? aL : aR, false, fs, fxs,
+                                ufs, rows);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) row[j] = rows[j];
+          if (cross == side) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) fo[k] = fc[k];
+#pragma unroll
+            for (int k = 0; k < NX; ++k) fox[k] = fxc[k];
+            uf = ufc;
+            continue;
+          }
+#pragma unroll
+          for (int k = 0; k < NF; ++k)
+            fo[k] = ((k >= L::oF && k < L::oF + L::NFC) || k >= L::oX) ? fs[k] : fc[k];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) fox[k] = fxc[k];
+#pragma unroll
+          for (int l = 0; l < NPX; ++l)
+            if (l == a.void_l) fox[1 + l] = fox[1 + l] + XT(ufs - ufc);
+          uf = ufs;
+        }
+        return;
+      }
+    }
+    riemann<AX>(cL_, xL, aL, cR_, xR, aR, fL, fxL, ufL, rowL);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) fR[k] = fL[k];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) fxR[k] = fxL[k];
+    ufR = ufL;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) rowR[j] = rowL[j];
   }
 
   // HLLD-type Riemann solver for the elastic mixture: outer waves S_L, S_R

@@ -401,6 +401,33 @@ def _crack_mask(case: Case, r: np.ndarray, theta: np.ndarray, angles: np.ndarray
     return m
 
 
+def add_void(case: Case, index: int = 1) -> Case:
+    """The same case with a void material (no void yet: fraction 0, density
+    0) inserted as material `index` (not the last): a grid that can open
+    void where critically damaged faces are in tension (Sec. 3.1)."""
+    import copy
+    nmat = len(case.materials)
+    assert 0 <= index < nmat
+    out = copy.deepcopy(case)
+    out.materials = case.materials[:index] + [void()] + case.materials[index:]
+    lay0, lay1 = case.layout, out.layout
+    w0 = case.prim
+    w1 = np.zeros((lay1.nfield, case.ncell))
+    phis = [w0[lay0.o_phi + l] for l in range(nmat - 1)]
+    rhos = [w0[lay0.o_rho + l] for l in range(nmat)]
+    zero = np.zeros(case.ncell)
+    phis = phis[:index] + [zero] + phis[index:]
+    rhos = rhos[:index] + [zero] + rhos[index:]
+    for l, v in enumerate(phis):
+        w1[lay1.o_phi + l] = v
+    for l, v in enumerate(rhos):
+        w1[lay1.o_rho + l] = v
+    w1[lay1.o_u:] = w0[lay0.o_u:]
+    out.prim = w1
+    out.name = case.name + "_void"
+    return out
+
+
 def fractured_ring(n: int = 512, cracks: int = 12, seed: int = 11, **kw) -> Case:
     """The expanding-ring geometry at fragmentation (Sec. 4.3), input for
     fragment labelling: the annulus cut by `cracks` radial cracks of
