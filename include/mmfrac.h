@@ -323,12 +323,12 @@ mm_status mm_conserved_totals(mm_grid* g, double* out, size_t out_len);
  * must not let a library allocate (cudaMalloc can synchronise the device and
  * fragments the pool), or a runtime whose allocator is off limits at the
  * point of the call.  They pass the state and the output; the block partial
- * sums go to one file-scope device array of 1024 x (MM_MAXMAT + 4) doubles
- * (48 KiB) that every GPU which loads the library keeps until the process
- * exits.
+ * sums go to one file-scope device array of 1024 x 7 doubles (56 KiB: up
+ * to 3 materials) that every GPU which loads the library keeps until the
+ * process exits.
  *   d_cons   device pointer, FP64 conserved fields [nfield][ncell] in the
  *            field order above (mm_read_fields(..., primitive = 0) layout);
- *   dim, ncell, n_materials (1..MM_MAXMAT), n_plastic (materials with a
+ *   dim, ncell, n_materials (1..3), n_plastic (materials with a
  *            plasticity model): the layout of d_cons;
  *   dx       host array, cell size per axis (dV = product over dim);
  *   d_out    device pointer to N + 4 doubles (as mm_conserved_totals);
