@@ -328,14 +328,20 @@ mm_status mm_conserved_totals(mm_grid* g, double* out, size_t out_len);
  * process exits.
  *   d_cons   device pointer, FP64 conserved fields [nfield][ncell] in the
  *            field order above (mm_read_fields(..., primitive = 0) layout);
- *   dim, ncell, n_materials (1..3), n_plastic (materials with a
- *            plasticity model): the layout of d_cons;
+ *   dim, ncell, n_materials (1..3): the layout of d_cons; n_plastic
+ *            (materials with a plasticity model) is only checked
+ *            (0..n_materials): the totals read fields that come before the
+ *            plastic ones, so their offsets do not depend on it;
  *   dx       host array, cell size per axis (dV = product over dim);
  *   d_out    device pointer to N + 4 doubles (as mm_conserved_totals);
  *   cuda_stream  stream to order the two kernels on (NULL: default stream).
- * The call is asynchronous on the stream.  The first call on a device (with
- * that device current) resolves the scratch array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * The call is asynchronous on the stream.  Each call looks up the scratch
+ * array's device address in the current context (cudaGetSymbolAddress).
+ * The first call in a context loads the library's device code there if it
+ * is not loaded yet (lazy module loading, the CUDA default), which
+ * materialises the array: a one-time device allocation by the driver.  Make
+ * that first call during setup, before any stream capture; later calls
+ * allocate nothing.
  * Every call on a device shares the one array and overwrites every entry it
  * reads, so nothing carries over, but calls that overlap on the GPU (other
  * streams, other threads) race on it: order them.  More materials than the

@@ -7,12 +7,11 @@
 // partial sums live in one file-scope device array of fixed size that every
 // GPU which loads this library keeps until the process exits.  The host
 // code must not pass the array's name to a kernel (in host code it names a
-// host-side stand-in); it resolves the device address once per device with
-// cudaGetSymbolAddress and passes that.
+// host-side stand-in); it resolves the device address with
+// cudaGetSymbolAddress at every call and passes that.
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "mm_internal.h"
 #include "mmfrac.h"
@@ -26,25 +25,15 @@ constexpr int kNoallocQuantities = MM_MAXMAT + 4;    // N masses, 3 momenta, ene
 // reads, so nothing has to be cleared between calls.
 static __device__ __align__(256) double mm_noalloc_partial[kNoallocBlocks * kNoallocQuantities];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-double* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device, resolved on the
-// first call made with that device current.
+// Device address of the scratch array in the current context.  Looked up at
+// every call (a host-side table lookup once the module is loaded) rather
+// than cached, so that it stays right after a context is reset and the
+// module loaded again at another address.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, mm_noalloc_partial);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, mm_noalloc_partial);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
