@@ -56,6 +56,7 @@ struct or_grid {
   long steps, bad_cell;
   long nbound; /* faces sent to first order by the phase-density bound */
   int xscheme; /* 0: X carried by the sweeps (R20); 1: WENO3 + RK3 (R28) */
+  int seed_x;  /* Lagrangian seeding into void before each step (R35; default on) */
 };
 
 /* Derived quantities of one state that the flux and the Riemann solver use. */
@@ -1423,6 +1424,7 @@ or_grid* or_create(int dim, const long n[3], const double lo[3],
   }
   g->nhist = 0;
   g->void_l = -1;
+  g->seed_x = 1;
   for (int l = 0; l < nmat; ++l) {
     g->mat[l] = mats[l];
     g->hslot[l] = mats[l].plasticity == 1 ? g->nhist++ : -1;
@@ -1490,10 +1492,144 @@ void or_destroy(or_grid* g) {
   free(g);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Lagrangian seeding into void (Sec. 3.2.1 seeding routine, R35): in each  */
+/* cell with nu > 1/2 and a normal, |grad nu| h > 1e-6 (h the largest cell  */
+/* size; a void of uniform fraction up to rounding has none), the unit      */
+/* normal n = -grad nu / |grad nu| (central differences; it points from    */
+/* the void into the material), a probe at                                  */
+/* p = c + 1.5 h n (c the cell centre) and                                  */
+/* X_new = X(p) - (p - c), X(p) multilinear in the cell-centred X.  All     */
+/* cells read the X of the step's start (the new values are written after   */
+/* every cell is computed).  Cells outside the grid follow the sweeps'      */
+/* ghost rules: periodic wraps (X shifted by the period), reflective        */
+/* mirrors (X_d reflected about the wall), transmissive copies the edge.    */
+/* ------------------------------------------------------------------------ */
+
+/* Cell index i along d (at most two cells outside the grid) mapped into the
+ * grid; *shift and *mirror say how X_d of that cell maps to the ghost. */
+static long ghost_map(const or_grid* g, int d, long i, double* shift, int* mirror,
+                      double* wall) {
+  const long n = g->n[d];
+  *shift = 0.0;
+  *mirror = 0;
+  *wall = 0.0;
+  if (i >= 0 && i < n) return i;
+  const int side = i < 0 ? 0 : 1;
+  const int bc = g->bc[d][side];
+  if (bc == OR_BC_PERIODIC) {
+    *shift = side == 0 ? -(g->hi[d] - g->lo[d]) : (g->hi[d] - g->lo[d]);
+    return side == 0 ? i + n : i - n;
+  }
+  if (bc == OR_BC_REFLECTIVE) {
+    *mirror = 1;
+    *wall = side == 0 ? g->lo[d] : g->hi[d];
+    return side == 0 ? -1 - i : 2 * n - 1 - i;
+  }
+  return side == 0 ? 0 : n - 1;
+}
+
+static double void_at(const or_grid* g, const long ix[3]) {
+  long j[3];
+  for (int d = 0; d < 3; ++d) {
+    double s, w;
+    int m;
+    j[d] = d < g->dim ? ghost_map(g, d, ix[d], &s, &m, &w) : 0;
+  }
+  const long c = j[0] + g->n[0] * (j[1] + g->n[1] * j[2]);
+  return g->U[(size_t)(g->o_phi + g->void_l) * g->ncell + c];
+}
+
+/* X of the cell at integer position ix (ghosts by the rules above). */
+static void x_of(const or_grid* g, const double* Xs, const long ix[3], double X[3]) {
+  long j[3];
+  double shift[3] = {0.0, 0.0, 0.0}, wall[3] = {0.0, 0.0, 0.0};
+  int mirror[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d)
+    j[d] = d < g->dim ? ghost_map(g, d, ix[d], &shift[d], &mirror[d], &wall[d]) : 0;
+  const long c = j[0] + g->n[0] * (j[1] + g->n[1] * j[2]);
+  for (int k = 0; k < g->dim; ++k) {
+    double x = Xs[(size_t)k * g->ncell + c];
+    if (mirror[k]) x = 2.0 * wall[k] - x;
+    X[k] = x + shift[k];
+  }
+}
+
+int or_seed_x(or_grid* g) {
+  if (g->void_l < 0) return OR_OK;
+  const int dim = g->dim;
+  const size_t nX = (size_t)dim * g->ncell;
+  double* Xs = malloc(sizeof(double) * nX);
+  double* Xn = malloc(sizeof(double) * nX);
+  if (!Xs || !Xn) {
+    free(Xs);
+    free(Xn);
+    return OR_EINVAL;
+  }
+  memcpy(Xs, g->U + (size_t)g->o_X * g->ncell, sizeof(double) * nX);
+  memcpy(Xn, Xs, sizeof(double) * nX);
+  double h = 0.0;
+  for (int d = 0; d < dim; ++d) h = g->dx[d] > h ? g->dx[d] : h;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < g->ncell; ++c) {
+    const long ix[3] = {c % g->n[0], (c / g->n[0]) % g->n[1], c / (g->n[0] * g->n[1])};
+    if (!(void_at(g, ix) > 0.5)) continue;
+    double gr[3] = {0.0, 0.0, 0.0}, gn = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      long a[3] = {ix[0], ix[1], ix[2]}, b[3] = {ix[0], ix[1], ix[2]};
+      a[d] -= 1;
+      b[d] += 1;
+      gr[d] = (void_at(g, b) - void_at(g, a)) / (2.0 * g->dx[d]);
+      gn += gr[d] * gr[d];
+    }
+    gn = sqrt(gn);
+    if (!(gn * h > 1e-6)) continue;
+    double cc[3], p[3], f[3];
+    long i0[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      cc[d] = g->lo[d] + ((double)ix[d] + 0.5) * g->dx[d];
+      p[d] = cc[d] + 1.5 * h * (-gr[d] / gn);
+      const double s = (p[d] - g->lo[d]) / g->dx[d] - 0.5;
+      const double fl = floor(s);
+      i0[d] = (long)fl;
+      f[d] = s - fl;
+    }
+    double Xi[3] = {0.0, 0.0, 0.0};
+    for (int corner = 0; corner < (1 << dim); ++corner) {
+      long q[3] = {0, 0, 0};
+      double w = 1.0;
+      for (int d = 0; d < dim; ++d) {
+        const int b = (corner >> d) & 1;
+        q[d] = i0[d] + b;
+        w *= b ? f[d] : 1.0 - f[d];
+      }
+      double Xq[3];
+      x_of(g, Xs, q, Xq);
+      for (int k = 0; k < dim; ++k) Xi[k] += w * Xq[k];
+    }
+    for (int k = 0; k < dim; ++k) Xn[(size_t)k * g->ncell + c] = Xi[k] - (p[k] - cc[k]);
+  }
+  memcpy(g->U + (size_t)g->o_X * g->ncell, Xn, sizeof(double) * nX);
+  free(Xs);
+  free(Xn);
+  return OR_OK;
+}
+
+int or_set_seed_x(or_grid* g, int on) {
+  if (on != 0 && on != 1) return OR_EINVAL;
+  g->seed_x = on;
+  return OR_OK;
+}
+
 int or_step(or_grid* g, int nsteps, double cfl, double dt_fixed, double* info) {
   int rc = OR_OK;
   for (int s = 0; s < nsteps; ++s) {
     double dt, smax = 0.0;
+    /* X in the void from the material around it, before the step (R35) */
+    if (g->void_l >= 0 && g->seed_x) {
+      rc = or_seed_x(g);
+      if (rc != OR_OK) break;
+    }
     if (dt_fixed > 0.0) {
       dt = dt_fixed;
     } else {

@@ -89,6 +89,13 @@ void or_set_threads(int n);
  * from the state at the step's start (Sec. 3.2.1).  OR_EINVAL otherwise. */
 int or_set_x_scheme(or_grid* g, int scheme);
 
+/* Lagrangian seeding into void (Sec. 3.2.1 seeding routine; reading in the
+ * source): or_seed_x applies it once to the present state (grids with a
+ * void material; no-op otherwise); or_set_seed_x(g, 0/1) turns off / on
+ * (default) its application before every step. */
+int or_seed_x(or_grid* g);
+int or_set_seed_x(or_grid* g, int on);
+
 /* Fragments at void cut-off theta (Sec. 4.2, 4.3; reading in the source):
  * labels[ncell] (may be NULL) gets each cell's fragment label, the smallest
  * cell index of its fragment, or -1; the first max_frag fragments in label

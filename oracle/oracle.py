@@ -95,6 +95,8 @@ def _bind(lib):
     lib.or_totals.argtypes = [ctypes.c_void_p, P(d)]
     lib.or_set_threads.argtypes = [i]
     lib.or_set_x_scheme.argtypes = [ctypes.c_void_p, i]
+    lib.or_seed_x.argtypes = [ctypes.c_void_p]
+    lib.or_set_seed_x.argtypes = [ctypes.c_void_p, i]
     lib.or_fragments.restype = L
     lib.or_fragments.argtypes = [ctypes.c_void_p, d, P(L), P(L), P(L), P(d), L]
     lib.or_thermo.argtypes = [P(Material), d, d, d, P(d)]
@@ -160,6 +162,15 @@ class OracleGrid:
         """0: X carried by the sweeps; 1: WENO3 + RK3 (Sec. 3.2.1)."""
         if self.lib.or_set_x_scheme(self.h, int(scheme)) != 0:
             raise ValueError("x scheme must be 0 or 1")
+
+    def seed_x(self) -> None:
+        """Lagrangian seeding into void once, on the present state (Sec. 3.2.1)."""
+        if self.lib.or_seed_x(self.h) != 0:
+            raise RuntimeError("oracle seeding failed")
+
+    def set_seed_x(self, on: bool) -> None:
+        """Seeding before every step on (default) or off."""
+        self.lib.or_set_seed_x(self.h, 1 if on else 0)
 
     def step(self, nsteps: int, cfl: float | None = None, dt: float = 0.0) -> dict:
         info = np.zeros(6)

@@ -247,6 +247,179 @@ def check_void_opening_galilean(lib=None):
     assert gaps[0] > 0 and abs(gaps[1] / gaps[0] - 1) < 1e-3, gaps
 
 
+# ---------------------------------------------------------------------------
+# Lagrangian seeding into void (Sec. 3.2.1 seeding routine, reading R35)
+# ---------------------------------------------------------------------------
+
+def seed_block(dim, n, ramp, bc=0, b=(3e-4, -2e-4, 1e-4), garbage=1.0, Lb=1e-3, p=1e5,
+               numax=1.0 - 1e-6):
+    """A CuBe block with a void fraction nu = ramp(x, y, z) clipped to
+    numax < 1 (the CuBe keeps a trace), at rest at 1e5 Pa, with X = x + b
+    where nu <= 1/2
+    and X = x + garbage where nu > 1/2; box [0, Lb]^dim, boundary rule bc on
+    every side; pressure p."""
+    mats = [W.void(), CUBE]
+    n3 = [n if k < dim else 1 for k in range(3)]
+    hi = [Lb if k < dim else 1.0 for k in range(3)]
+    c = W.Case("seed", dim, n3, [0, 0, 0], hi, [bc] * (2 * dim), mats, None, cfl=0.6)
+    lay = c.layout
+    c.prim = W.blank_prim(lay, c.ncell)
+    cen = c.centres()
+    nu = np.clip(ramp(*cen[:dim]), 0.0, numax)
+    c.prim[lay.o_phi] = nu
+    c.prim[lay.o_rho] = 0.0
+    c.prim[lay.o_rho + 1] = CUBE["rho0"]
+    c.prim[lay.o_p] = p
+    for d in range(dim):
+        c.prim[lay.o_X + d] = cen[d] + np.where(nu > 0.5, garbage, b[d])
+    return c
+
+
+def _seeded_cells(c, nu):
+    """Cells the routine seeds: nu > 1/2 and |grad nu| h > 1e-6 (central
+    differences, the boundary rule applied to the neighbours)."""
+    lay = c.layout
+    dim = c.dim
+    A = nu.reshape([c.n[k] for k in range(dim)][::-1])
+    g = np.zeros(A.shape)
+    for d in range(dim):
+        ax = dim - 1 - d
+        if c.bc[2 * d] == W.BC_PERIODIC:
+            up, dn = np.roll(A, -1, axis=ax), np.roll(A, 1, axis=ax)
+        else:
+            pad = np.concatenate([np.take(A, [0], axis=ax), A, np.take(A, [-1], axis=ax)], axis=ax)
+            up = np.take(pad, range(2, A.shape[ax] + 2), axis=ax)
+            dn = np.take(pad, range(0, A.shape[ax]), axis=ax)
+        g += ((up - dn) / (2 * c.dx[d])) ** 2
+    h = max(c.dx[:dim])
+    return ((A > 0.5) & (np.sqrt(g) * h > 1e-6)).reshape(-1)
+
+
+def _check_seeding(c, rounds, b, lib, tol=1e-12, garbage_deep=True, margin=3):
+    if not garbage_deep:
+        # garbage only where the routine seeds; the void it leaves alone
+        # (nu uniform around it) holds X = x + b
+        lay = c.layout
+        keep = ~_seeded_cells(c, c.prim[lay.o_phi])
+        cen = c.centres()
+        for d in range(c.dim):
+            c.prim[lay.o_X + d][keep] = cen[d][keep] + b[d]
+    g = OracleGrid(c, lib=lib)
+    lay = c.layout
+    U0 = g.read(False)
+    for _ in range(rounds):
+        g.seed_x()
+    U = g.read(False)
+    nu = U0[lay.o_phi]
+    seeded = _seeded_cells(c, nu)
+    assert seeded.sum() >= 4
+    # checked: seeded cells whose probe stencils (and those of the cells
+    # they read, round after round) stay off transmissive boundaries: there
+    # the ghost copies the edge cell, which does not continue an affine X
+    ix = np.indices([c.n[k] for k in range(c.dim)][::-1]).reshape(c.dim, -1)[::-1]
+    inner = np.ones(c.ncell, dtype=bool)
+    for d in range(c.dim):
+        if c.bc[2 * d] == W.BC_TRANSMISSIVE:
+            inner &= (ix[d] >= margin) & (ix[d] <= c.n[d] - 1 - margin)
+    chk = seeded & inner
+    assert chk.sum() >= 4
+    cen = c.centres()
+    for d in range(c.dim):
+        X = U[lay.o_X + d]
+        # seeded cells: the material's X continued, c + b, to rounding
+        err = np.abs(X[chk] - (cen[d][chk] + b[d])).max()
+        assert err <= tol * (c.hi[d] - c.lo[d]), (d, err)
+    # every other cell and every other field unchanged bit for bit
+    keep = ~seeded
+    assert np.array_equal(U[:, keep], U0[:, keep])
+    other = [f for f in range(lay.nfield) if not lay.o_X <= f < lay.o_X + c.dim]
+    assert np.array_equal(U[other], U0[other])
+
+
+def _ramp(s, w):
+    """nu rising linearly from 0 to 1 over a width w centred at s = 0."""
+    return np.clip(0.5 + s / w, 0.0, 1.0)
+
+
+def check_seeding_continues_affine_x_1d(lib=None):
+    """1D: void rising to the right over 8 cells; after six applications
+    (each reaches about a cell further from the material) every seeded cell
+    holds the material's X = x + b continued (1e-12 of the box)."""
+    Lb, n = 1e-3, 64
+    c = seed_block(1, n, lambda x: _ramp(x - 0.5 * Lb, 8 * Lb / n), Lb=Lb)
+    _check_seeding(c, 6, (3e-4,), lib)
+
+
+def check_seeding_continues_affine_x_2d(lib=None):
+    """2D: the void rises across an oblique line (normal at 30 degrees); the
+    probe's bilinear interpolation of X = x + b is exact, so every seeded
+    cell holds c + b (1e-12) whatever the numerical normal."""
+    Lb, n = 1e-3, 48
+    th = np.deg2rad(30.0)
+    c = seed_block(2, n, lambda x, y: _ramp(np.cos(th) * (x - 0.5 * Lb) + np.sin(th) * (y - 0.5 * Lb),
+                                           8 * Lb / n), Lb=Lb)
+    _check_seeding(c, 8, (3e-4, -2e-4), lib)
+
+
+def check_seeding_continues_affine_x_3d(lib=None):
+    """3D: the same across an oblique plane (garbage in the seeded cells
+    only: at the top of the ramp the probes' stencils touch void that is
+    never seeded; the probe's direction is pinned in 1D and 2D)."""
+    Lb, n = 1e-3, 20
+    nrm = np.array([0.5, 0.3, 0.81])
+    nrm /= np.linalg.norm(nrm)
+    c = seed_block(3, n, lambda x, y, z: _ramp(nrm[0] * (x - 0.5 * Lb) + nrm[1] * (y - 0.5 * Lb)
+                                               + nrm[2] * (z - 0.5 * Lb), 8 * Lb / n), Lb=Lb)
+    _check_seeding(c, 16, (3e-4, -2e-4, 1e-4), lib, garbage_deep=False, margin=6)
+
+
+def check_seeding_across_periodic_wrap(lib=None):
+    """Periodic 1D: the void rises from x = 0 to the right and the material
+    lies before the wrap (x near the box's end); probes from the first
+    cells cross the wrap, where X continues shifted by the period."""
+    Lb, n = 1e-3, 64
+
+    def ramp(x):
+        # nu rises through 1/2 at x = 0 (the wrap) and falls back at L/2
+        s = np.where(x < 0.5 * Lb, x, x - Lb)
+        return _ramp(s, 8 * Lb / n) * _ramp(0.5 * Lb - 4 * Lb / n - x, 8 * Lb / n)
+    c = seed_block(1, n, ramp, bc=W.BC_PERIODIC, Lb=Lb)
+    _check_seeding(c, 8, (3e-4,), lib)
+
+
+def check_seeding_across_reflective_wall(lib=None):
+    """Reflective 1D: one cell of material at the right wall, the void
+    rising away from it to the left, and X = x (b = 0, the only affine X a
+    mirror continues): the probes of the cells next to it cross the wall,
+    take the mirrored X there, and every seeded cell holds c."""
+    Lb, n = 1e-3, 32
+    dx = Lb / n
+    c = seed_block(1, n, lambda x: _ramp((Lb - 1.2 * dx) - x, 9 * dx), bc=W.BC_REFLECTIVE,
+                   b=(0.0,), Lb=Lb)
+    _check_seeding(c, 8, (0.0,), lib)
+
+
+def check_seeding_in_the_step(lib=None):
+    """A stress-free block (p = 0 at the reference density, so the void's
+    (1 - nu) p puts no force on it) moving at 120 m/s along x into void,
+    X = x + b everywhere: seeding before every step keeps the affine X that
+    the transport at uniform velocity carries exactly, X = x + b - u t
+    after 30 steps (1e-11 of the box)."""
+    Lb, n = 1e-3, 64
+    c = seed_block(1, n, lambda x: _ramp(x - 0.6 * Lb, 8 * Lb / n), Lb=Lb, garbage=3e-4, p=0.0)
+    lay = c.layout
+    c.prim[lay.o_u] = 120.0
+    g = OracleGrid(c, lib=lib)
+    info = g.step(30)
+    w = g.read()
+    x = c.centres()[0]
+    assert _seeded_cells(c, w[lay.o_phi]).sum() >= 4
+    # (eight cells from each end: the transmissive ghosts copy the edge,
+    # which is not an affine continuation, and that reaches a few cells in)
+    err = np.abs(w[lay.o_X][8:-8] - (x[8:-8] + 3e-4 - 120.0 * info["t"])).max()
+    assert err <= 1e-11 * Lb, err
+
+
 CHECKS = {
     "no_opening_in_compression": check_no_opening_in_compression,
     "no_opening_without_critical_damage": check_no_opening_without_critical_damage,
@@ -255,6 +428,12 @@ CHECKS = {
     "porous_stress_equilibrium": check_porous_stress_equilibrium,
     "void_opening_mirror": check_void_opening_mirror,
     "void_opening_galilean": check_void_opening_galilean,
+    "seeding_continues_affine_x_1d": check_seeding_continues_affine_x_1d,
+    "seeding_continues_affine_x_2d": check_seeding_continues_affine_x_2d,
+    "seeding_continues_affine_x_3d": check_seeding_continues_affine_x_3d,
+    "seeding_across_periodic_wrap": check_seeding_across_periodic_wrap,
+    "seeding_across_reflective_wall": check_seeding_across_reflective_wall,
+    "seeding_in_the_step": check_seeding_in_the_step,
 }
 
 

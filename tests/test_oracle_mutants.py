@@ -75,6 +75,24 @@ MUTANTS = [
     ("void_energy_in_closure",
      "    if (is_void(&g->mat[l])) continue; /* no energy, no part in the closure */\n",
      ""),
+    ("seed_probe_into_the_void",
+     "p[d] = cc[d] + 1.5 * h * (-gr[d] / gn);",
+     "p[d] = cc[d] + 1.5 * h * (gr[d] / gn);"),
+    ("seed_offset_sign",
+     "Xn[(size_t)k * g->ncell + c] = Xi[k] - (p[k] - cc[k]);",
+     "Xn[(size_t)k * g->ncell + c] = Xi[k] + (p[k] - cc[k]);"),
+    ("seed_weights_swapped",
+     "w *= b ? f[d] : 1.0 - f[d];",
+     "w *= b ? 1.0 - f[d] : f[d];"),
+    ("seed_periodic_without_shift",
+     "*shift = side == 0 ? -(g->hi[d] - g->lo[d]) : (g->hi[d] - g->lo[d]);",
+     "*shift = 0.0;"),
+    ("seed_mirror_ignored",
+     "if (mirror[k]) x = 2.0 * wall[k] - x;",
+     ""),
+    ("seed_threshold_inverted",
+     "if (!(void_at(g, ix) > 0.5)) continue;",
+     "if (!(void_at(g, ix) < 0.5)) continue;"),
     ("void_stress_not_scaled",
      "const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;",
      "const double pm = ax->p;"),
