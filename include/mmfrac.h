@@ -164,6 +164,18 @@ mm_status mm_synchronize(mm_grid* g, mm_step_info* info);
 enum { MM_X_SWEEP = 0, MM_X_WENO3_RK3 = 1 };
 mm_status mm_set_x_transport(mm_grid* g, int scheme);
 
+/* Lagrangian seeding into void (Sec. 3.2.1 seeding routine), on grids with a
+ * void material: before each step, every cell with void fraction nu > 1/2
+ * and a normal (|grad nu| h > 1e-6, central differences) takes
+ * X = X(p) - (p - c), c its
+ * centre, p = c + 1.5 h n the probe point, n = -grad nu / |grad nu| (into
+ * the material), h the largest cell size, X(p) multilinear in the
+ * cell-centred X of the step's start; ghost cells follow the boundary rules.
+ * on = 1 (default) or 0; no effect on grids without void (whose X the step
+ * carries everywhere).  Grids with void hold dim x ncell values of scratch
+ * for it from mm_set_materials on.  Errors: MM_EINVAL. */
+mm_status mm_set_lagrangian_seeding(mm_grid* g, int on);
+
 /* Fragments of the present state (Sec. 4.2, 4.3 demarcate fragments by the
  * contour nu = theta of the void volume fraction, theta = 0.25, 0.5, 0.75,
  * and report fragment masses).  A crack is critically damaged solid

@@ -91,6 +91,8 @@ struct mm_grid {
   // X by WENO3 + RK3: scheme and its scratch (velocities, two stages)
   int xscheme = MM_X_SWEEP;
   void* xs[3] = {nullptr, nullptr, nullptr};
+  void* xseed = nullptr;    // Lagrangian seeding scratch (grids with void)
+  bool seed_x = true;       // seeding before each step (grids with void)
   // fragment labelling scratch (allocated on the first mm_fragments):
   // per-cell parents, fragment numbers of the roots and solid masses, the
   // per-block root offsets, and per-fragment labels, cell counts and masses
@@ -399,6 +401,12 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   a.nhist = nhist;
   a.nfield = nfield;
   a.void_l = void_l;
+  if (void_l >= 0 && !g->xseed &&
+      cudaMalloc(&g->xseed, elem_size(g) * (size_t)g->dim * g->ncell) != cudaSuccess) {
+    g->xseed = nullptr;
+    return fail(MM_ENOMEM, "device allocation of the seeding scratch failed");
+  }
+  a.xseed = g->xseed;
   for (int l = 0; l < MM_MAXMAT; ++l) {
     const MatK& k = mk[l];
     a.mat[l] = k;
@@ -486,6 +494,17 @@ mm_status enqueue_one(mm_grid* g, double cfl) {
   {
     KArgs a = args_for(g);
     a.cfl = cfl;
+    if (a.void_l >= 0 && g->seed_x) {
+      // Lagrangian seeding into void from the step's start (all cells read
+      // the old X; the new X are copied over after every cell is done)
+      prof_begin(g, MM_K_XTRANSPORT);
+      CUDA_TRY(go(g, 9, 0, 0, a));
+      const size_t es = elem_size(g);
+      CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(g->U[g->cur]) + es * (size_t)(g->nfield - g->dim) * g->ncell,
+                               g->xseed, es * (size_t)g->dim * g->ncell, cudaMemcpyDeviceToDevice,
+                               g->stream));
+      prof_end(g);
+    }
     // the CFL reduction's last CTA also forms dt (no separate launch)
     prof_begin(g, MM_K_CFL);
     CUDA_TRY(go(g, 2, 0, 0, a));
@@ -673,6 +692,14 @@ mm_status mm_profile_read(mm_grid* g, double* ms, int64_t* counts, int n, int re
   return MM_OK;
 }
 
+mm_status mm_set_lagrangian_seeding(mm_grid* g, int on) {
+  if (!g) return fail(MM_EINVAL, "mm_set_lagrangian_seeding: null grid");
+  if (on != 0 && on != 1) return fail(MM_EINVAL, "mm_set_lagrangian_seeding: on must be 0 or 1");
+  g->seed_x = on != 0;
+  drop_graphs(g);
+  return MM_OK;
+}
+
 mm_status mm_set_x_transport(mm_grid* g, int scheme) {
   if (!g) return fail(MM_EINVAL, "mm_set_x_transport: null grid");
   if (scheme != MM_X_SWEEP && scheme != MM_X_WENO3_RK3)
@@ -820,6 +847,7 @@ mm_status mm_destroy(mm_grid* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   for (int i = 0; i < 3; ++i) cudaFree(g->xs[i]);
+  cudaFree(g->xseed);
   cudaFree(g->fparent);
   cudaFree(g->ffid);
   cudaFree(g->fcm);

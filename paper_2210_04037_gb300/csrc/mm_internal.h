@@ -111,6 +111,7 @@ struct KArgs {
   double* prim;        // [nfield][ncell] doubles for init / read
   double* partial;     // per-block partial totals
   void* xs[3];         // X by WENO3 + RK3: cell velocities, stage 1, stage 2 ([dim][ncell], R)
+  void* xseed;         // Lagrangian seeding (void grids): X after seeding ([dim][ncell], S)
   int* frag;           // fragment labelling: per-cell parent index, -1 outside fragments
   double* fmass;       // fragment labelling: per-cell solid mass dV sum (phi rho)_solid
   double fcut;         // fragment labelling: void cut-off theta

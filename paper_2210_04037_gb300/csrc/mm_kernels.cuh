@@ -1645,6 +1645,117 @@ __global__ void __launch_bounds__(256) k_xstage(KArgs a, int stage) {
   }
 }
 
+// ------------------------------------------------------------ seeding ----
+// Lagrangian seeding into void (Sec. 3.2.1 seeding routine): each cell with
+// void fraction nu > 1/2 and a normal (|grad nu| h > 1e-6) takes
+// X = X(p) - (p - c), c its centre, p = c + 1.5 h n the probe, n =
+// -grad nu / |grad nu| (pointing into the material), h the largest cell
+// size, X(p) multilinear in the cell-centred X of the step's start.  Cells
+// outside the grid follow the sweeps' ghost rules (periodic: wrapped, X
+// shifted by the period; reflective: mirrored, X reflected about the wall;
+// transmissive: the edge cell).  The geometry and the interpolation run in
+// FP64 on both paths, in the order of their definition; every cell's X
+// (seeded or not) goes to a.xseed, copied over the state's X afterwards.
+
+// Index along d mapped into the grid; X_d of that cell maps to the ghost by
+// X -> 2 wall - X (mirror) and + shift.
+__device__ __forceinline__ long long seed_map(const KArgs& a, int d, long long i, double& shift,
+                                              bool& mirror, double& wall) {
+  const long long n = a.n[d];
+  shift = 0.0;
+  mirror = false;
+  wall = 0.0;
+  if (i >= 0 && i < n) return i;
+  const int side = i < 0 ? 0 : 1;
+  const int bc = a.bc[d][side];
+  if (bc == BC_P) {
+    shift = side == 0 ? -(a.hi[d] - a.lo[d]) : (a.hi[d] - a.lo[d]);
+    return side == 0 ? i + n : i - n;
+  }
+  if (bc == BC_R) {
+    mirror = true;
+    wall = side == 0 ? a.lo[d] : a.hi[d];
+    return side == 0 ? -1 - i : 2 * n - 1 - i;
+  }
+  return side == 0 ? 0 : n - 1;
+}
+
+template <class P, int DIM, int NMAT, int NH>
+__global__ void __launch_bounds__(256) k_seed(KArgs a) {
+  typedef typename P::S S;
+  typedef Lay<DIM, NMAT, NH> L;
+  const S* U = static_cast<const S*>(a.Uin);
+  S* out = static_cast<S*>(a.xseed);
+  const long long nc = a.ncell;
+  const long long nuo = phislot<P, DIM, NMAT, NH>(a, a.void_l, 0);
+  double h = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) h = a.dx[d] > h ? a.dx[d] : h;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long ix[3] = {c % a.n[0], (c / a.n[0]) % a.n[1], c / ((long long)a.n[0] * a.n[1])};
+    bool seed = double(U[nuo + c]) > 0.5;
+    double gr[3] = {0.0, 0.0, 0.0}, gn = 0.0;
+    if (seed) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        double sh, wl;
+        bool mr;
+        long long q[2];
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+          long long j[3] = {ix[0], ix[1], ix[2]};
+          j[d] = seed_map(a, d, ix[d] + (o == 0 ? -1 : 1), sh, mr, wl);
+          q[o] = j[0] + (long long)a.n[0] * (j[1] + (long long)a.n[1] * j[2]);
+        }
+        gr[d] = (double(U[nuo + q[1]]) - double(U[nuo + q[0]])) / (2.0 * a.dx[d]);
+        gn += gr[d] * gr[d];
+      }
+      gn = sqrt(gn);
+      seed = gn * h > 1e-6;
+    }
+    if (!seed) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) out[(long long)k * nc + c] = U[(long long)(L::oX + k) * nc + c];
+      continue;
+    }
+    double cc[3], p[3], f[3];
+    long long i0[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      cc[d] = a.lo[d] + (double(ix[d]) + 0.5) * a.dx[d];
+      p[d] = cc[d] + 1.5 * h * (-gr[d] / gn);
+      const double s = (p[d] - a.lo[d]) / a.dx[d] - 0.5;
+      const double fl = floor(s);
+      i0[d] = (long long)fl;
+      f[d] = s - fl;
+    }
+    double Xi[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int corner = 0; corner < (1 << DIM); ++corner) {
+      long long j[3] = {0, 0, 0};
+      double shift[3] = {0.0, 0.0, 0.0}, wall[3] = {0.0, 0.0, 0.0};
+      bool mirror[3] = {false, false, false};
+      double w = 1.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const int b = (corner >> d) & 1;
+        j[d] = seed_map(a, d, i0[d] + b, shift[d], mirror[d], wall[d]);
+        w *= b ? f[d] : 1.0 - f[d];
+      }
+      const long long q = j[0] + (long long)a.n[0] * (j[1] + (long long)a.n[1] * j[2]);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        double x = double(U[(long long)(L::oX + k) * nc + q]);
+        if (mirror[k]) x = 2.0 * wall[k] - x;
+        Xi[k] += w * (x + shift[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) out[(long long)k * nc + c] = S(Xi[k] - (p[k] - cc[k]));
+  }
+}
+
 // ------------------------------------------------------ init and read ----
 template <class P, int DIM, int NMAT, int NH>
 __global__ void k_init(KArgs a) {

@@ -121,6 +121,13 @@ struct Launch {
         k_frag_mark<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a);
         break;
       }
+      case 9: {
+        if constexpr (Voidable<P>::value)
+          k_seed<P, DIM, NMAT, NH><<<grid_for(a.ncell, 256), 256, 0, s>>>(a);
+        else
+          return cudaErrorInvalidValue;
+        break;
+      }
       case 4: {
         const int g = grid_for(a.ncell, 128 * MM_SRC_BATCHES);
         bool bounded = false;

@@ -80,7 +80,8 @@ class StepInfo(ctypes.Structure):
                 ("steps_done", ctypes.c_int64), ("bad_cell", ctypes.c_int64)]
 
 
-EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport", "mm_step",
+EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport",
+           "mm_set_lagrangian_seeding", "mm_step",
            "mm_step_async", "mm_synchronize",
            "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
@@ -114,6 +115,8 @@ def load(path: str = LIB_PATH):
         lib.mm_step_async.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         lib.mm_set_x_transport.argtypes = [vp, ctypes.c_int]
         lib.mm_set_x_transport.restype = ctypes.c_int
+        lib.mm_set_lagrangian_seeding.argtypes = [vp, ctypes.c_int]
+        lib.mm_set_lagrangian_seeding.restype = ctypes.c_int
         lib.mm_fragments.argtypes = [vp, ctypes.c_double, P(ctypes.c_int64), ctypes.c_size_t,
                                      P(Fragment), ctypes.c_size_t, P(ctypes.c_int64)]
         lib.mm_fragments.restype = ctypes.c_int
@@ -240,6 +243,12 @@ def set_x_transport(grid, scheme: int) -> None:
     _check(load().mm_set_x_transport(grid, int(scheme)))
 
 
+def set_lagrangian_seeding(grid, on: bool) -> None:
+    """Seeding of X into void before each step (Sec. 3.2.1), grids with a
+    void material: on (default) or off."""
+    _check(load().mm_set_lagrangian_seeding(grid, 1 if on else 0))
+
+
 def step_async(grid, n_steps: int, cfl: float) -> None:
     """Enqueue n_steps steps without waiting; in-step failures are reported
     by the next synchronize / step / read_fields."""
@@ -342,6 +351,9 @@ class Grid:
             destroy(self.h)
             self.h = None
             raise
+
+    def set_lagrangian_seeding(self, on: bool) -> None:
+        set_lagrangian_seeding(self.h, on)
 
     def step(self, n_steps: int, cfl: float | None = None) -> dict:
         return step(self.h, n_steps, self.case.cfl if cfl is None else cfl)
