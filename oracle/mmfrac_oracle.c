@@ -84,10 +84,20 @@ typedef struct {
  * shear energy e_s = G J^2 / rho (Eq. shearEnergy); theta = eta^Gamma0 gives
  * a constant Gamma = Gamma0, hence the Mie-Grueneisen form
  *   p = p_ref + rho Gamma (e - e_ref).
+ * Steinberg variant (shear_model 1; Sec. 2.1.2 and the U-Nb closure of
+ * Sec. 4.3, R36): G = psi (G0 + Gp p_c0(rho) eta^(-1/3)), p_c0 the undamaged
+ * cold pressure, and the Debye temperature of Burakovsky and Preston, whose
+ * logarithmic derivative is Gamma(rho) = Gamma0 + Gamma1 eta^(-1/3) +
+ * Gamma2 eta^(-gamma_s); the same Mie-Grueneisen form then holds with
+ * Gamma(rho), and the shear pressure is p_s = rho^2 d e_s/d rho =
+ * J^2 (rho G' - G).  Where the form is negative (strong tension) G = 0.
+ * out[5] = rho Gamma'(rho) / Gamma: the isentropic sound speed of the form
+ *   c^2 = dp_ref/drho + (Gamma + 1 + rho Gamma'/Gamma) (p - p_ref) / rho.
  * Ideal gas is the G = 0 case with e_ref = p_ref = 0, Gamma = gamma - 1.
  */
 void or_thermo(const or_material* m, double rho, double psi, double J2,
                double* out) {
+  out[5] = 0.0;
   if (m->eos == 0) {
     out[0] = 0.0;
     out[1] = 0.0;
@@ -111,6 +121,39 @@ void or_thermo(const or_material* m, double rho, double psi, double J2,
   /* d p_c / d rho = psi K0 eta^(a-1) ((2a-1) eta^a + 1 - a) / (a rho0) */
   const double dpc = psi * m->K0 * pow(eta, a - 1.0) *
                      ((2.0 * a - 1.0) * ea + (1.0 - a)) / (a * m->rho0);
+  if (m->shear_model == 1) {
+    /* Steinberg: G = psi (G0 + Gp q), q = p_c0 u, u = eta^(-1/3), with the
+     * undamaged cold pressure p_c0 and its derivatives
+     *   p_c0'  = K0 E ((2a-1) E + 1 - a) / (a rho),
+     *   p_c0'' = K0 E ((2a-1)^2 E - (a-1)^2) / (a rho^2),  E = eta^a,
+     * and u' = -u / (3 rho), u'' = 4 u / (9 rho^2). */
+    const double pc0 = m->K0 / (2.0 * a * a) * (2.0 * a * q * ea - q * q);
+    const double pc1 = m->K0 * ea * ((2.0 * a - 1.0) * ea + (1.0 - a)) / (a * rho);
+    const double pc2 = m->K0 * ea * ((2.0 * a - 1.0) * (2.0 * a - 1.0) * ea -
+                                     (a - 1.0) * (a - 1.0)) / (a * rho * rho);
+    const double u = pow(eta, -1.0 / 3.0);
+    const double qs = pc0 * u;
+    const double q2 = u * (pc2 - 2.0 * pc1 / (3.0 * rho) + 4.0 * pc0 / (9.0 * rho * rho));
+    const double q1 = u * (pc1 - pc0 / (3.0 * rho));
+    /* the form turns negative in strong tension (p_c < -G0 / Gp eta^(1/3),
+     * about 20 % expansion for U-Nb, where a trace phase in a gas cell can
+     * go): there the material has no shear stiffness, G = G' = G'' = 0 */
+    const int pos = m->G0 + m->Gp * qs > 0.0;
+    const double G = pos ? psi * (m->G0 + m->Gp * qs) : 0.0;
+    const double dG = pos ? psi * m->Gp * q1 : 0.0, d2G = pos ? psi * m->Gp * q2 : 0.0;
+    const double es = G * J2 / rho;
+    const double ps = J2 * (rho * dG - G);
+    const double dps = J2 * rho * d2G;
+    const double g2 = pow(eta, -m->gamma_s);
+    const double Gam = m->Gamma0 + m->Gamma1 * u + m->Gamma2 * g2;
+    out[0] = ec + es;
+    out[1] = pc + ps;
+    out[2] = dpc + dps;
+    out[3] = G;
+    out[4] = Gam;
+    out[5] = (-m->Gamma1 * u / 3.0 - m->gamma_s * m->Gamma2 * g2) / Gam;
+    return;
+  }
   /* shear part: G(rho), e_s = G J2/rho, p_s = rho^2 de_s/drho = beta G J2 */
   const double G = psi * m->G0 * pow(eta, m->beta + 1.0);
   const double es = G * J2 / rho;
@@ -244,7 +287,7 @@ static void vol_fracs(const or_grid* g, const double* w, double phi[]) {
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  double th[OR_MAXMAT][5];
+  double th[OR_MAXMAT][6];
   double xi, Gmix;
   double devH[9], J2;
 } mix_t;
@@ -277,12 +320,14 @@ static int finish_aux(const or_grid* g, const double* phi, const double* rho_l,
     for (int j = 0; j < 3; ++j)
       ax->sig[3 * i + j] =
           (i == j ? -pm : 0.0) + 2.0 * mx->Gmix * mx->devH[3 * i + j];
-  /* frozen mixture sound speed: xi c^2 = sum_l y_l xi_l c_l^2 */
+  /* frozen mixture sound speed: xi c^2 = sum_l y_l xi_l c_l^2, c_l^2 the
+   * isentropic sound speed of material l (with rho Gamma'/Gamma for a
+   * density-dependent Gamma, R36) */
   double s = 0.0;
   for (int l = 0; l < g->nmat; ++l) {
     if (is_void(&g->mat[l])) continue;
     const double Gam = mx->th[l][4];
-    const double cl2 = mx->th[l][2] + (Gam + 1.0) * (ax->p - mx->th[l][1]) /
+    const double cl2 = mx->th[l][2] + (Gam + 1.0 + mx->th[l][5]) * (ax->p - mx->th[l][1]) /
                                           rho_l[l];
     s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;
   }
@@ -1248,7 +1293,7 @@ static int mix_shear(const or_material* mats, int nmat, const double* phi,
   int can_yield = 1;
   *Gmix = 0.0;
   for (int l = 0; l < nmat; ++l) {
-    double th[5];
+    double th[6];
     const double psi = is_damaged(&mats[l]) ? 1.0 - D[l] : 1.0;
     or_thermo(&mats[l], rho[l], psi, 0.0, th);
     *Gmix += phi[l] * th[3];

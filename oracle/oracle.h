@@ -14,7 +14,8 @@
  *   - state and transport equations (Sec. 2.1, Eqs. for phi, phi*rho,
  *     phi*rho*alpha, rho*u, rho*E, the unimodular deformation tensor, X),
  *   - closures: Mie-Grueneisen split with the Romenskii cold energy, the
- *     Romenskii shear modulus, constant Grueneisen coefficient, Hencky strain,
+ *     Romenskii shear modulus with a constant Grueneisen coefficient or the
+ *     Steinberg shear modulus with a density-dependent one, Hencky strain,
  *     shear energy G*J^2/rho, stress -p I + 2 G dev(H) (Sec. 2.1.1, 2.1.2),
  *   - ideal gas as the G=0 special case,
  *   - damage degradation of G and of the cold energy, the Bonora damage rate
@@ -55,6 +56,11 @@ typedef struct {
   double c1, c2, c3, n_hard, edot0;
   int damage;             /* 0 none, 1 Bonora, 2 simple (Ddot0 (1-D) epsdot) */
   double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+  int shear_model;        /* Romenskii solids: 0 Romenskii G = G0 eta^(beta+1) with
+                             constant Gamma0; 1 Steinberg G = G0 + Gp p_c eta^(-1/3)
+                             with Gamma = Gamma0 + Gamma1 eta^(-1/3) + Gamma2
+                             eta^(-gamma_s) (Sec. 2.1.2, Sec. 4.3) */
+  double Gp, Gamma1, Gamma2, gamma_s;
 } or_material;
 
 typedef struct or_grid or_grid;
@@ -105,7 +111,8 @@ long or_fragments(const or_grid* g, double theta, long* labels, long* frag_label
 
 /* ---- single-point routines exported for the pins ---- */
 void or_thermo(const or_material* m, double rho, double psi, double J2,
-               double* out /* e_ref, p_ref, dpref_drho, G, Gamma */);
+               double* out /* e_ref, p_ref, dpref_drho, G, Gamma,
+                              rho Gamma'(rho) / Gamma */);
 int or_hencky(const double F[9], double devH[9], double lam[3], double Q[9]);
 double or_lookup(int dim, const float* phi0, const long pn[3],
                  const double plo[3], const double ph[3], const double X[3]);

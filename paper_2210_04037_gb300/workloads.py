@@ -40,12 +40,14 @@ PHI_MIN = 1e-6
 MATERIAL_KEYS = ("eos", "rho0", "K0", "G0", "alpha", "beta", "Gamma0",
                  "gamma_gas", "plasticity", "c1", "c2", "c3", "n_hard",
                  "edot0", "damage", "D_crit", "eps_t", "eps_c", "alpha_D",
-                 "poisson", "Ddot0")
+                 "poisson", "Ddot0", "shear_model", "Gp", "Gamma1", "Gamma2",
+                 "gamma_s")
+SHEAR_ROMENSKII, SHEAR_STEINBERG = 0, 1
 
 
 def material(**kw) -> Dict[str, float]:
     m = {k: 0.0 for k in MATERIAL_KEYS}
-    m.update(eos=0, plasticity=0, damage=0, edot0=1.0, gamma_gas=1.4)
+    m.update(eos=0, plasticity=0, damage=0, edot0=1.0, gamma_gas=1.4, shear_model=0)
     m.update(kw)
     return m
 
@@ -75,6 +77,22 @@ def al_h32(damage: str = "simple", plastic: bool = True) -> Dict[str, float]:
                  beta=2.28816, Gamma0=1.48389)
     if plastic:
         m.update(plasticity=1, c1=0.275e9, c2=0.114e9, c3=0.002, n_hard=0.42)
+    if damage == "simple" and plastic:
+        m.update(damage=2, Ddot0=0.15, D_crit=0.1)
+    return m
+
+
+def u_nb(damage: str = "simple", plastic: bool = True) -> Dict[str, float]:
+    """U-Nb: the Romenskii cold energy with the Steinberg shear modulus
+    G = G0 + Gp p_c eta^(-1/3) and Gamma = Gamma0 + Gamma1 eta^(-1/3) +
+    Gamma2 eta^(-gamma) (Romenskii-Steinberg row), Johnson-Cook row (no
+    thermal term), the simple damage model of the expanding-ring test
+    (Ddot0 = 0.15, D_crit = 0.1, Sec. 4.3)."""
+    m = material(eos=1, rho0=17411.0, K0=111.27e9, G0=26.34e9, alpha=1.105,
+                 Gamma0=0.5, shear_model=SHEAR_STEINBERG, Gp=1.1226, Gamma1=1.056,
+                 Gamma2=1.068, gamma_s=3.843)
+    if plastic:
+        m.update(plasticity=1, c1=0.780e9, c2=0.253e9, c3=0.012, n_hard=0.22)
     if damage == "simple" and plastic:
         m.update(damage=2, Ddot0=0.15, D_crit=0.1)
     return m
@@ -325,11 +343,13 @@ def spall_1d(ncell: int = 1000, seed: int = 1, sd: float = 0.05,
 
 def ring_2d(n: int = 512, seed: int = 2, a: float = 0.1, v: float = 200.0,
             width: float = 0.064, r0: float = 0.020, r1: float = 0.024,
-            lattice_h: float = 0.0005) -> Case:
-    """2D expanding ring: Al-H32 annulus r0..r1 with radial velocity v in
-    ideal-gas air at rest, 1e5 Pa; simple damage; phi0 ~ U(1-a, 1+a) on a
-    lattice of spacing lattice_h covering the annulus."""
-    mats = [al_h32("simple"), air()]
+            lattice_h: float = 0.0005, solid: Optional[Dict[str, float]] = None,
+            sd: Optional[float] = None) -> Case:
+    """2D expanding ring: Al-H32 (or `solid`) annulus r0..r1 with radial
+    velocity v in ideal-gas air at rest, 1e5 Pa; simple damage; phi0 ~
+    U(1-a, 1+a) (or, with sd given, rectified N(1, sd^2)) on a lattice of
+    spacing lattice_h covering the annulus."""
+    mats = [al_h32("simple") if solid is None else solid, air()]
     half = 0.5 * width
     case = Case("ring_2d", 2, [n, n, 1], [-half, -half, 0], [half, half, 1],
                 [BC_TRANSMISSIVE] * 4, mats, None, cfl=0.6, steps=100)
@@ -343,9 +363,21 @@ def ring_2d(n: int = 512, seed: int = 2, a: float = 0.1, v: float = 200.0,
                    [np.where(inside, v * x / rs, 0.0), np.where(inside, v * y / rs, 0.0)])
     ext = r1 + 2 * lattice_h
     m = int(np.ceil(2 * ext / lattice_h)) + 1
-    case.phi0 = perturbation_uniform(seed, [m, m], a)
+    case.phi0 = (perturbation_uniform(seed, [m, m], a) if sd is None
+                 else perturbation_gaussian(seed, [m, m], sd))
     case.pn, case.plo, case.ph = [m, m, 1], [-ext, -ext, 0], [lattice_h, lattice_h, 1]
     return case
+
+
+def ring_unb_2d(n: int = 256, seed: int = 21, v: float = 210.0) -> Case:
+    """The expanding U-Nb ring of Sec. 4.3 in 2D: the annulus 17.185 ..
+    17.945 mm of U-Nb (Steinberg closure, simple damage) in air on the
+    +-30 mm box, moving radially at v (the driver's first speed; the rigid
+    driver itself is not modelled), phi0 rectified N(1, 0.167^2)."""
+    c = ring_2d(n, seed=seed, v=v, width=0.060, r0=0.017185, r1=0.017945, solid=u_nb("simple"),
+                sd=0.167)
+    c.name = "ring_unb_2d"
+    return c
 
 
 def cylinder_3d(n: int = 256, seed: int = 3, sd: float = 0.1, v: float = 250.0,

@@ -33,13 +33,13 @@ def elastic_cube(n, length, u_of_x, bc=(1, 1), plastic=False, rho_of_x=None):
 
 
 def periodic_mix_2d(n, seed=5, shear=0.003, plastic=True, p0=5e8, dp=5e7,
-                    rho_gas=700.0, vel=5.0, bc=1):
-    """Smooth periodic copper/air mixture under compression (no tension in
-    gas-rich cells, where an ideal-gas phase would have unbounded negative
-    energy), with a shear that yields; drives the mixture, shear and
-    plastic terms."""
+                    rho_gas=700.0, vel=5.0, bc=1, solid=None):
+    """Smooth periodic copper (or `solid`)/air mixture under compression (no
+    tension in gas-rich cells, where an ideal-gas phase would have unbounded
+    negative energy), with a shear that yields; drives the mixture, shear
+    and plastic terms."""
     rng = np.random.default_rng(seed)
-    mats = [W.cube("bonora", plastic=plastic), W.air()]
+    mats = [W.cube("bonora", plastic=plastic) if solid is None else solid, W.air()]
     c = W.Case("mix2d", 2, [n, n, 1], [0, 0, 0], [1e-3, 1e-3, 1], [bc] * 4, mats, None, cfl=0.5)
     lay = c.layout
     c.prim = W.blank_prim(lay, c.ncell)
@@ -47,7 +47,7 @@ def periodic_mix_2d(n, seed=5, shear=0.003, plastic=True, p0=5e8, dp=5e7,
     k = 2 * np.pi / 1e-3
     a = rng.uniform(0.5, 1.5, 4)
     frac = 0.5 + 0.45 * np.sin(k * x + a[0]) * np.cos(k * y + a[1])
-    W.fill_two_phase(c, frac, 8370.0 * (1 + 0.002 * np.cos(k * y)), rho_gas,
+    W.fill_two_phase(c, frac, mats[0]["rho0"] * (1 + 0.002 * np.cos(k * y)), rho_gas,
                      p0 + dp * np.sin(k * x + a[2]),
                      [vel * np.sin(k * y + a[3]), vel * np.cos(k * x)])
     c.prim[lay.F_index(0, 1)] = shear * np.sin(k * x)

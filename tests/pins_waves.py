@@ -171,7 +171,7 @@ def thermal_pressure(case, w, mats):
     lib0 = load()
     lay = case.layout
     out = np.empty(case.ncell)
-    buf = np.zeros(5)
+    buf = np.zeros(6)
     pb = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     structs = [material_struct(m) for m in mats]
     for c in range(case.ncell):

@@ -22,10 +22,10 @@ def _arr(a):
 
 def thermo(m, rho, psi=1.0, J2=0.0):
     lib = load()
-    out, p = _arr(np.zeros(5))
+    out, p = _arr(np.zeros(6))
     ms = material_struct(m)
     lib.or_thermo(ctypes.byref(ms), rho, psi, J2, p)
-    return dict(e=out[0], p=out[1], dp=out[2], G=out[3], Gamma=out[4])
+    return dict(e=out[0], p=out[1], dp=out[2], G=out[3], Gamma=out[4], dlnG=out[5])
 
 
 def hencky(F):
@@ -64,9 +64,10 @@ def test_hencky_matches_matrix_logarithm():
 
 def test_cold_pressure_is_density_derivative_of_cold_energy():
     """p = rho^2 de/drho (Eq. p_energy_derivative) by central differences of
-    the cold + shear energy, for Romenskii CuBe and Al (alpha != 1); and
-    dp/drho by differences of p."""
-    for m in (W.cube(), W.al_h32()):
+    the cold + shear energy, for Romenskii CuBe and Al (alpha != 1) and for
+    U-Nb with the Steinberg shear modulus (whose shear pressure carries
+    G'(rho)); and dp/drho by differences of p."""
+    for m in (W.cube(), W.al_h32(), W.u_nb()):
         for eta in (0.7, 0.95, 1.0, 1.1, 1.4):
             for J2 in (0.0, 1e-4):
                 for psi in (1.0, 0.6):
@@ -92,6 +93,65 @@ def test_linear_moduli_at_reference_density():
         t = thermo(m, m["rho0"], 0.7, 0.0)
         assert t["dp"] * m["rho0"] == pytest.approx(0.7 * m["K0"], rel=1e-14)
         assert t["G"] == pytest.approx(0.7 * m["G0"], rel=1e-14)
+
+
+def test_steinberg_closure_at_reference_and_its_grueneisen_derivative():
+    """U-Nb, Steinberg closure (R36): at rho0 the cold pressure vanishes, so
+    G = G0 and dG/dp_c = Gp; Gamma(rho0) = Gamma0 + Gamma1 + Gamma2; the
+    returned rho Gamma'/Gamma equals the central difference of Gamma."""
+    m = W.u_nb()
+    t = thermo(m, m["rho0"], 1.0, 0.0)
+    assert t["G"] == pytest.approx(m["G0"], rel=1e-14)
+    assert t["dp"] * m["rho0"] == pytest.approx(m["K0"], rel=1e-14)
+    assert t["Gamma"] == pytest.approx(m["Gamma0"] + m["Gamma1"] + m["Gamma2"], rel=1e-14)
+    h = 1e-6 * m["rho0"]
+    tp, tm = thermo(m, m["rho0"] + h), thermo(m, m["rho0"] - h)
+    assert (tp["G"] - tm["G"]) / (tp["p"] - tm["p"]) == pytest.approx(m["Gp"], rel=1e-6)
+    for eta in (0.8, 1.0, 1.3):
+        rho = eta * m["rho0"]
+        h = 1e-6 * rho
+        t0, tp, tm = thermo(m, rho), thermo(m, rho + h), thermo(m, rho - h)
+        dl = rho * (tp["Gamma"] - tm["Gamma"]) / (2 * h) / t0["Gamma"]
+        assert t0["dlnG"] == pytest.approx(dl, rel=1e-7)
+    # a Romenskii solid has a constant Gamma
+    assert thermo(W.cube(), 9000.0)["dlnG"] == 0.0
+
+
+def _one_cell_state(m, rho, e):
+    """A uniform 1D U-Nb grid at rest with density rho and specific internal
+    energy e (F = I): its pressure and its CFL signal speed (c_L at rest)."""
+    c = cases.elastic_cube(4, 1e-3, lambda x: 0 * x)
+    c.materials = [m]
+    lay = c.layout
+    c.prim = W.blank_prim(lay, 4)
+    c.prim[lay.o_rho] = rho
+    c.prim[lay.o_p] = 1e5
+    c.prim[lay.o_X] = c.centres()[0]
+    g = OracleGrid(c)
+    U = g.read(False)
+    U[lay.o_rho] = rho
+    U[lay.o_p] = rho * e
+    g.write_conserved(U)
+    p = g.read()[lay.o_p][0]
+    _, smax = g.cfl_dt()
+    return p, smax
+
+
+def test_steinberg_sound_speed_is_isentropic_derivative():
+    """The closure's sound speed for U-Nb (density-dependent Gamma, R36)
+    equals the isentropic derivative of its pressure, dp/drho along
+    de = p drho / rho^2, by central differences of whole cell states (the
+    shear part 4/3 G/rho removed from c_L^2; F = I)."""
+    m = dict(W.u_nb(), plasticity=0, damage=0)
+    for eta, e in ((1.0, 2e4), (1.12, 5e4), (0.93, 1e4)):
+        rho = eta * m["rho0"]
+        p, cL = _one_cell_state(m, rho, e)
+        G = thermo(m, rho)["G"]
+        d = 1e-4 * rho
+        pp, _ = _one_cell_state(m, rho + d, e + p / rho**2 * d)
+        pm, _ = _one_cell_state(m, rho - d, e - p / rho**2 * d)
+        c2 = (pp - pm) / (2 * d)
+        assert cL**2 - 4 / 3 * G / rho == pytest.approx(c2, rel=1e-6), (eta, e)
 
 
 def test_longitudinal_sound_speed_of_cube_and_air():
