@@ -84,7 +84,13 @@ typedef struct {
  * batches or on the server).  Johnson-Cook yield (c1 + c2 eps^n_hard)
  * max(1, 1 + c3 ln(epsdot/edot0)).  Damage: Bonora (D_crit, eps_t = the
  * threshold strain, eps_c = the critical strain, alpha_D, poisson) or the
- * simple law Ddot = Ddot0 (1-D) epsdot (Sec. 4.3).  SI units. */
+ * simple law Ddot = Ddot0 (1-D) epsdot (Sec. 4.3).  Shear model of a
+ * Romenskii solid: MM_SHEAR_ROMENSKII (G above, constant Gamma0) or
+ * MM_SHEAR_STEINBERG (Sec. 2.1.2 and the U-Nb closure of Sec. 4.3):
+ * G = G0 + Gp p_c eta^(-1/3), p_c the cold pressure, eta = rho/rho0, and
+ * Gamma = Gamma0 + Gamma1 eta^(-1/3) + Gamma2 eta^(-gamma_s) (beta unused);
+ * both degraded by (1 - D) as above.  SI units. */
+enum { MM_SHEAR_ROMENSKII = 0, MM_SHEAR_STEINBERG = 1 };
 typedef struct {
   int eos;
   double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
@@ -92,6 +98,8 @@ typedef struct {
   double c1, c2, c3, n_hard, edot0;
   int damage;
   double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
+  int shear_model;
+  double Gp, Gamma1, Gamma2, gamma_s;
 } mm_material;
 
 /* Initial state: prim = [nfield][ncell] primitive fields in the order above

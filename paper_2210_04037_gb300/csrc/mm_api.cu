@@ -310,6 +310,14 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     if (m.eos == MM_EOS_ROMENSKII &&
         !(m.rho0 > 0 && m.K0 > 0 && m.G0 >= 0 && m.alpha > 0 && m.Gamma0 > 0))
       return fail(MM_EINVAL, "material %d: Romenskii parameters out of range", l);
+    if (m.shear_model != MM_SHEAR_ROMENSKII && m.shear_model != MM_SHEAR_STEINBERG)
+      return fail(MM_EINVAL, "material %d: unknown shear model", l);
+    if (m.shear_model == MM_SHEAR_STEINBERG &&
+        !(m.eos == MM_EOS_ROMENSKII && m.Gp >= 0 && m.gamma_s > 0 &&
+          m.Gamma0 + m.Gamma1 + m.Gamma2 > 0 && m.Gamma0 > 0 && m.Gamma1 >= 0 && m.Gamma2 >= 0))
+      return fail(MM_EINVAL,
+                  "material %d: the Steinberg model takes a Romenskii solid, Gp >= 0, "
+                  "Gamma0 > 0, Gamma1, Gamma2 >= 0, gamma_s > 0", l);
     if (m.plasticity != MM_PL_NONE && m.plasticity != MM_PL_JOHNSON_COOK)
       return fail(MM_EINVAL, "material %d: unknown plasticity model", l);
     if (m.plasticity == MM_PL_JOHNSON_COOK && !(m.c1 >= 0 && m.c2 >= 0 && m.edot0 > 0))
@@ -328,6 +336,11 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     k.eos = m.eos;
     k.plasticity = m.plasticity;
     k.damage = m.damage;
+    k.shear_model = m.eos == MM_EOS_ROMENSKII ? m.shear_model : MM_SHEAR_ROMENSKII;
+    k.Gp = m.Gp;
+    k.Gamma1 = m.Gamma1;
+    k.Gamma2 = m.Gamma2;
+    k.gamma_s = m.gamma_s;
     k.rho0 = m.rho0;
     k.K0 = m.K0;
     k.G0 = m.G0;
@@ -430,6 +443,11 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     f.edot0 = float(k.edot0);
     f.D_crit = float(k.D_crit);
     f.D_cut = float(k.D_cut);
+    f.shear_model = k.shear_model;
+    f.Gp = float(k.Gp);
+    f.Gamma1 = float(k.Gamma1);
+    f.Gamma2 = float(k.Gamma2);
+    f.gamma_s = float(k.gamma_s);
     f.eps_t = float(k.eps_t);
     f.eps_c = float(k.eps_c);
     f.alpha_D = float(k.alpha_D);

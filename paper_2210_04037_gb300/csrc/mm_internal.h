@@ -12,7 +12,7 @@
 // Material constants as the kernels use them (copied from mm_material, plus
 // derived values computed once on the host).
 struct MatK {
-  int eos, plasticity, damage, pad;
+  int eos, plasticity, damage, shear_model;  // shear_model: 0 Romenskii, 1 Steinberg
   double rho0, K0, G0, alpha, beta, Gamma0, gamma_gas;
   double c1, c2, c3, n_hard, edot0;
   double D_crit, eps_t, eps_c, alpha_D, poisson, Ddot0;
@@ -26,6 +26,8 @@ struct MatK {
   // state reads below D_crit by rounding (FP32 storage: about 1e-7 a step)
   // or by a trace of undamaged material mixed in
   double D_cut;
+  // Steinberg shear modulus and Grueneisen function (shear_model 1)
+  double Gp, Gamma1, Gamma2, gamma_s;
 };
 
 // The same constants in FP32 for the FP32-split kernels, which read them as
@@ -43,6 +45,8 @@ struct MatKf {
   float K0_arho0;  // K0 / (alpha rho0)
   float c2n;       // c2 n_hard
   float D_cut;     // the FP64 threshold rounded to FP32
+  int shear_model;
+  float Gp, Gamma1, Gamma2, gamma_s;
 };
 
 // First failure seen on the device (sticky until the host clears it).

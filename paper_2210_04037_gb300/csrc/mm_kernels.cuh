@@ -1280,7 +1280,8 @@ __device__ __forceinline__ void sources_cells(
         if (m.eos == 1 && m.G0 > 0 && m.plasticity != 1) can_yield = false;
         if constexpr (!P::split) {
           R te, tp, tdp, tG;
-          thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG);
+          R tga, tdg;
+          thermo(m, rho[l], m.damage != 0 ? R(1) - Dr[l] : R(1), R(0), te, tp, tdp, tG, tga, tdg);
           Gm += phir[l] * tG;
         }
       }

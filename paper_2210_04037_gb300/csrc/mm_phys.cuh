@@ -125,10 +125,21 @@ struct Lay {
 // dp_ref/drho and G.  Romenskii cold energy psi K0/(2 rho alpha^2)
 // (eta^alpha - 1)^2, G = psi G0 eta^(beta+1), e_s = G J2 / rho, so
 // p_c = psi K0/(2 alpha^2) (2 alpha q eta^alpha - q^2) with q = eta^alpha - 1
-// and p_s = beta G J2.  Ideal gas: all zero.
+// and p_s = beta G J2.  Ideal gas: all zero.  Gam: the Grueneisen
+// coefficient at rho and dlg = rho Gamma'(rho) / Gamma, which enters the
+// isentropic sound speed (zero where Gamma is constant).
+// Steinberg variant (shear_model 1, Sec. 2.1.2 and the U-Nb closure of
+// Sec. 4.3): G = psi (G0 + Gp p_c0 u), p_c0 the undamaged cold pressure,
+// u = eta^(-1/3), so p_s = rho^2 de_s/drho = J2 (rho G' - G) and
+// dp_s/drho = J2 rho G'', from p_c0' = K0 E ((2a-1) E + 1 - a) / (a rho),
+// p_c0'' = K0 E ((2a-1)^2 E - (a-1)^2) / (a rho^2) (E = eta^a),
+// u' = -u / (3 rho), u'' = 4 u / (9 rho^2); Gamma = Gamma0 + Gamma1 u +
+// Gamma2 eta^(-gamma_s).  G = G' = G'' = 0 where G0 + Gp p_c0 u <= 0.
 template <class R>
 __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, R& p,
-                                       R& dp, R& G) {
+                                       R& dp, R& G, R& Gam, R& dlg) {
+  Gam = R(m.Gamma);
+  dlg = R(0);
   if (m.eos != 1) {  // ideal gas or void
     e = R(0); p = R(0); dp = R(0); G = R(0);
     return;
@@ -140,6 +151,28 @@ __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, 
   const R ec = psi * K0 / (R(2) * rho * a * a) * (q * q);
   const R pc = psi * K0 / (R(2) * a * a) * (R(2) * a * q * ea - q * q);
   const R dpc = psi * K0 * mpow(eta, a - R(1)) * ((R(2) * a - R(1)) * ea + (R(1) - a)) / (a * rho0);
+  if (m.shear_model == 1) {
+    const R pc0 = K0 / (R(2) * a * a) * (R(2) * a * q * ea - q * q);
+    const R pc1 = K0 * ea * ((R(2) * a - R(1)) * ea + (R(1) - a)) / (a * rho);
+    const R pc2 = K0 * ea * ((R(2) * a - R(1)) * (R(2) * a - R(1)) * ea -
+                             (a - R(1)) * (a - R(1))) / (a * rho * rho);
+    const R u = mpow(eta, R(-1.0 / 3.0));
+    const R qs = pc0 * u;
+    const R q2 = u * (pc2 - R(2) * pc1 / (R(3) * rho) + R(4) * pc0 / (R(9) * rho * rho));
+    const R q1 = u * (pc1 - pc0 / (R(3) * rho));
+    // no shear stiffness where the form turns negative (strong tension)
+    const bool pos = R(m.G0) + R(m.Gp) * qs > R(0);
+    const R Gs = pos ? psi * (R(m.G0) + R(m.Gp) * qs) : R(0);
+    const R dG = pos ? psi * R(m.Gp) * q1 : R(0), d2G = pos ? psi * R(m.Gp) * q2 : R(0);
+    e = ec + Gs * J2 / rho;
+    p = pc + J2 * (rho * dG - Gs);
+    dp = dpc + J2 * rho * d2G;
+    G = Gs;
+    const R g2 = mpow(eta, -R(m.gamma_s));
+    Gam = R(m.Gamma0) + R(m.Gamma1) * u + R(m.Gamma2) * g2;
+    dlg = (-R(m.Gamma1) * u / R(3) - R(m.gamma_s) * R(m.Gamma2) * g2) / Gam;
+    return;
+  }
   const R Gs = psi * R(m.G0) * mpow(eta, bb + R(1));
   e = ec + Gs * J2 / rho;
   p = pc + bb * Gs * J2;
@@ -151,7 +184,9 @@ __device__ __forceinline__ void thermo(const MatK& m, R rho, R psi, R J2, R& e, 
 // eta^(alpha-1) = eta^alpha / eta, and the precomputed K0/(2 alpha^2) and
 // K0/(alpha rho0) in place of divisions.
 __device__ __forceinline__ void thermo(const MatKf& m, float rho, float psi, float J2, float& e,
-                                       float& p, float& dp, float& G) {
+                                       float& p, float& dp, float& G, float& Gam, float& dlg) {
+  Gam = m.Gamma;
+  dlg = 0.f;
   if (m.eos != 1) {  // ideal gas or void
     e = 0.f; p = 0.f; dp = 0.f; G = 0.f;
     return;
@@ -165,6 +200,26 @@ __device__ __forceinline__ void thermo(const MatKf& m, float rho, float psi, flo
   const float ec = k2 * ir * (q * q);
   const float pc = k2 * (2.f * a * q * ea - q * q);
   const float dpc = psi * m.K0_arho0 * (ea * m.rho0 * ir) * ((2.f * a - 1.f) * ea + (1.f - a));
+  if (m.shear_model == 1) {  // Steinberg, as in the FP64 closure
+    const float pc0 = m.K0_2a2 * (2.f * a * q * ea - q * q);
+    const float pc1 = m.K0 * ea * ((2.f * a - 1.f) * ea + (1.f - a)) * ir / a;
+    const float pc2 = m.K0 * ea * ((2.f * a - 1.f) * (2.f * a - 1.f) * ea - (a - 1.f) * (a - 1.f)) *
+                      (ir * ir) / a;
+    const float u = mpow(eta, -1.f / 3.f);
+    const float q1 = u * (pc1 - pc0 * ir * (1.f / 3.f));
+    const float q2 = u * (pc2 - 2.f * pc1 * ir * (1.f / 3.f) + 4.f * pc0 * (ir * ir) * (1.f / 9.f));
+    const float g0 = m.G0 + m.Gp * pc0 * u;
+    const float gp = g0 > 0.f ? psi * m.Gp : 0.f;  // G = 0 where the form is negative
+    const float Gs = g0 > 0.f ? psi * g0 : 0.f;
+    e = ec + Gs * J2 * ir;
+    p = pc + J2 * (rho * gp * q1 - Gs);
+    dp = dpc + J2 * rho * gp * q2;
+    G = Gs;
+    const float g2 = mpow(eta, -m.gamma_s);
+    Gam = m.Gamma0 + m.Gamma1 * u + m.Gamma2 * g2;
+    dlg = (-m.Gamma1 * u * (1.f / 3.f) - m.gamma_s * m.Gamma2 * g2) / Gam;
+    return;
+  }
   const float Gs = psi * m.G0 * mpow(eta, bb + 1.f);
   const float gj = Gs * J2;
   e = ec + gj * ir;
@@ -482,10 +537,11 @@ struct Phys {
   }
 
   // Mixture quantities of the isobaric Allaire closure with one deformation
-  // tensor: per-material e_ref, p_ref, dp_ref, and xi = sum phi_l/Gamma_l,
-  // G_mix = sum phi_l G_l.
+  // tensor: per-material e_ref, p_ref, dp_ref, Gamma_l and 1/Gamma_l at the
+  // phase density (constant but for the Steinberg closure) with
+  // rho Gamma'/Gamma, and xi = sum phi_l/Gamma_l, G_mix = sum phi_l G_l.
   struct Mix {
-    R e[NMAT], p[NMAT], dp[NMAT];
+    R e[NMAT], p[NMAT], dp[NMAT], ga[NMAT], gi[NMAT], dg[NMAT];
     R xi, Gm, J2;
     R devH[9];
   };
@@ -507,12 +563,14 @@ struct Phys {
       const auto& m = matp<R>(a, l);
       const R psi = m.damage != 0 ? R(1) - D[l] : R(1);
       R G;
-      thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G);
+      thermo(m, rho[l], psi, mx.J2, mx.e[l], mx.p[l], mx.dp[l], G, mx.ga[l], mx.dg[l]);
+      // 1/Gamma_l: the host's constant, or its value at rho_l (Steinberg)
+      mx.gi[l] = m.shear_model == 1 ? R(1) / mx.ga[l] : R(m.xi);
       if (isvoid(a, l)) continue;  // no part in the pressure equilibrium
       if constexpr (P::split)
-        mx.xi += phi[l] * m.xi;
+        mx.xi += phi[l] * mx.gi[l];
       else
-        mx.xi += phi[l] / R(m.Gamma);
+        mx.xi += phi[l] / mx.ga[l];
       mx.Gm += phi[l] * G;
     }
     return true;
@@ -520,7 +578,7 @@ struct Phys {
 
   // sigma = -p I + 2 G_mix dev(H); c_L^2 = c^2 + 4/3 G_mix/rho with the
   // frozen mixture speed xi c^2 = sum y_l xi_l c_l^2,
-  // c_l^2 = dp_ref,l + (Gamma_l + 1)(p - p_ref,l)/rho_l.
+  // c_l^2 = dp_ref,l + (Gamma_l + 1 + rho Gamma_l'/Gamma_l)(p - p_ref,l)/rho_l.
   template <int AX>
   __device__ static __forceinline__ bool finish(const KArgs& a, R p, const R rho[NMAT],
                                                 const R arho[NMAT], const Mix& mx, Aux<R>& ax,
@@ -538,10 +596,10 @@ struct Phys {
 #pragma unroll
     for (int l = 0; l < NMAT; ++l) {
       if (isvoid(a, l)) continue;
-      const R Gam = R(matp<R>(a, l).Gamma);
-      const R cl2 = mx.dp[l] + (Gam + R(1)) * (p - mx.p[l]) / rho[l];
+      const R Gam = mx.ga[l];
+      const R cl2 = mx.dp[l] + (Gam + R(1) + mx.dg[l]) * (p - mx.p[l]) / rho[l];
       if constexpr (P::split)
-        s += (arho[l] / ax.rho) * matp<R>(a, l).xi * cl2;
+        s += (arho[l] / ax.rho) * mx.gi[l] * cl2;
       else
         s += (arho[l] / ax.rho) * (R(1) / Gam) * cl2;
     }
@@ -596,7 +654,7 @@ struct Phys {
       R re = R(0);
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
-        if (!isvoid(a, l)) re += arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * (p - mx.p[l]);
+        if (!isvoid(a, l)) re += arho[l] * mx.e[l] + phi[l] * mx.gi[l] * (p - mx.p[l]);
       const R kef = R(0.5) * ax.rho * (ax.u[0] * ax.u[0] + ax.u[1] * ax.u[1] + ax.u[2] * ax.u[2]);
       // the FP32 sum equals the FP64 sum rounded to FP32 (double rounding is
       // exact for one addition); the FP64 total is formed only when asked for
@@ -609,7 +667,7 @@ struct Phys {
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
         if (!isvoid(a, l))
-          rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(a.mat[l].Gamma);
+          rhoe += E(arho[l] * mx.e[l]) + E(phi[l]) * (pE - E(mx.p[l])) / E(mx.ga[l]);
       ke = 0.5 * E(ax.rho) *
            (E(ax.u[0]) * E(ax.u[0]) + E(ax.u[1]) * E(ax.u[1]) + E(ax.u[2]) * E(ax.u[2]));
     }
@@ -698,7 +756,7 @@ struct Phys {
       R num = rhoE_d ? R(*rhoE_d - E(ke)) : R(cx[0]) - ke;
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
-        if (!isvoid(a, l)) num += -arho[l] * mx.e[l] + phi[l] * matp<R>(a, l).xi * mx.p[l];
+        if (!isvoid(a, l)) num += -arho[l] * mx.e[l] + phi[l] * mx.gi[l] * mx.p[l];
       pE = E(num / mx.xi);
     } else {
       const E ke = 0.5 * E(ax.rho) *
@@ -706,7 +764,7 @@ struct Phys {
       E num = (rhoE_d ? *rhoE_d : E(cx[0])) - ke;
 #pragma unroll
       for (int l = 0; l < NMAT; ++l)
-        if (!isvoid(a, l)) num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(a.mat[l].Gamma);
+        if (!isvoid(a, l)) num += -E(arho[l] * mx.e[l]) + E(phi[l]) * E(mx.p[l]) / E(mx.ga[l]);
       pE = num / E(mx.xi);
     }
 #pragma unroll

@@ -49,7 +49,10 @@ class Material(ctypes.Structure):
                 ("c3", ctypes.c_double), ("n_hard", ctypes.c_double), ("edot0", ctypes.c_double),
                 ("damage", ctypes.c_int), ("D_crit", ctypes.c_double), ("eps_t", ctypes.c_double),
                 ("eps_c", ctypes.c_double), ("alpha_D", ctypes.c_double),
-                ("poisson", ctypes.c_double), ("Ddot0", ctypes.c_double)]
+                ("poisson", ctypes.c_double), ("Ddot0", ctypes.c_double),
+                ("shear_model", ctypes.c_int), ("Gp", ctypes.c_double),
+                ("Gamma1", ctypes.c_double), ("Gamma2", ctypes.c_double),
+                ("gamma_s", ctypes.c_double)]
 
 
 class Init(ctypes.Structure):

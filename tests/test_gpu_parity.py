@@ -71,6 +71,13 @@ PARITY_CASES = {
     # cells along x): the z sweep carries the in-plane shear
     "mix_2d_in_yz_plane_3d": (lambda: cases.embed_3d(cases.periodic_mix_2d(14, seed=3, shear=0.03),
                                                      (1, 2))[0], 60),
+    # U-Nb with the Steinberg shear modulus and density-dependent Gamma
+    # (R36): the compressed periodic mixture with yielding shear, and the
+    # U-Nb ring of the expanding-ring test over its horizon (the oracle
+    # against itself from a 1e-15 perturbation: 6e-11 at 20 steps)
+    "steinberg_mix_2d_50": (lambda: cases.periodic_mix_2d(50, shear=0.03, solid=W.u_nb("simple")),
+                            100),
+    "steinberg_ring_unb_2d_256": (lambda: W.ring_unb_2d(256), 20),
 }
 
 
@@ -98,6 +105,18 @@ def test_fp64_matches_oracle(name):
     assert info["steps"] == steps
     assert info["t"] == pytest.approx(oinfo["t"], rel=1e-12)
     assert np.allclose(tot, otot, rtol=1e-12, atol=1e-12 * np.abs(otot).max())
+
+
+def test_fp32_split_steinberg_against_oracle():
+    """FP32-split with the Steinberg closure (R36) against the FP64 oracle
+    on the smooth U-Nb/air mixture: relative L1 <= 1e-3 per field after 100
+    steps."""
+    case = cases.periodic_mix_2d(50, shear=0.01, vel=2.0, solid=W.u_nb("simple"))
+    out, info, tot, ref, oinfo, otot, T0, G0 = run_both(case, 100, mmfrac.FP32_SPLIT)
+    r = rel_l1(out, ref)
+    names = case.layout.names()
+    worst = int(np.argmax(r))
+    assert r.max() <= 1e-3, f"{names[worst]}: rel L1 {r[worst]:.3e}"
 
 
 def test_uniform_state_is_bitwise_preserved_on_gpu():

@@ -1,8 +1,11 @@
 """Served runs with continuous batching through the C ABI: a run's result is
 the same as the same grid stepped alone, whatever was served beside it (FP32-
 split: to 1e-4 relative L1 per field, since the batched and single-grid
-kernels may differ in FMA contraction; in practice the bits agree);
-admission follows the memory budget; bounded waits time out."""
+kernels may differ in FMA contraction; the momentum components and the
+off-diagonal Fbar components against the L1 norm of their group, as in the
+batch tests: the cylinder's axial momentum is 1e-3 of the total and grows
+from rounding in the chaotic diffuse zone); admission follows the memory
+budget; bounded waits time out."""
 import time
 
 import numpy as np
@@ -13,10 +16,18 @@ from paper_2210_04037_gb300 import mmfrac, workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def same_state(u, ref):
+def same_state(u, ref, lay):
     num = np.abs(u - ref).sum(axis=1)
     den = np.abs(ref).sum(axis=1)
-    return bool(np.all(num <= 1e-4 * np.where(den > 0, den, 1.0)))
+    mom = list(range(lay.o_u, lay.o_u + lay.dim))
+    off = [lay.F_index(i, j) for i in range(3) for j in range(3)
+           if i != j and lay.F_index(i, j) is not None]
+    for group in (mom, off):
+        if group:
+            den[group] = den[group].sum()
+    r = num / np.where(den > 0, den, 1.0)
+    k = int(np.argmax(r))
+    return bool(r[k] <= 1e-4), f"{lay.names()[k]}: {r[k]:.3e}"
 
 
 def alone(case, steps, prec=mmfrac.FP32_SPLIT):
@@ -43,7 +54,8 @@ def test_served_mix_equals_runs_alone():
         assert info["steps_done"] == n
         assert info["t"] == pytest.approx(rinfo["t"], rel=1e-6)
         assert info["submit_s"] <= info["admit_s"] <= info["done_s"]
-        assert same_state(out, ref), case.name
+        ok, worst = same_state(out, ref, case.layout)
+        assert ok, (case.name, worst)
     st = srv.stats()
     assert st["used_bytes"] == 0 and st["pending"] == 0
     assert st["admitted"] == st["retired"] == len(ids)
@@ -58,7 +70,8 @@ def test_memory_budget_serves_one_run_at_a_time():
     for rid, case in zip(ids, cases):
         info, out = srv.wait(rid, timeout=120)
         infos.append(info)
-        assert same_state(out, alone(case, 8)[0])
+        ok, worst = same_state(out, alone(case, 8)[0], case.layout)
+        assert ok, (case.name, worst)
     for a, b in zip(infos, infos[1:]):
         assert b["admit_s"] >= a["done_s"]
     with pytest.raises(mmfrac.MMError) as e:
