@@ -458,11 +458,73 @@ def run_fragments(args, rank: int, world: int):
                                 "kind": "oracle",
                                 "sample": f"one labelling of the full {case.ncell}-cell workload "
                                           f"({el:.1f} s wall, single-threaded search)"}
+    if not args.no_extra:
+        line["self_fractured"] = run_self_fractured(args, prec, stream, calls, dist, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+SELF_FRACTURED_N = 1024
+
+
+def run_self_fractured(args, prec, stream, calls, dist, rank, world):
+    """Fragment labelling on a state the step itself fractured: the
+    expanding CuBe plate (workloads.expanding_plate, 1024^2, a void material
+    beside it) stepped on the GPU until it has broken into fragments (not
+    timed), then `calls` labellings timed with CUDA events, L2 flushed
+    between them; the labels checked against the oracle's labelling of the
+    same state."""
+    import torch
+    from paper_2210_04037_gb300 import mmfrac
+    case = W.expanding_plate(SELF_FRACTURED_N)
+    g = mmfrac.Grid(case, prec, stream=stream.cuda_stream)
+    steps, nfrag = 0, 1
+    while steps < 12000 and nfrag < 8:
+        g.step(250)
+        steps += 250
+        nfrag = g.fragments(FRAG_CUT, labels=False, max_frags=0)[1]["n"]
+    info = g.synchronize()
+    lab, f = g.fragments(FRAG_CUT, labels=True, max_frags=0)
+    flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    start = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    stop = [torch.cuda.Event(enable_timing=True) for _ in range(calls)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(calls):
+        flush.add_(1)
+        start[s].record(stream)
+        g.fragments(FRAG_CUT, labels=False, max_frags=0)
+        stop[s].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(start, stop)), dist)
+    U = g.read(primitive=False)
+    g.close()
+    out = {"workload": f"CuBe plate 1 mm, {SELF_FRACTURED_N}^2 cells, stretched in-plane at "
+                       f"2e5/s (workloads.expanding_plate), fractured by {steps} steps of its "
+                       f"own ({args.precision}, t = {info['t'] * 1e6:.2f} us)",
+           "cells": case.ncell, "steps_to_fracture": steps, "fragments": f["n"],
+           "member_fraction": float((lab >= 0).mean()),
+           "value": world * case.ncell * calls / (ms * 1e-3), "unit": "cells/s",
+           "ms_per_call": ms / calls, "l2": "flushed between calls (256 MiB write)"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import OracleGrid
+        o = OracleGrid(case)
+        o.write_conserved(U)
+        t0 = time.perf_counter()
+        olab, of = o.fragments(FRAG_CUT)
+        el = time.perf_counter() - t0
+        # (the FP32-split state stores every volume fraction; the oracle forms
+        # the last as 1 - sum, so a cell within FP32 rounding of the cut-off
+        # can fall on the other side)
+        out["oracle_fragments"] = of["n"]
+        out["cells_labelled_differently_from_oracle"] = int((olab != lab).sum())
+        out["cpu_baseline"] = {"value": case.ncell / el, "unit": "cells/s", "cores": 1,
+                               "kind": "oracle", "sample": "one labelling of the same state"}
+    return out
 
 
 def time_device(case, precision, steps, warmup, stream, flush_buf, profile=True, x_transport=0):

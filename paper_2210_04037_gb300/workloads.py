@@ -460,6 +460,51 @@ def add_void(case: Case, index: int = 1) -> Case:
     return out
 
 
+def expanding_plate(n: int = 512, dim: int = 2, rate: float = 2e5, L: float = 1e-3,
+                    sd: float = 0.1, seed: int = 7, lattice_h: float = 2e-5,
+                    nz: Optional[int] = None) -> Case:
+    """A CuBe plate (Bonora damage) stretched in its plane at the strain rate
+    `rate`, u = rate (x, y) (and u_z = 0 in 3D, nz cells thick, periodic in
+    z), with a void material beside it (no void yet) and the yield stress
+    perturbed by phi0 ~ rectified N(1, sd^2) on a lattice of spacing
+    lattice_h; transmissive in x and y.  The stretch yields the plate, damage
+    grows where the perturbed strength is low, and the void opens along the
+    cracks that join them (Sec. 3.1): a state the step itself fractures, as
+    in the expanding-disk and ring tests of Sec. 4.2 and 4.3.  The plate is
+    L wide (n cells); at 64 cells on 1 mm the first cracks open within about
+    200 steps, and the steps to fracture grow with n at a fixed L."""
+    mats = [void(), cube("bonora")]
+    dx = L / n
+    half = 0.5 * L
+    nz_ = (nz if nz is not None else 4) if dim == 3 else 1
+    hz = 0.5 * nz_ * dx
+    bc = [BC_TRANSMISSIVE] * 4 + ([BC_PERIODIC] * 2 if dim == 3 else [])
+    case = Case("expanding_plate", dim, [n, n, nz_], [-half, -half, -hz if dim == 3 else 0],
+                [half, half, hz if dim == 3 else 1], bc, mats, None, cfl=0.6, steps=300)
+    lay = case.layout
+    case.prim = blank_prim(lay, case.ncell)
+    cen = case.centres()
+    case.prim[lay.o_phi] = 0.0
+    case.prim[lay.o_rho] = 0.0
+    case.prim[lay.o_rho + 1] = mats[1]["rho0"]
+    case.prim[lay.o_u] = rate * cen[0]
+    case.prim[lay.o_u + 1] = rate * cen[1]
+    case.prim[lay.o_p] = 1.0e5
+    for d in range(dim):
+        case.prim[lay.o_X + d] = cen[d]
+    m = int(np.ceil(L / lattice_h)) + 3
+    ext = half + lattice_h
+    if dim == 2:
+        case.phi0 = perturbation_gaussian(seed, [m, m], sd)
+        case.pn, case.plo, case.ph = [m, m, 1], [-ext, -ext, 0], [lattice_h, lattice_h, 1]
+    else:
+        mz = int(np.ceil(2 * hz / lattice_h)) + 3
+        case.phi0 = perturbation_gaussian(seed, [m, m, mz], sd)
+        case.pn, case.plo = [m, m, mz], [-ext, -ext, -hz - lattice_h]
+        case.ph = [lattice_h] * 3
+    return case
+
+
 def fractured_ring(n: int = 512, cracks: int = 12, seed: int = 11, **kw) -> Case:
     """The expanding-ring geometry at fragmentation (Sec. 4.3), input for
     fragment labelling: the annulus cut by `cracks` radial cracks of
