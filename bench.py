@@ -55,7 +55,7 @@ WORKLOAD_TEXT = {
                 "target, Bonora damage, phi0 ~ rectified N(1,0.05^2) per cell",
     "ensemble_2d": "batched ensemble: {n} seeded 2D expanding rings (the ring workload, seeds "
                    "100..), grids uneven 128^2..768^2 in steps of 8, stepped together: one launch "
-                   "per kernel kind over all members, CUDA graph replay, autotuned tile shapes",
+                   "per kernel kind over all members, CUDA graph replay, autotuned tile shapes and persistent CTAs per SM",
     "serve": "served runs: {n} requests with Poisson arrivals (16/s, seeded) mixing 1D spall "
              "(1e3..1e4 cells, 400 steps), 2D ring (256^2..1024^2, 60 steps) and 3D cylinder "
              "(128^3..256^3, 10 steps), FP32-split, memory-based admission, continuous batching",
@@ -594,8 +594,11 @@ def run_ensemble(args, rank: int, world: int, nested: bool = False, dist=None):
     grids = [mmfrac.Grid(c, prec, stream=stream.cuda_stream) for c in members]
     b = mmfrac.Batch(grids, stream=stream.cuda_stream)
     b.step(args.warmup)
-    chosen = b.autotune(reps=3)
-    b.step(1)  # captures the step with the chosen tiles
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        tune = b.autotune(reps=3, cache=os.path.join(td, "tune.txt"))
+    chosen = tune["variant"]
+    b.step(1)  # captures the step with the chosen launch configurations
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -654,7 +657,7 @@ def run_ensemble(args, rank: int, world: int, nested: bool = False, dist=None):
         "dtype": "f32+f64" if prec == W.FP32_SPLIT else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT["ensemble_2d"].format(n=m), "members": m,
                    "cells": ncell, "precision": args.precision,
-                   "tile_variants": chosen[:2],
+                   "tile_variants": chosen[:2], "cta_per_sm": tune["cta_per_sm"][:2],
                    "l2": "state larger than L2", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

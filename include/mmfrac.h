@@ -252,11 +252,31 @@ mm_status mm_batch_set_options(mm_batch* b, int use_graph, const int tile_varian
  * and returned by mm_batch_synchronize.  Errors: MM_EINVAL, MM_ECUDA. */
 mm_status mm_batch_step(mm_batch* b, int n_steps, double cfl);
 
-/* Time each tile shape of each sweep axis on the batch's current states
- * (reps timed launches after one warm-up; a sweep into the free buffer
- * leaves the state unchanged), keep the fastest, and return the choice in
- * chosen (may be NULL).  Blocks.  Errors: MM_EINVAL, MM_ECUDA. */
+/* Time each launch configuration of each sweep axis on the batch's current
+ * states (reps timed launches after one warm-up; a sweep into the free
+ * buffer leaves the state unchanged), keep the fastest, and return the
+ * chosen tile shapes in chosen (may be NULL).  The configurations: the
+ * compiled tile shapes (FP32-split: 2 per axis; FP64: 1) times the
+ * persistent CTAs per SM (as many as fit, 1, 2).  Blocks.  Errors:
+ * MM_EINVAL, MM_ECUDA. */
 mm_status mm_batch_autotune(mm_batch* b, int reps, int chosen[3]);
+
+/* The same search with a persistent choice.  The batch's size class is
+ * log2 of its median member cell count; the cache key is the device (name
+ * and SM count), precision, dimension, material layout and size class.
+ * With cache_path non-NULL and force 0, a choice cached under the key is
+ * taken without timing; otherwise the search runs and its choice is
+ * appended to the file (plain text, one line per key, the last line for a
+ * key wins; not locked against other processes).  out (may be NULL)
+ * receives the choice. */
+typedef struct {
+  int variant[3];     /* tile shape per sweep axis */
+  int cta_per_sm[3];  /* persistent CTAs per SM per sweep axis (0: as many as fit) */
+  int from_cache;     /* 1: read from the cache, 0: timed */
+  int size_class;     /* log2 of the median member cell count */
+} mm_tune;
+mm_status mm_batch_autotune_ex(mm_batch* b, int reps, const char* cache_path, int force,
+                               mm_tune* out);
 
 /* Wait for the batch's work and report the first failure latched by a
  * member (its index in the message).  Errors as mm_step. */

@@ -2,6 +2,7 @@
 // the step driver loop (dt stays on the device), read-back and totals.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -933,6 +934,8 @@ struct mm_batch {
   unsigned long long* counter = nullptr;  // [8] work counters of one step
   std::vector<long long> h_tstart, h_cstart;
   int variant[3] = {0, 0, 0};
+  int cps[3] = {0, 0, 0};  // persistent sweep CTAs per SM per axis (0: as many as fit)
+  int cps_src = 0;         // the same for the source kernel
   int parity = 0;  // flips with every sweep: the members' buffers relative to creation
   int use_graph = 1;
   bool warmed = false;
@@ -975,6 +978,7 @@ BatchK batch_k(const mm_batch* b, int phase, const long long* start, long long t
   k.total = total;
   k.chunk = kChunk;
   k.M = b->M;
+  k.cta_per_sm = 0;
   return k;
 }
 
@@ -998,13 +1002,16 @@ cudaError_t batch_enqueue(mm_batch* b, double cfl) {
     const int v = b->variant[d];
     const size_t o = (size_t)(d * 2 + v) * (M + 1);
     prof_begin(b, MM_K_SWEEP_X + d);
-    e = L(1, d, v, b->nmat, b->nhist, batch_k(b, 1 + d, b->tstart + o, b->h_tstart[o + M]),
-          b->stream);
+    BatchK k = batch_k(b, 1 + d, b->tstart + o, b->h_tstart[o + M]);
+    k.cta_per_sm = b->cps[d];
+    e = L(1, d, v, b->nmat, b->nhist, k, b->stream);
     prof_end(b);
     if (e != cudaSuccess) return e;
   }
   prof_begin(b, MM_K_SOURCES);
-  e = L(2, 0, 0, b->nmat, b->nhist, batch_k(b, 4, b->cstart, b->h_cstart[M]), b->stream);
+  BatchK ks = batch_k(b, 4, b->cstart, b->h_cstart[M]);
+  ks.cta_per_sm = b->cps_src;
+  e = L(2, 0, 0, b->nmat, b->nhist, ks, b->stream);
   prof_end(b);
   return e;
 }
@@ -1161,47 +1168,154 @@ mm_status mm_batch_step(mm_batch* b, int n_steps, double cfl) {
   return MM_OK;
 }
 
-mm_status mm_batch_autotune(mm_batch* b, int reps, int chosen[3]) {
-  if (!b) return fail(MM_EINVAL, "mm_batch_autotune: null batch");
-  if (reps < 1) reps = 1;
-  batch_launcher L = batch_launch_of(b->prec, b->dim);
-  const int M = b->M;
-  cudaEvent_t e0, e1;
-  CUDA_TRY(cudaEventCreate(&e0));
-  CUDA_TRY(cudaEventCreate(&e1));
-  for (int d = 0; d < b->dim; ++d) {
-    float best = -1.f;
-    for (int v = 0; v < (b->prec == MM_FP64 ? 1 : 2); ++v) {
-      const size_t o = (size_t)(d * 2 + v) * (M + 1);
-      // a sweep from the current state into the free buffer (phase 1 of the
-      // current parity) leaves the state as it is: it can be timed freely
-      const BatchK k = batch_k(b, 1, b->tstart + o, b->h_tstart[o + M]);
-      float ms = 0.f;
-      for (int r = -1; r < reps; ++r) {
-        CUDA_TRY(cudaMemsetAsync(b->counter + 1, 0, sizeof(unsigned long long), b->stream));
-        CUDA_TRY(cudaEventRecord(e0, b->stream));
-        CUDA_TRY(L(1, d, v, b->nmat, b->nhist, k, b->stream));
-        CUDA_TRY(cudaEventRecord(e1, b->stream));
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float t = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
-        if (r >= 0) ms += t;  // r = -1 warms up
+namespace {
+
+// Size class of a batch: log2 of its median member cell count.
+int batch_size_class(const mm_batch* b) {
+  std::vector<long long> n;
+  for (const mm_grid* g : b->m) n.push_back(g->ncell);
+  std::sort(n.begin(), n.end());
+  const long long med = n[n.size() / 2];
+  int c = 0;
+  while ((2LL << c) <= med) ++c;
+  return c;
+}
+
+// Cache key: the device, precision, dimension, material layout and size
+// class of a batch.
+std::string tune_key(const mm_batch* b, int size_class) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  std::string name = "unknown";
+  int sms = 0;
+  if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) {
+    name = p.name;
+    sms = p.multiProcessorCount;
+  }
+  for (char& ch : name)
+    if (ch == ' ' || ch == '|') ch = '_';
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s|%d|%s|%d|%d|%d|%d", name.c_str(), sms,
+                b->prec == MM_FP64 ? "fp64" : "fp32split", b->dim, b->nmat, b->nhist, size_class);
+  return buf;
+}
+
+// The cached choice for key: tile variant and CTAs per SM per axis.
+bool tune_read(const char* path, const std::string& key, int v[3], int c[3]) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    char k[300];
+    int a[6];
+    if (std::sscanf(line, "%299s %d %d %d %d %d %d", k, &a[0], &a[1], &a[2], &a[3], &a[4],
+                    &a[5]) == 7 &&
+        key == k) {
+      for (int d = 0; d < 3; ++d) {
+        v[d] = a[d];
+        c[d] = a[3 + d];
       }
-      if (best < 0.f || ms < best) {
-        best = ms;
-        b->variant[d] = v;
-      }
+      found = true;  // the last line for a key wins
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  batch_drop_graphs(b);
-  if (chosen)
-    for (int d = 0; d < 3; ++d) chosen[d] = b->variant[d];
-  for (mm_grid* g : b->m) {
-    mm_status st = check_device_error(g, "mm_batch_autotune");
-    if (st != MM_OK) return st;
+  std::fclose(f);
+  return found;
+}
+
+// Appends the choice for key (a later line for the same key overrides).
+bool tune_write(const char* path, const std::string& key, const int v[3], const int c[3]) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return false;
+  std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], c[0], c[1], c[2]);
+  return std::fclose(f) == 0;
+}
+
+}  // namespace
+
+mm_status mm_batch_autotune_ex(mm_batch* b, int reps, const char* cache_path, int force,
+                               mm_tune* out) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_autotune_ex: null batch");
+  if (reps < 1) reps = 1;
+  const int cls = batch_size_class(b);
+  const std::string key = tune_key(b, cls);
+  int from_cache = 0;
+  int v[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+  if (cache_path && !force && tune_read(cache_path, key, v, c)) {
+    bool ok = true;
+    for (int d = 0; d < 3; ++d)
+      ok = ok && (v[d] == 0 || (v[d] == 1 && b->prec != MM_FP64)) && c[d] >= 0 && c[d] <= 64;
+    if (ok) from_cache = 1;
   }
+  if (!from_cache) {
+    // search: tile variant x persistent CTAs per SM (as many as fit, 1, 2)
+    // per sweep axis, each timed as a sweep from the current state into the
+    // free buffer (phase 1 of the current parity), which leaves the state
+    // as it is
+    batch_launcher L = batch_launch_of(b->prec, b->dim);
+    const int M = b->M;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int cps_options[3] = {0, 1, 2};
+    for (int d = 0; d < b->dim; ++d) {
+      float best = -1.f;
+      for (int vv = 0; vv < (b->prec == MM_FP64 ? 1 : 2); ++vv) {
+        for (int ci = 0; ci < 3; ++ci) {
+          const size_t o = (size_t)(d * 2 + vv) * (M + 1);
+          BatchK k = batch_k(b, 1, b->tstart + o, b->h_tstart[o + M]);
+          k.cta_per_sm = cps_options[ci];
+          float ms = 0.f;
+          for (int r = -1; r < reps; ++r) {
+            CUDA_TRY(cudaMemsetAsync(b->counter + 1, 0, sizeof(unsigned long long), b->stream));
+            CUDA_TRY(cudaEventRecord(e0, b->stream));
+            CUDA_TRY(L(1, d, vv, b->nmat, b->nhist, k, b->stream));
+            CUDA_TRY(cudaEventRecord(e1, b->stream));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            if (r >= 0) ms += t;  // r = -1 warms up
+          }
+          if (best < 0.f || ms < best) {
+            best = ms;
+            v[d] = vv;
+            c[d] = cps_options[ci];
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (mm_grid* g : b->m) {
+      mm_status st = check_device_error(g, "mm_batch_autotune");
+      if (st != MM_OK) return st;
+    }
+    if (cache_path && !tune_write(cache_path, key, v, c))
+      return fail(MM_EINVAL, "mm_batch_autotune_ex: cannot write the cache file %s", cache_path);
+  }
+  for (int d = 0; d < 3; ++d) {
+    b->variant[d] = v[d];
+    b->cps[d] = c[d];
+  }
+  batch_drop_graphs(b);
+  if (out) {
+    for (int d = 0; d < 3; ++d) {
+      out->variant[d] = v[d];
+      out->cta_per_sm[d] = c[d];
+    }
+    out->from_cache = from_cache;
+    out->size_class = cls;
+  }
+  return MM_OK;
+}
+
+mm_status mm_batch_autotune(mm_batch* b, int reps, int chosen[3]) {
+  mm_tune t;
+  mm_status st = mm_batch_autotune_ex(b, reps, nullptr, 1, &t);
+  if (st != MM_OK) return st;
+  if (chosen)
+    for (int d = 0; d < 3; ++d) chosen[d] = t.variant[d];
   return MM_OK;
 }
 

@@ -157,6 +157,7 @@ struct BatchK {
   long long total;   // start[M]
   long long chunk;   // cells per unit of the CFL and source launches (multiple of 128)
   int M;
+  int cta_per_sm;    // persistent CTAs per SM (0: as many as fit)
 };
 
 // Sets the message mm_last_error() returns on the calling thread.

@@ -164,6 +164,7 @@ struct Launch {
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     if (per < 1) per = 1;
+    if (b.cta_per_sm > 0 && b.cta_per_sm < per) per = b.cta_per_sm;
     long long grid = (long long)sms * per;
     if (grid > b.total) grid = b.total;
     if (grid < 1) return cudaSuccess;

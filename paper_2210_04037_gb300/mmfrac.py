@@ -41,6 +41,11 @@ class GridDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("n_materials", ctypes.c_int)]
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int * 3), ("cta_per_sm", ctypes.c_int * 3),
+                ("from_cache", ctypes.c_int), ("size_class", ctypes.c_int)]
+
+
 class Material(ctypes.Structure):
     _fields_ = [("eos", ctypes.c_int), ("rho0", ctypes.c_double), ("K0", ctypes.c_double),
                 ("G0", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
@@ -90,8 +95,8 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
            "mm_conserved_totals_noalloc", "mm_batch_create", "mm_batch_set_options",
-           "mm_batch_step", "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
-           "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
+           "mm_batch_step", "mm_batch_autotune", "mm_batch_autotune_ex", "mm_batch_synchronize",
+           "mm_batch_destroy", "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
            "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy")
 KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources", "xtransport",
                 "frag_mark", "frag_union", "frag_count", "frag_collect")
@@ -127,6 +132,8 @@ def load(path: str = LIB_PATH):
         lib.mm_batch_set_options.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
         lib.mm_batch_step.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         lib.mm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        lib.mm_batch_autotune_ex.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                             P(Tune)]
         lib.mm_batch_synchronize.argtypes = [vp]
         lib.mm_batch_destroy.argtypes = [vp]
         lib.mm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -161,7 +168,8 @@ def load(path: str = LIB_PATH):
         for fn in ("mm_create_grid", "mm_set_materials", "mm_step", "mm_step_async",
                    "mm_synchronize", "mm_read_fields", "mm_conserved_totals", "mm_destroy",
                    "mm_batch_create", "mm_batch_set_options", "mm_batch_step",
-                   "mm_batch_autotune", "mm_batch_synchronize", "mm_batch_destroy",
+                   "mm_batch_autotune", "mm_batch_autotune_ex", "mm_batch_synchronize",
+                   "mm_batch_destroy",
                    "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
                    "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy"):
             getattr(lib, fn).restype = ctypes.c_int
@@ -421,10 +429,21 @@ class Batch:
         self.step_async(n_steps, cfl)
         self.synchronize()
 
-    def autotune(self, reps: int = 3):
-        out = (ctypes.c_int * 3)()
-        _check(load().mm_batch_autotune(self.h, int(reps), out))
-        return list(out)
+    def autotune(self, reps: int = 3, cache: str | None = None, force: bool = False):
+        """Search the launch configurations (tile shape x persistent CTAs per
+        SM per sweep axis); with `cache`, a choice cached for this device and
+        size class is taken without timing, and a timed one is saved there.
+        Returns the chosen tile shapes (without `cache`) or the whole
+        choice as a dict."""
+        if cache is None:
+            out = (ctypes.c_int * 3)()
+            _check(load().mm_batch_autotune(self.h, int(reps), out))
+            return list(out)
+        t = Tune()
+        _check(load().mm_batch_autotune_ex(self.h, int(reps), cache.encode(), 1 if force else 0,
+                                           ctypes.byref(t)))
+        return dict(variant=list(t.variant), cta_per_sm=list(t.cta_per_sm),
+                    from_cache=bool(t.from_cache), size_class=int(t.size_class))
 
     def profile_enable(self, on: bool = True) -> None:
         _check(load().mm_batch_profile_enable(self.h, 1 if on else 0))

@@ -119,6 +119,41 @@ def test_autotune_leaves_the_states_unchanged():
         g.close()
 
 
+def test_autotune_cache_and_launch_configurations(tmp_path):
+    """The search over tile shape x persistent CTAs per SM: its choice is
+    saved under the batch's device and size class, a later batch of the
+    same class takes it from the cache without timing, force times again;
+    every configuration steps the members as they step alone."""
+    cache = str(tmp_path / "tune.txt")
+
+    def make():
+        grids = [mmfrac.Grid(W.ring_2d(n, seed=60 + n), mmfrac.FP32_SPLIT) for n in (40, 48, 56)]
+        return grids, mmfrac.Batch(grids)
+
+    grids, b = make()
+    t1 = b.autotune(reps=1, cache=cache)
+    assert not t1["from_cache"] and t1["size_class"] == 11  # median 48^2 = 2304 cells
+    assert all(v in (0, 1) for v in t1["variant"]) and all(c in (0, 1, 2) for c in t1["cta_per_sm"])
+    b.close()
+    for g in grids:
+        g.close()
+    grids, b = make()
+    t2 = b.autotune(reps=1, cache=cache)
+    assert t2["from_cache"] and t2["variant"] == t1["variant"] and t2["cta_per_sm"] == t1["cta_per_sm"]
+    t3 = b.autotune(reps=1, cache=cache, force=True)
+    assert not t3["from_cache"]
+    b.step(6)
+    got = [(g.read(False), g.synchronize()) for g in grids]
+    b.close()
+    for g, c in zip(grids, (40, 48, 56)):
+        g.close()
+    for (u, info), n in zip(got, (40, 48, 56)):
+        ref, rinfo = alone(W.ring_2d(n, seed=60 + n), mmfrac.FP32_SPLIT, 6)
+        assert same_state(u, ref, mmfrac.FP32_SPLIT, W.ring_2d(n).layout)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 2 and lines[0].split()[0] == lines[1].split()[0]
+
+
 def test_batch_argument_errors():
     g2 = mmfrac.Grid(W.ring_2d(32), mmfrac.FP32_SPLIT)
     g1 = mmfrac.Grid(W.spall_1d(64), mmfrac.FP32_SPLIT)
