@@ -59,7 +59,9 @@ enum { MM_DMG_NONE = 0, MM_DMG_BONORA = 1, MM_DMG_SIMPLE = 2 };
  * bc[k][side] one of MM_BC_*; precision MM_FP64 (every step in FP64) or
  * MM_FP32_SPLIT (reconstruction and fluxes in FP32, total energy, energy
  * recovery, plastic return iteration and totals in FP64); n_materials 1..2,
- * or 3 when one of them is void (MM_EOS_VOID). */
+ * or 3 when one of them is void (MM_EOS_VOID); at most one material with a
+ * plasticity model, or two on 1D and 2D grids without void (two or three
+ * materials, e.g. two solids in a gas). */
 typedef struct {
   int dim;
   int64_t n[3];

@@ -372,11 +372,15 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
     }
     if (m.plasticity == MM_PL_JOHNSON_COOK) hslot[l] = nhist++;
   }
-  if (nhist > 1) return fail(MM_EINVAL, "at most one plastic material is supported");
+  if (nhist > 2) return fail(MM_EINVAL, "at most two plastic materials are supported");
+  if (nhist == 2 && (g->dim > 2 || void_l >= 0))
+    return fail(MM_EINVAL, "two plastic materials are supported on 1D and 2D grids without void");
   if (void_l >= 0 && nhist != 1)
     return fail(MM_EINVAL, "a grid with void needs exactly one plastic material");
-  if (n == 3 && void_l < 0)
-    return fail(MM_EINVAL, "three materials are supported with one of them void");
+  if (n == 3 && void_l < 0 && nhist != 2)
+    return fail(MM_EINVAL,
+                "three materials are supported with one of them void, or with two plastic "
+                "solids (1D, 2D)");
   const int nF = g->dim == 1 ? 3 : (g->dim == 2 ? 5 : 9);
   const int nfield = (g->nmat - 1) + g->nmat + g->dim + 1 + nF + 2 * nhist + g->dim;
   if (init->phi0) {
@@ -1040,8 +1044,9 @@ mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_ba
     for (int j = 0; j < i; ++j)
       if (grids[j] == g) return fail(MM_EINVAL, "mm_batch_create: member %d repeats member %d", i, j);
   }
-  if (g0->nmat != 2)
-    return fail(MM_EINVAL, "mm_batch_create: batches are built for two materials");
+  if (g0->nmat != 2 || g0->nhist > 1)
+    return fail(MM_EINVAL,
+                "mm_batch_create: batches are built for two materials, at most one plastic");
   for (int i = 0; i < n; ++i)
     if (grids[i]->base.void_l >= 0)
       return fail(MM_EINVAL, "mm_batch_create: member %d holds void; void grids run alone", i);

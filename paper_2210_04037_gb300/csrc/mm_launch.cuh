@@ -242,6 +242,11 @@ struct Launch {
     if (a.nmat == 1 && a.nhist == 1) return run<DIM, 1, 1>(what, axis, flag, a, out, nblocks, s);
     if (a.nmat == 2 && a.nhist == 0) return run<DIM, 2, 0>(what, axis, flag, a, out, nblocks, s);
     if (a.nmat == 2 && a.nhist == 1) return run<DIM, 2, 1>(what, axis, flag, a, out, nblocks, s);
+    // two plastic solids (with or without a gas), 1D and 2D grids
+    if constexpr (DIM <= 2) {
+      if (a.nmat == 2 && a.nhist == 2) return run<DIM, 2, 2>(what, axis, flag, a, out, nblocks, s);
+      if (a.nmat == 3 && a.nhist == 2) return run<DIM, 3, 2>(what, axis, flag, a, out, nblocks, s);
+    }
     return cudaErrorInvalidValue;
   }
 

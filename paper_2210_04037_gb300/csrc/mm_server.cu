@@ -286,11 +286,11 @@ mm_status mm_server_submit(mm_server* s, const mm_grid_desc* desc, const mm_mate
   }
   if (desc->dim < 1 || desc->dim > 3 || n_mat != desc->n_materials || n_mat != 2 || n_steps < 0 ||
       !(cfl > 0.0) || !(cfl <= 1.0) || mats[0].eos == MM_EOS_VOID ||
-      mats[1].eos == MM_EOS_VOID ||
+      mats[1].eos == MM_EOS_VOID || plastic_count(mats, n_mat) > 1 ||
       (desc->precision != MM_FP64 && desc->precision != MM_FP32_SPLIT)) {
     mm_internal_set_error(
-        "mm_server_submit: dim 1..3, two materials (no void), n_steps >= 0, cfl in (0, 1] and a "
-        "known precision are required");
+        "mm_server_submit: dim 1..3, two materials (no void, at most one plastic), n_steps >= 0, "
+        "cfl in (0, 1] and a known precision are required");
     return MM_EINVAL;
   }
   RunP r = std::make_shared<Run>();

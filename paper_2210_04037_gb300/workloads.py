@@ -341,6 +341,42 @@ def spall_1d(ncell: int = 1000, seed: int = 1, sd: float = 0.05,
     return case
 
 
+def spall_al_cube_1d(ncell: int = 1000, seed: int = 1, a: float = 0.0,
+                     v_flyer: float = 300.0) -> Case:
+    """The 1D spallation test of Sec. 4.1 with its three materials: an
+    Al-H32 flyer (Al 5083 H32: Romenskii and Johnson-Cook rows, no damage)
+    2 mm thick at v_flyer onto a 6 mm CuBe target at rest (Bonora damage),
+    air either side at 1e5 Pa, on [0, 11] mm; transmissive ends; the CuBe's
+    yield stress perturbed by phi0 ~ U(1 - a, 1 + a) per cell (a = 0: none).
+    Volume fractions from exact cell coverage, clipped to [1e-6, 1 - 1e-6]
+    with the air taking the rest."""
+    al, cu, gas = al_h32("none"), cube("bonora"), air()
+    mats = [al, cu, gas]
+    case = Case("spall_al_cube_1d", 1, [ncell, 1, 1], [0.0, 0, 0], [0.011, 1, 1],
+                [BC_TRANSMISSIVE] * 2, mats, None, cfl=0.6, steps=2000)
+    lay = case.layout
+    case.prim = blank_prim(lay, ncell)
+    dx = case.dx[0]
+    edges = np.arange(ncell + 1) * dx
+    f_al = _coverage_1d(edges[:-1], edges[1:], 0.001, 0.003)
+    f_cu = _coverage_1d(edges[:-1], edges[1:], 0.003, 0.009)
+    f_al = np.clip(f_al, PHI_MIN, 1.0 - 2 * PHI_MIN)
+    f_cu = np.clip(f_cu, PHI_MIN, 1.0 - f_al - PHI_MIN)
+    case.prim[lay.o_phi] = f_al
+    case.prim[lay.o_phi + 1] = f_cu
+    case.prim[lay.o_rho] = al["rho0"]
+    case.prim[lay.o_rho + 1] = cu["rho0"]
+    case.prim[lay.o_rho + 2] = gas["rho0"]
+    x = case.centres()[0]
+    case.prim[lay.o_u] = np.where(f_al > 0.5, v_flyer, 0.0)
+    case.prim[lay.o_p] = 1.0e5
+    case.prim[lay.o_X] = x
+    if a > 0:
+        case.phi0 = perturbation_uniform(seed, [ncell], a)
+        case.pn, case.plo, case.ph = [ncell, 1, 1], [0.5 * dx, 0, 0], [dx, 1, 1]
+    return case
+
+
 def ring_2d(n: int = 512, seed: int = 2, a: float = 0.1, v: float = 200.0,
             width: float = 0.064, r0: float = 0.020, r1: float = 0.024,
             lattice_h: float = 0.0005, solid: Optional[Dict[str, float]] = None,

@@ -329,3 +329,31 @@ def cracked_block(dim, n, p=-2e8, vel=5.0, seed=0, with_void=True, bc=0):
     for d in range(dim):
         c.prim[lay.o_X + d] = cen[d]
     return c
+
+
+def three_mix_2d(n, seed=8, shear=0.02, p0=5e8, dp=5e7, vel=5.0, bc=1):
+    """Smooth periodic mixture of two plastic solids and a gas (Al-H32,
+    CuBe with Bonora damage, air at 700 kg/m^3) under compression, with a
+    shear that yields: the two-plastic closure in 2D."""
+    rng = np.random.default_rng(seed)
+    mats = [W.al_h32("none"), W.cube("bonora"), W.air()]
+    c = W.Case("mix3m", 2, [n, n, 1], [0, 0, 0], [1e-3, 1e-3, 1], [bc] * 4, mats, None, cfl=0.5)
+    lay = c.layout
+    c.prim = W.blank_prim(lay, c.ncell)
+    x, y = c.centres()
+    k = 2 * np.pi / 1e-3
+    a = rng.uniform(0.5, 1.5, 5)
+    f_al = 0.3 + 0.2 * np.sin(k * x + a[0]) * np.cos(k * y + a[1])
+    f_cu = 0.3 + 0.2 * np.cos(k * x + a[2]) * np.sin(k * y)
+    c.prim[lay.o_phi] = f_al
+    c.prim[lay.o_phi + 1] = f_cu
+    c.prim[lay.o_rho] = mats[0]["rho0"] * (1 + 0.002 * np.cos(k * y))
+    c.prim[lay.o_rho + 1] = mats[1]["rho0"] * (1 + 0.002 * np.sin(k * x))
+    c.prim[lay.o_rho + 2] = 700.0
+    c.prim[lay.o_u] = vel * np.sin(k * y + a[3])
+    c.prim[lay.o_u + 1] = vel * np.cos(k * x)
+    c.prim[lay.o_p] = p0 + dp * np.sin(k * x + a[4])
+    c.prim[lay.F_index(0, 1)] = shear * np.sin(k * x)
+    c.prim[lay.o_X] = x
+    c.prim[lay.o_X + 1] = y
+    return c
