@@ -104,9 +104,10 @@ def ensemble_cases(m: int):
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
 # once those differ.
-TRAFFIC_SRC_SHA256 = "02d9816d76c400538692bb22cc8863360673f61cd53ec29a15d858d25af821dd"
-TRAFFIC = {("ring_2d", 512, "fp32split"): {"sweep_x": 17892608, "sweep_y": 17892608,
-                                           "sources": 17976064}}
+TRAFFIC_SRC_SHA256 = "f502280bb60a07c988a49b0728427e3472025ce1a3986f167d61265b2d18c29c"
+TRAFFIC = {("cylinder_3d", 256, "fp32split"): {"sweep_x": 3045382144, "sweep_y": 3371834368,
+                                               "sweep_z": 3474848000, "sources": 1306199808,
+                                               "cfl": 1545544192}}
 
 
 def kernel_src_hash() -> str:
