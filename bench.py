@@ -619,6 +619,7 @@ def run_ensemble(args, rank: int, world: int, nested: bool = False, dist=None):
     b.step(args.steps)
     prof = b.profile_read()
     b.profile_enable(False)
+    ngroups = b.num_groups()
     b.close()
     for g in grids:
         g.close()
@@ -659,6 +660,7 @@ def run_ensemble(args, rank: int, world: int, nested: bool = False, dist=None):
         "config": {"workload": WORKLOAD_TEXT["ensemble_2d"].format(n=m), "members": m,
                    "cells": ncell, "precision": args.precision,
                    "tile_variants": chosen[:2], "cta_per_sm": tune["cta_per_sm"][:2],
+                   "member_groups": ngroups,
                    "l2": "state larger than L2", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -940,6 +940,9 @@ struct mm_batch {
   int variant[3] = {0, 0, 0};
   int cps[3] = {0, 0, 0};  // persistent sweep CTAs per SM per axis (0: as many as fit)
   int cps_src = 0;         // the same for the source kernel
+  // groups of members stepped one after another (each group's state sized
+  // to stay in L2 between its launches): member index bounds, ngroups + 1
+  std::vector<int> gstart;
   int parity = 0;  // flips with every sweep: the members' buffers relative to creation
   int use_graph = 1;
   bool warmed = false;
@@ -983,6 +986,19 @@ BatchK batch_k(const mm_batch* b, int phase, const long long* start, long long t
   k.chunk = kChunk;
   k.M = b->M;
   k.cta_per_sm = 0;
+  k.base = 0;
+  return k;
+}
+
+// The same launch restricted to members [g0, g1) of group gi (its own work
+// counter; unit numbers stay those of the whole batch).
+BatchK batch_kg(const mm_batch* b, int phase, const long long* start, const long long* h_start,
+                int g0, int g1, int gi) {
+  BatchK k = batch_k(b, phase, start + g0, h_start[g1]);
+  k.args += g0;
+  k.counter = b->counter + 8 * gi + phase;
+  k.base = h_start[g0];
+  k.M = g1 - g0;
   return k;
 }
 
@@ -990,34 +1006,70 @@ BatchK batch_k(const mm_batch* b, int phase, const long long* start, long long t
 cudaError_t batch_enqueue(mm_batch* b, double cfl) {
   batch_launcher L = batch_launch_of(b->prec, b->dim);
   const int M = b->M;
-  cudaError_t e = cudaMemsetAsync(b->counter, 0, 8 * sizeof(unsigned long long), b->stream);
+  const int G = (int)b->gstart.size() - 1;
+  cudaError_t e = cudaMemsetAsync(b->counter, 0, 8 * sizeof(unsigned long long) * G, b->stream);
   if (e != cudaSuccess) return e;
-  prof_begin(b, MM_K_CFL);
-  e = L(0, 0, 0, b->nmat, b->nhist, batch_k(b, 0, b->cstart, b->h_cstart[M]), b->stream);
-  prof_end(b);
-  if (e != cudaSuccess) return e;
-  prof_begin(b, MM_K_DT);
-  k_dt_batch<<<(M + 127) / 128, 128, 0, b->stream>>>(
-      b->args + (size_t)b->parity * kPhases * M, M, cfl);
-  prof_end(b);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  for (int d = 0; d < b->dim; ++d) {
-    const int v = b->variant[d];
-    const size_t o = (size_t)(d * 2 + v) * (M + 1);
-    prof_begin(b, MM_K_SWEEP_X + d);
-    BatchK k = batch_k(b, 1 + d, b->tstart + o, b->h_tstart[o + M]);
-    k.cta_per_sm = b->cps[d];
-    e = L(1, d, v, b->nmat, b->nhist, k, b->stream);
+  // one group after another: every launch of a step on a group's members
+  // (whose state then stays in L2), members independent of one another
+  for (int gi = 0; gi < G; ++gi) {
+    const int g0 = b->gstart[gi], g1 = b->gstart[gi + 1];
+    prof_begin(b, MM_K_CFL);
+    e = L(0, 0, 0, b->nmat, b->nhist, batch_kg(b, 0, b->cstart, b->h_cstart.data(), g0, g1, gi),
+          b->stream);
+    prof_end(b);
+    if (e != cudaSuccess) return e;
+    prof_begin(b, MM_K_DT);
+    k_dt_batch<<<(g1 - g0 + 127) / 128, 128, 0, b->stream>>>(
+        b->args + (size_t)b->parity * kPhases * M + g0, g1 - g0, cfl);
+    prof_end(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int d = 0; d < b->dim; ++d) {
+      const int v = b->variant[d];
+      const size_t o = (size_t)(d * 2 + v) * (M + 1);
+      prof_begin(b, MM_K_SWEEP_X + d);
+      BatchK k = batch_kg(b, 1 + d, b->tstart + o, b->h_tstart.data() + o, g0, g1, gi);
+      k.cta_per_sm = b->cps[d];
+      e = L(1, d, v, b->nmat, b->nhist, k, b->stream);
+      prof_end(b);
+      if (e != cudaSuccess) return e;
+    }
+    prof_begin(b, MM_K_SOURCES);
+    BatchK ks = batch_kg(b, 4, b->cstart, b->h_cstart.data(), g0, g1, gi);
+    ks.cta_per_sm = b->cps_src;
+    e = L(2, 0, 0, b->nmat, b->nhist, ks, b->stream);
     prof_end(b);
     if (e != cudaSuccess) return e;
   }
-  prof_begin(b, MM_K_SOURCES);
-  BatchK ks = batch_k(b, 4, b->cstart, b->h_cstart[M]);
-  ks.cta_per_sm = b->cps_src;
-  e = L(2, 0, 0, b->nmat, b->nhist, ks, b->stream);
-  prof_end(b);
   return e;
+}
+
+// Greedy groups of consecutive members whose state copies (both buffers)
+// sum to at most `bytes` each (a larger member is a group of its own);
+// bytes <= 0: one group of every member.
+void batch_group(mm_batch* b, long long bytes) {
+  b->gstart.assign(1, 0);
+  long long acc = 0;
+  for (int i = 0; i < b->M; ++i) {
+    const mm_grid* g = b->m[i];
+    const long long mb = 2 * (long long)(elem_size(g) * (size_t)(g->nfield + 1) * g->ncell +
+                                         (g->prec == MM_FP64 ? 0 : sizeof(double) * g->ncell));
+    if (bytes > 0 && i > b->gstart.back() && acc + mb > bytes) {
+      b->gstart.push_back(i);
+      acc = 0;
+    }
+    acc += mb;
+  }
+  b->gstart.push_back(b->M);
+}
+
+// Default group budget: 60 % of the device's L2 cache.
+long long default_group_bytes() {
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0)
+    return 0;
+  return (long long)l2 * 6 / 10;
 }
 
 void batch_advance(mm_batch* b) {
@@ -1103,7 +1155,7 @@ mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_ba
   if (cudaMalloc(&b->args, sizeof(KArgs) * A.size()) != cudaSuccess ||
       cudaMalloc(&b->tstart, sizeof(long long) * b->h_tstart.size()) != cudaSuccess ||
       cudaMalloc(&b->cstart, sizeof(long long) * b->h_cstart.size()) != cudaSuccess ||
-      cudaMalloc(&b->counter, sizeof(unsigned long long) * 8) != cudaSuccess) {
+      cudaMalloc(&b->counter, sizeof(unsigned long long) * 8 * n) != cudaSuccess) {
     batch_free(b);
     return fail(MM_ENOMEM, "device allocation of the batch tables failed");
   }
@@ -1118,9 +1170,19 @@ mm_status mm_batch_create(mm_grid* const* grids, int n, void* cuda_stream, mm_ba
     batch_free(b);
     return fail(MM_ECUDA, "mm_batch_create: %s", cudaGetErrorString(e));
   }
+  batch_group(b, 0);
   *out = b;
   return MM_OK;
 }
+
+mm_status mm_batch_set_grouping(mm_batch* b, int64_t group_bytes) {
+  if (!b) return fail(MM_EINVAL, "mm_batch_set_grouping: null batch");
+  batch_group(b, group_bytes < 0 ? default_group_bytes() : group_bytes);  // (L2 budget)
+  batch_drop_graphs(b);
+  return MM_OK;
+}
+
+int mm_batch_num_groups(const mm_batch* b) { return b ? (int)b->gstart.size() - 1 : 0; }
 
 mm_status mm_batch_set_options(mm_batch* b, int use_graph, const int tile_variant[3]) {
   if (!b) return fail(MM_EINVAL, "mm_batch_set_options: null batch");

@@ -154,6 +154,7 @@ struct BatchK {
   const KArgs* args;
   const long long* start;
   unsigned long long* counter;
+  long long base;    // units before the launch's first member (start[0])
   long long total;   // start[M]
   long long chunk;   // cells per unit of the CFL and source launches (multiple of 128)
   int M;

@@ -747,20 +747,37 @@ __device__ __forceinline__ int batch_member(const BatchK& bk, long long u) {
   return lo;
 }
 
-// Next unit for the CTA (uniform); ka <- the arguments of its member.
+// Next unit for the CTA (uniform); ka <- the arguments of its member,
+// copied only when the member differs from the previous unit's (s_m, -1 at
+// the start): a CTA's units are mostly of one member.  GRAB units are taken
+// from the counter at a time (s_unit the next one, s_end the end of the
+// taken range; both -1 at the start), which spreads the atomic's latency
+// over them.
+template <int GRAB = 1>
 __device__ __forceinline__ bool batch_next(const BatchK& bk, KArgs& ka, long long& unit,
-                                           long long& s_unit) {
+                                           long long& s_unit, long long& s_end, int& s_m) {
   __syncthreads();  // the previous unit is finished by every thread
-  if (threadIdx.x == 0) s_unit = (long long)atomicAdd(bk.counter, 1ull);
+  if (threadIdx.x == 0) {
+    if (s_unit < 0 || s_unit >= s_end) {
+      s_unit = bk.base + (long long)atomicAdd(bk.counter, (unsigned long long)GRAB);
+      s_end = s_unit + GRAB;
+    }
+  }
   __syncthreads();
   const long long u = s_unit;
   if (u >= bk.total) return false;
   const int m = batch_member(bk, u);
   unit = u - bk.start[m];
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(bk.args + m);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ka);
-  for (int i = threadIdx.x; i < int(sizeof(KArgs) / 8); i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
+  __syncthreads();  // every thread has read s_unit
+  if (threadIdx.x == 0) s_unit = u + 1;
+  if (m != s_m) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(bk.args + m);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ka);
+    for (int i = threadIdx.x; i < int(sizeof(KArgs) / 8); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();  // every thread has read s_m before it changes
+    if (threadIdx.x == 0) s_m = m;
+    __syncthreads();
+  }
   return true;
 }
 
@@ -771,9 +788,15 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX, V>::NT) k_sweep_batch(BatchK 
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
   __shared__ KArgs ka;
-  __shared__ long long s_unit;
+  __shared__ long long s_unit, s_end;
+  __shared__ int s_m;
+  if (threadIdx.x == 0) {
+    s_m = -1;
+    s_unit = -1;
+    s_end = -1;
+  }
   long long t;
-  while (batch_next(bk, ka, t, s_unit)) {
+  while (batch_next<4>(bk, ka, t, s_unit, s_end, s_m)) {
     int ta, tw, rr;
     tile_of<AX, SH::TL, SH::TW>(ka, t, ta, tw, rr);
     sweep_tile<P, DIM, NMAT, NH, AX, V>(ka, ta, tw, rr, true, false, smem, ok1, ok2);
@@ -1403,12 +1426,18 @@ template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(128, P::split ? 5 : 1) k_sources_batch(BatchK bk) {
   __shared__ typename std::conditional<P::split, SrcQueue<P, DIM, NMAT, NH>, int>::type qs;
   __shared__ KArgs ka;
-  __shared__ long long s_unit;
+  __shared__ long long s_unit, s_end;
+  __shared__ int s_m;
+  if (threadIdx.x == 0) {
+    s_m = -1;
+    s_unit = -1;
+    s_end = -1;
+  }
   if constexpr (P::split) {
     if (threadIdx.x == 0) qs.n = 0;
   }
   long long ch;
-  while (batch_next(bk, ka, ch, s_unit)) {
+  while (batch_next(bk, ka, ch, s_unit, s_end, s_m)) {
     const double dt = ka.info->dt;
     const long long step = ka.info->steps;
     const long long b0 = ch * bk.chunk;
@@ -1493,9 +1522,15 @@ __global__ void __launch_bounds__(256, P::split ? 4 : 1) k_cfl(KArgs a) {
 template <class P, int DIM, int NMAT, int NH>
 __global__ void __launch_bounds__(256) k_cfl_batch(BatchK bk) {
   __shared__ KArgs ka;
-  __shared__ long long s_unit;
+  __shared__ long long s_unit, s_end;
+  __shared__ int s_m;
+  if (threadIdx.x == 0) {
+    s_m = -1;
+    s_unit = -1;
+    s_end = -1;
+  }
   long long ch;
-  while (batch_next(bk, ka, ch, s_unit)) {
+  while (batch_next(bk, ka, ch, s_unit, s_end, s_m)) {
     const long long b0 = ch * bk.chunk;
     const long long b1 = b0 + bk.chunk < ka.ncell ? b0 + bk.chunk : ka.ncell;
     const double smax = cfl_max<P, DIM, NMAT, NH>(ka, b0 + threadIdx.x, b1, blockDim.x,

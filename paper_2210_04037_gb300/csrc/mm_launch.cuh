@@ -166,7 +166,7 @@ struct Launch {
     if (per < 1) per = 1;
     if (b.cta_per_sm > 0 && b.cta_per_sm < per) per = b.cta_per_sm;
     long long grid = (long long)sms * per;
-    if (grid > b.total) grid = b.total;
+    if (grid > b.total - b.base) grid = b.total - b.base;
     if (grid < 1) return cudaSuccess;
     kernel<<<(unsigned)grid, threads, smem, s>>>(b);
     return cudaGetLastError();

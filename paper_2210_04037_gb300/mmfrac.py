@@ -95,7 +95,8 @@ EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
            "mm_last_error", "mm_kernel_launches", "mm_profile_enable", "mm_profile_read",
            "mm_conserved_totals_noalloc", "mm_batch_create", "mm_batch_set_options",
-           "mm_batch_step", "mm_batch_autotune", "mm_batch_autotune_ex", "mm_batch_synchronize",
+           "mm_batch_step", "mm_batch_autotune", "mm_batch_autotune_ex", "mm_batch_set_grouping",
+           "mm_batch_num_groups", "mm_batch_synchronize",
            "mm_batch_destroy", "mm_batch_profile_enable", "mm_batch_profile_read", "mm_server_create",
            "mm_server_submit", "mm_server_wait", "mm_server_stats", "mm_server_destroy")
 KERNEL_KINDS = ("cfl", "dt", "sweep_x", "sweep_y", "sweep_z", "sources", "xtransport",
@@ -134,6 +135,10 @@ def load(path: str = LIB_PATH):
         lib.mm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
         lib.mm_batch_autotune_ex.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                              P(Tune)]
+        lib.mm_batch_set_grouping.argtypes = [vp, ctypes.c_int64]
+        lib.mm_batch_set_grouping.restype = ctypes.c_int
+        lib.mm_batch_num_groups.argtypes = [vp]
+        lib.mm_batch_num_groups.restype = ctypes.c_int
         lib.mm_batch_synchronize.argtypes = [vp]
         lib.mm_batch_destroy.argtypes = [vp]
         lib.mm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -428,6 +433,14 @@ class Batch:
     def step(self, n_steps: int, cfl: float | None = None) -> None:
         self.step_async(n_steps, cfl)
         self.synchronize()
+
+    def set_grouping(self, group_bytes: int = -1) -> None:
+        """Members stepped in groups of at most group_bytes of state each
+        (0: one group; negative: the default, 60 % of L2)."""
+        _check(load().mm_batch_set_grouping(self.h, int(group_bytes)))
+
+    def num_groups(self) -> int:
+        return int(load().mm_batch_num_groups(self.h))
 
     def autotune(self, reps: int = 3, cache: str | None = None, force: bool = False):
         """Search the launch configurations (tile shape x persistent CTAs per

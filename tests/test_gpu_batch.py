@@ -102,6 +102,27 @@ def test_tile_shapes_and_graphs_do_not_change_results():
             assert i["steps"] == j["steps"]
 
 
+@pytest.mark.parametrize("prec", [mmfrac.FP64, mmfrac.FP32_SPLIT])
+def test_member_groups_do_not_change_results(prec):
+    """Members stepped in L2-sized groups (here: every member its own group,
+    and one group of all) end where they end alone; FP64 bit for bit."""
+    members = [W.ring_2d(n, seed=70 + n) for n in (40, 56, 48)]
+    for grouping, groups in ((1, 3), (0, 1)):
+        grids = [mmfrac.Grid(c, prec) for c in members]
+        b = mmfrac.Batch(grids)
+        b.set_grouping(grouping)
+        assert b.num_groups() == groups
+        b.step(7)
+        out = [(g.read(False), g.synchronize()) for g in grids]
+        b.close()
+        for g in grids:
+            g.close()
+        for c, (u, info) in zip(members, out):
+            ref, rinfo = alone(c, prec, 7)
+            assert same_state(u, ref, prec, c.layout), (grouping, c.name)
+            assert info["steps"] == rinfo["steps"]
+
+
 def test_autotune_leaves_the_states_unchanged():
     grids = [mmfrac.Grid(W.ring_2d(n, seed=40 + n), mmfrac.FP32_SPLIT) for n in (36, 52)]
     for g in grids:
