@@ -186,6 +186,21 @@ mm_status mm_set_x_transport(mm_grid* g, int scheme);
  * for it from mm_set_materials on.  Errors: MM_EINVAL. */
 mm_status mm_set_lagrangian_seeding(mm_grid* g, int on);
 
+/* TMA tile loads in the y and z sweeps (the split update of Sec. 3.1 along
+ * the second and third axes; no change to what a step computes).  3D
+ * FP32-split grids of two materials without void whose n[0] is a multiple
+ * of 4 get tensor maps of their state from mm_set_materials on; their y and
+ * z sweeps, where they run as columns of tiles per CTA (large grids), then
+ * stage each tile's new cells in shared memory with cp.async.bulk.tensor
+ * copies issued one tile ahead instead of per-thread loads.  The staged
+ * values are the stored ones, so both loads give the same bits.
+ * on = 1 (default) uses the maps, 0 the per-thread loads, -1 leaves the
+ * switch as it is.  active (may be null) receives 1 where the grid has maps
+ * and the switch is on, else 0.  A staged tile whose copy has not arrived
+ * within one second ends its CTA with MM_ETIMEOUT (reported by the next
+ * synchronising call).  Errors: MM_EINVAL. */
+mm_status mm_set_tma_loads(mm_grid* g, int on, int* active);
+
 /* Fragments of the present state (Sec. 4.2, 4.3 demarcate fragments by the
  * contour nu = theta of the void volume fraction, theta = 0.25, 0.5, 0.75,
  * and report fragment masses).  A crack is critically damaged solid

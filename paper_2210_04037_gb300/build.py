@@ -27,6 +27,7 @@ for _d in (1, 2, 3):
     for _b in ("", "_batch", "_void"):
         UNITS[f"mm_fp64_d{_d}{_b}.cu"] = ["--fmad=false"]
         UNITS[f"mm_fp32_d{_d}{_b}.cu"] = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
+UNITS["mm_fp32_d3_tma.cu"] = UNITS["mm_fp32_d3.cu"]
 
 
 def nvcc() -> str:

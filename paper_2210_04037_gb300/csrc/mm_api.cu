@@ -94,6 +94,10 @@ struct mm_grid {
   void* xs[3] = {nullptr, nullptr, nullptr};
   void* xseed = nullptr;    // Lagrangian seeding scratch (grids with void)
   bool seed_x = true;       // seeding before each step (grids with void)
+  // tensor maps of the TMA-staged y and z sweeps (3D FP32-split grids of
+  // two materials without void, n[0] a multiple of 4), and their switch
+  SweepTmaSet* tma = nullptr;
+  bool tma_on = true;
   // fragment labelling scratch (allocated on the first mm_fragments):
   // per-cell parents, fragment numbers of the roots and solid masses, the
   // per-block root offsets, and per-fragment labels, cell counts and masses
@@ -126,6 +130,8 @@ void free_state(mm_grid* g) {
     g->U[i] = nullptr;
     g->E[i] = nullptr;
   }
+  delete g->tma;  // maps of the freed buffers
+  g->tma = nullptr;
   cudaFree(g->prim);
   cudaFree(g->phi0);
   g->prim = nullptr;
@@ -155,6 +161,7 @@ mm_status check_device_error(mm_grid* g, const char* where) {
     const char* what = e.code == MM_ENONFINITE ? "inadmissible state"
                        : e.code == MM_ENOCONV  ? "plastic return did not converge"
                        : e.code == MM_EDT      ? "non-positive time step"
+                       : e.code == MM_ETIMEOUT ? "a bounded wait in a kernel gave up"
                                                : "device error";
     return fail((mm_status)e.code, "%s: %s at cell %lld, step %lld", where, what, e.cell, e.step);
   }
@@ -202,6 +209,7 @@ KArgs args_for(mm_grid* g) {
   a.Uout = g->U[g->cur];
   a.Ein = g->E[g->cur];
   a.Eout = g->E[g->cur];
+  a.tma = g->tma_on ? g->tma : nullptr;
   return a;
 }
 
@@ -414,6 +422,12 @@ mm_status mm_set_materials(mm_grid* g, const mm_material* mats, int n, const mm_
   if (cudaMalloc(&g->prim, sizeof(double) * nfield * g->ncell) != cudaSuccess) {
     free_state(g);
     return fail(MM_ENOMEM, "device allocation of the staging buffer failed");
+  }
+  if (g->prec == MM_FP32_SPLIT && g->dim == 3 && void_l < 0) {
+    // maps for the TMA-staged y and z sweeps, where they describe the grid
+    SweepTmaSet t;
+    const int n3[3] = {(int)g->desc.n[0], (int)g->desc.n[1], (int)g->desc.n[2]};
+    if (mm_p32_d3_tma_encode(&t, g->U, g->E, n3, g->nmat, nhist)) g->tma = new SweepTmaSet(t);
   }
   KArgs& a = g->base;
   a.nhist = nhist;
@@ -720,6 +734,17 @@ mm_status mm_set_lagrangian_seeding(mm_grid* g, int on) {
   if (on != 0 && on != 1) return fail(MM_EINVAL, "mm_set_lagrangian_seeding: on must be 0 or 1");
   g->seed_x = on != 0;
   drop_graphs(g);
+  return MM_OK;
+}
+
+mm_status mm_set_tma_loads(mm_grid* g, int on, int* active) {
+  if (!g) return fail(MM_EINVAL, "mm_set_tma_loads: null grid");
+  if (on < -1 || on > 1) return fail(MM_EINVAL, "mm_set_tma_loads: on must be -1, 0 or 1");
+  if (on >= 0 && g->tma_on != (on != 0)) {
+    g->tma_on = on != 0;
+    drop_graphs(g);  // they hold the launches of the other kernels
+  }
+  if (active) *active = g->tma_on && g->tma ? 1 : 0;
   return MM_OK;
 }
 

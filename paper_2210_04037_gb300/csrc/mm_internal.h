@@ -2,6 +2,7 @@
 // translation units (mm_fp64.cu, mm_fp32.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,6 +117,8 @@ struct KArgs {
   double* partial;     // per-block partial totals
   void* xs[3];         // X by WENO3 + RK3: cell velocities, stage 1, stage 2 ([dim][ncell], R)
   void* xseed;         // Lagrangian seeding (void grids): X after seeding ([dim][ncell], S)
+  const void* tma;     // host address of the grid's SweepTmaSet, or null (read by the host
+                       // launcher only, which passes the maps of Uin to the kernel)
   int* frag;           // fragment labelling: per-cell parent index, -1 outside fragments
   double* fmass;       // fragment labelling: per-cell solid mass dV sum (phi rho)_solid
   double fcut;         // fragment labelling: void cut-off theta
@@ -203,3 +206,36 @@ MM_DECLARE_BATCH_LAUNCHER(mm_p32_d1_batch)
 MM_DECLARE_BATCH_LAUNCHER(mm_p32_d2_batch)
 MM_DECLARE_BATCH_LAUNCHER(mm_p32_d3_batch)
 #undef MM_DECLARE_BATCH_LAUNCHER
+
+// TMA tile loads of the 3D FP32-split y and z sweeps (k_sweep_col_tma): one
+// tensor map per part of the state a tile reads, with a box of TW cells
+// along x, TL along the sweep axis and one along the remaining axis: the
+// float slots 0 .. oE - 1 (lo) and oE + 1 .. NF (hi; slot oE is unused in
+// the split form) of the [slot][z][y][x] float array, and the FP64 rho E
+// array (e).  Maps live in kernel parameters (__grid_constant__).
+struct ColTma {
+  CUtensorMap lo, hi, e;
+};
+
+// A grid's maps: per state buffer U[b] (E[b]) and sweep axis 1, 2.  nlo,
+// nhi, TL, TW: the box the maps were encoded with; the launcher uses them
+// only when they equal its kernel's (so the bytes a tile expects are the
+// bytes the copies deliver).
+struct SweepTmaSet {
+  const void* U[2];
+  ColTma m[2][2];
+  int nlo, nhi, TL[2], TW;
+};
+
+// Encodes s for a 3D FP32-split grid without void of n cells per axis,
+// nmat materials and nhist plastic materials whose state buffers are U[b]
+// ([nfield + 1][ncell] floats) and E[b] ([ncell] doubles).  Returns false
+// (s untouched) where a map cannot describe the grid: n[0] not a multiple
+// of 4 (row strides of 16 bytes), an encoder that is unavailable or refuses.
+// Launches the staged column sweep of a 3D FP32-split grid of two materials
+// (nhist 0 or 1) along axis 1 or 2: K tiles per CTA, grid CTAs, maps tm.
+cudaError_t mm_p32_d3_col_tma(int nhist, int axis, const KArgs& a, int K, unsigned grid,
+                              const ColTma& tm, cudaStream_t s);
+
+bool mm_p32_d3_tma_encode(SweepTmaSet* s, void* const U[2], double* const E[2], const int n[3],
+                          int nmat, int nhist);

@@ -11,13 +11,83 @@
 
 namespace mm {
 
-enum { ST_ENONFINITE = -4, ST_ENOCONV = -5, ST_EDT = -6 };
+enum { ST_ECUDA = -3, ST_ENONFINITE = -4, ST_ENOCONV = -5, ST_EDT = -6, ST_ETIMEOUT = -7 };
 enum { BC_T = 0, BC_P = 1, BC_R = 2 };
 
 __device__ __forceinline__ void report(DevErr* e, int code, long long cell, long long step) {
   if (atomicCAS(&e->code, 0, code) == 0) {
     e->cell = cell;
     e->step = step;
+  }
+}
+
+// ------------------------------------------------ TMA and mbarrier (PTX) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One-arrival mbarrier at shared address bar, made visible to the async
+// proxy (TMA) before its first use.
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The arrival of the phase, expecting `bytes` of TMA writes before it completes.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Orders the CTA's earlier generic accesses of shared memory (a barrier
+// before it makes every thread's visible) before later TMA writes there.
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Tiled TMA loads of a box at element coordinates (x first) into shared
+// memory at dst, completing `box bytes` on the mbarrier at bar.  The map is
+// a kernel parameter (__grid_constant__).  x times the element size is a
+// multiple of 16 bytes at every call site; boxes reaching outside the
+// tensor read zeros there.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* m, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* m, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// Waits until the phase of the given parity of the mbarrier at bar has
+// completed, for at most one second of the global timer (and 2^26 tries);
+// false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (long long it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (it == 0)
+      t0 = t;
+    else if (t - t0 > 1000000000ull || it > (1LL << 26))
+      return false;
   }
 }
 
@@ -262,6 +332,86 @@ struct SweepShape {
   }
 };
 
+// TMA staging of a column sweep's tiles (3D FP32-split, y and z): the
+// state of the TL new cells x TW of a tile (axis positions 4 .. TL + 3, the
+// rows a0 + 2 .. a0 + TL + 1) as three boxes: float slots 0 .. oE - 1,
+// slots oE + 1 .. NF, then rho E (doubles); box element (slot s, position
+// p, column w) at (s TL + p - 4) TW + w.  The boxes sit in the half-step
+// records (r2) between the two items carried at the front and the two
+// carried from the end, which are dead from phase 4 of one tile (when the
+// next tile's copy is issued) to phase 1 of the next (when it is read).
+template <class P, int DIM, int NMAT, int NH, int AX>
+struct ColStageShape {
+  typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
+  static_assert(P::split && sizeof(typename P::R) == 4 && sizeof(typename P::X) == 4 && AX != 0,
+                "staging of the FP32-split y and z sweeps");
+  typedef Lay<DIM, NMAT, NH> L;
+  static constexpr int NLO = L::oE, NHI = L::NF - L::oE;
+  static constexpr uint32_t SLOT = uint32_t(SH::TL) * SH::TW * 4;
+  static constexpr uint32_t bytes = (NLO + NHI) * SLOT + uint32_t(SH::TL) * SH::TW * 8;
+  static constexpr size_t r2 = 4 * size_t(SH::NX) * (size_t(SH::N1) + 2 * size_t(SH::N2) +
+                                                     SH::NR * size_t(SH::N3)) +
+                               4 * size_t(SH::N1) * SH::C1;
+  // first byte past the front carried items, and the start of the end ones
+  static constexpr size_t lo = r2 + 4 * size_t(4 * SH::TW) * SH::C2;
+  static constexpr size_t hi = r2 + 4 * size_t(2 * SH::TL * SH::TW) * SH::C2;
+  static_assert(lo + 127 + bytes <= hi, "the staged boxes fit between the carried records");
+};
+
+// The staging state of a CTA: maps, mbarrier, the wait's phase parity (per
+// thread), the boxes' offset from the dynamic shared memory, and whether
+// every wait so far completed.
+struct ColStage {
+  const ColTma* tm;
+  uint32_t bar;
+  uint32_t parity;
+  uint32_t dst;  // shared address of the boxes (128-byte aligned)
+  uint32_t off;  // dst - shared address of the dynamic shared memory
+  bool ok;
+};
+
+// Issues the copies of tile ta's new cells (one thread; after a barrier
+// that ends every generic access of the boxes' bytes).
+template <class P, int DIM, int NMAT, int NH, int AX>
+__device__ __forceinline__ void col_issue(const ColStage& st, int ta, int w0, int rr) {
+  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+  const int r0 = ta * CS::SH::TL + 2;
+  const int y = AX == 1 ? r0 : rr, z = AX == 1 ? rr : r0;
+  fence_async_shared();
+  mbar_expect_tx(st.bar, CS::bytes);
+  tma_load_4d(st.dst, &st.tm->lo, w0, y, z, 0, st.bar);
+  tma_load_4d(st.dst + CS::NLO * CS::SLOT, &st.tm->hi, w0, y, z, CS::NLO + 1, st.bar);
+  tma_load_3d(st.dst + (CS::NLO + CS::NHI) * CS::SLOT, &st.tm->e, w0, y, z, st.bar);
+}
+
+// The conserved state of a staged cell (box position pos = (p - 4) TW + w):
+// the values load_at reads from global memory.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__device__ __forceinline__ void stage_at(const unsigned char* box, int pos, typename P::R* c,
+                                         typename P::X* cx, double* rhoE) {
+  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+  typedef Lay<DIM, NMAT, NH> L;
+  typedef typename P::R R;
+  typedef typename P::X XT;
+  constexpr int NPX = Phys<P, DIM, NMAT, NH>::NPX, TLW = CS::SH::TL * CS::SH::TW;
+  const float* lo = reinterpret_cast<const float*>(box);
+  const float* hi = lo + CS::NLO * TLW;
+  const double* ev = reinterpret_cast<const double*>(hi + CS::NHI * TLW);
+#pragma unroll
+  for (int f = 0; f < L::NF; ++f)
+    c[f] = (f == L::oE || f < L::oARHO) ? R(0)
+                                        : R(f < L::oE ? lo[f * TLW + pos]
+                                                      : hi[(f - L::oE - 1) * TLW + pos]);
+#pragma unroll
+  for (int l = 0; l < NPX; ++l) {
+    const int slot = l < L::NPHI ? L::oPHI + l : L::NF;
+    cx[1 + l] = XT(slot < L::oE ? lo[slot * TLW + pos] : hi[(slot - L::oE - 1) * TLW + pos]);
+  }
+  const double e = ev[pos];
+  cx[0] = XT(e);
+  *rhoE = e;
+}
+
 // One tile of one sweep along AX: Uin -> Uout.  Phases over the tile (each
 // a pass of the CTA's threads over its items, separated by barriers):
 //   1. load + primitive recovery of the tile cells with a halo of two,
@@ -280,10 +430,16 @@ struct SweepShape {
 // state (same_still against the tile's first cell), the sweep leaves the
 // tile's cells as they are; they are copied to Uout and nothing is
 // computed.  Returns false then (no records to carry), true otherwise.
-template <class P, int DIM, int NMAT, int NH, int AX, int V>
+//
+// TM = 1 (k_sweep_col_tma): the tile's new in-grid cells come from the
+// boxes staged by TMA (sc), whose copy was issued before the call; the
+// copy of tile ta + 1 is issued here when carry is set (after phase 3, or
+// at once for a still tile).  A wait that gives up reports MM_ETIMEOUT and
+// clears sc->ok; the call then returns false and the CTA stops.
+template <class P, int DIM, int NMAT, int NH, int AX, int V, int TM = 0>
 __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int rr, bool first,
                                            bool carry, unsigned char* smem, unsigned char* ok1,
-                                           unsigned char* ok2) {
+                                           unsigned char* ok2, ColStage* sc = nullptr) {
   typedef typename P::R R;
   typedef Phys<P, DIM, NMAT, NH> PH;
   typedef Lay<DIM, NMAT, NH> L;
@@ -330,6 +486,17 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       }
     }
     if (__syncthreads_and(still)) {
+      if constexpr (TM) {
+        // the staged boxes are not needed; the next tile's copy reuses them
+        const bool got = mbar_wait(sc->bar, sc->parity);
+        sc->parity ^= 1u;
+        if (__syncthreads_or(!got)) {
+          if (threadIdx.x == 0) report(a.err, ST_ETIMEOUT, cell_index(a, w0, 0, 0), step);
+          sc->ok = false;
+          return false;
+        }
+        if (carry && threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(*sc, ta + 1, w0, rr);
+      }
       for (int it = threadIdx.x; it < N4; it += NT) {
         int p4, w;
         SH::pos(it, TL, p4, w);
@@ -349,6 +516,15 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
   // 1. primitive recovery of every tile cell, halo of two included
   // (positions 0..3 carried when the tile follows one of the same CTA)
   const int s1 = first ? 0 : 4;
+  if constexpr (TM) {
+    const bool got = mbar_wait(sc->bar, sc->parity);
+    sc->parity ^= 1u;
+    if (__syncthreads_or(!got)) {
+      if (threadIdx.x == 0) report(a.err, ST_ETIMEOUT, cell_index(a, w0, 0, 0), step);
+      sc->ok = false;
+      return false;
+    }
+  }
   for (int it0 = threadIdx.x; it0 < (TL + 4 - s1) * TW; it0 += NT) {
     int p, w;
     SH::pos(it0, TL + 4 - s1, p, w);
@@ -360,7 +536,20 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       R c[NF];
       XT cx[NX];
       double eE;
-      const long long idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
+      long long idx = 0;
+      bool staged = false;
+      if constexpr (TM) {
+        if (p >= 4 && gi < na) {
+          int co[3];
+          co[AX] = gi;
+          co[TD] = w0 + w;
+          co[3 - AX - TD] = rr;
+          idx = cell_index(a, co[0], co[1], co[2]);
+          stage_at<P, DIM, NMAT, NH, AX>(smem + sc->off, (p - 4) * TW + w, c, cx, &eE);
+          staged = true;
+        }
+      }
+      if (!staged) idx = load_cell<P, DIM, NMAT, NH, AX>(a, gi, w0 + w, rr, c, cx, &eE);
       R* rec = r1 + it * C1;
       Aux<R> ax;
       if (PH::template u2w<AX>(a, c, cx, rec, x1 + it * NX, ax, &eE)) {
@@ -614,6 +803,10 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
   }
   __syncthreads();
 
+  // the next tile's boxes are copied while this one is updated
+  if constexpr (TM)
+    if (carry && threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(*sc, ta + 1, w0, rr);
+
   // 4. conservative update with the non-conservative terms
   for (int it = threadIdx.x; it < N4; it += NT) {
     int p4, w;
@@ -733,6 +926,51 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep_col(KArgs a, int
   for (int ta = t0; ta < t1; ++ta)
     first = !sweep_tile<P, DIM, NMAT, NH, AX, 0>(a, ta, tw, rr, first, ta + 1 < t1, smem, ok1,
                                                  ok2);
+}
+
+// k_sweep_col with the tiles' new cells staged by TMA (3D FP32-split y and
+// z sweeps; maps of the launch's Uin and Ein in tm): the copy of a CTA's
+// first tile is issued before its loop, each later one during the update
+// of the tile before it, so a tile's loads overlap the previous tile's work.
+// Registers bounded for three CTAs per SM, as many as the shared memory of
+// the 16 x 8 tiles holds (unbounded, ptxas took 210: two CTAs).
+template <class P, int DIM, int NMAT, int NH, int AX>
+__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT, 3)
+    k_sweep_col_tma(const __grid_constant__ KArgs a, int K, const __grid_constant__ ColTma tm) {
+  typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
+  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+  constexpr int TD = 0;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
+  __shared__ __align__(8) unsigned long long bar;
+  const int nta = (a.n[AX] + SH::TL - 1) / SH::TL, ntt = (a.n[TD] + SH::TW - 1) / SH::TW;
+  const int nch = (nta + K - 1) / K;
+  long long b = blockIdx.x;
+  const int ch = int(b % nch);
+  b /= nch;
+  const int tw = int(b % ntt), rr = int(b / ntt);
+  const int t0 = ch * K, t1 = t0 + K < nta ? t0 + K : nta;
+  // a map the TMA unit reads must sit on a 64-byte boundary (parameters
+  // keep the type's 128-byte alignment; checked, not assumed)
+  if (reinterpret_cast<uintptr_t>(&tm) & 63) {
+    if (threadIdx.x == 0) report(a.err, ST_ECUDA, blockIdx.x, a.info->steps);
+    return;
+  }
+  ColStage sc;
+  sc.tm = &tm;
+  sc.bar = smem_u32(&bar);
+  sc.parity = 0;
+  const uint32_t base = smem_u32(smem);
+  sc.dst = (base + uint32_t(CS::lo) + 127u) & ~127u;
+  sc.off = sc.dst - base;
+  sc.ok = true;
+  if (threadIdx.x == 0) mbar_init(sc.bar);
+  __syncthreads();
+  if (threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(sc, t0, tw * SH::TW, rr);
+  bool first = true;
+  for (int ta = t0; ta < t1 && sc.ok; ++ta)
+    first = !sweep_tile<P, DIM, NMAT, NH, AX, 0, 1>(a, ta, tw, rr, first, ta + 1 < t1, smem, ok1,
+                                                    ok2, &sc);
 }
 
 // ------------------------------------------------------------ batches ----

@@ -65,9 +65,19 @@ struct Launch {
       k_sweep<P, DIM, NMAT, NH, AX><<<(unsigned)(nta * cols), SH::NT, SH::smem, s>>>(a);
       return cudaGetLastError();
     }
+    const long long nch = (nta + K - 1) / K;
+    if constexpr (std::is_same<P, P32>::value && DIM == 3 && AX != 0 && NMAT == 2 && NH <= 1) {
+      // tiles staged by TMA where the grid has maps for this state buffer
+      // (two materials; mm_fp32_d3_tma.cu)
+      typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+      const SweepTmaSet* ts = static_cast<const SweepTmaSet*>(a.tma);
+      const int b = !ts ? -1 : (a.Uin == ts->U[0] ? 0 : (a.Uin == ts->U[1] ? 1 : -1));
+      if (b >= 0 && ts->nlo == CS::NLO && ts->nhi == CS::NHI && ts->TL[AX - 1] == SH::TL &&
+          ts->TW == SH::TW)
+        return mm_p32_d3_col_tma(NH, AX, a, (int)K, (unsigned)(nch * cols), ts->m[b][AX - 1], s);
+    }
     cudaError_t e = smem_attr<k_sweep_col<P, DIM, NMAT, NH, AX>>(SH::smem);
     if (e != cudaSuccess) return e;
-    const long long nch = (nta + K - 1) / K;
     k_sweep_col<P, DIM, NMAT, NH, AX><<<(unsigned)(nch * cols), SH::NT, SH::smem, s>>>(a, (int)K);
     return cudaGetLastError();
   }

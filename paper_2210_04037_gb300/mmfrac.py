@@ -89,7 +89,7 @@ class StepInfo(ctypes.Structure):
 
 
 EXPORTS = ("mm_create_grid", "mm_set_materials", "mm_set_x_transport",
-           "mm_set_lagrangian_seeding", "mm_step",
+           "mm_set_lagrangian_seeding", "mm_set_tma_loads", "mm_step",
            "mm_step_async", "mm_synchronize",
            "mm_read_fields",
            "mm_conserved_totals", "mm_num_fields", "mm_num_cells", "mm_destroy",
@@ -126,6 +126,8 @@ def load(path: str = LIB_PATH):
         lib.mm_set_x_transport.restype = ctypes.c_int
         lib.mm_set_lagrangian_seeding.argtypes = [vp, ctypes.c_int]
         lib.mm_set_lagrangian_seeding.restype = ctypes.c_int
+        lib.mm_set_tma_loads.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+        lib.mm_set_tma_loads.restype = ctypes.c_int
         lib.mm_fragments.argtypes = [vp, ctypes.c_double, P(ctypes.c_int64), ctypes.c_size_t,
                                      P(Fragment), ctypes.c_size_t, P(ctypes.c_int64)]
         lib.mm_fragments.restype = ctypes.c_int
@@ -265,6 +267,17 @@ def set_lagrangian_seeding(grid, on: bool) -> None:
     _check(load().mm_set_lagrangian_seeding(grid, 1 if on else 0))
 
 
+def set_tma_loads(grid, on=None) -> bool:
+    """TMA tile loads in the y and z sweeps of 3D FP32-split grids (two
+    materials, no void, n[0] a multiple of 4): on True (default) / False,
+    None to leave the switch.  Returns whether the grid's y and z sweeps use
+    them (maps present and the switch on)."""
+    active = ctypes.c_int(0)
+    _check(load().mm_set_tma_loads(grid, -1 if on is None else (1 if on else 0),
+                                   ctypes.byref(active)))
+    return bool(active.value)
+
+
 def step_async(grid, n_steps: int, cfl: float) -> None:
     """Enqueue n_steps steps without waiting; in-step failures are reported
     by the next synchronize / step / read_fields."""
@@ -370,6 +383,9 @@ class Grid:
 
     def set_lagrangian_seeding(self, on: bool) -> None:
         set_lagrangian_seeding(self.h, on)
+
+    def set_tma_loads(self, on=None) -> bool:
+        return set_tma_loads(self.h, on)
 
     def step(self, n_steps: int, cfl: float | None = None) -> dict:
         return step(self.h, n_steps, self.case.cfl if cfl is None else cfl)
