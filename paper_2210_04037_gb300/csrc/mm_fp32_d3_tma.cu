@@ -1,4 +1,4 @@
-// The TMA-staged column sweeps of 3D FP32-split grids of two materials and
+// The TMA-staged y and z sweeps of 3D FP32-split grids of two materials and
 // the encoder of their tensor maps (a unit of its own, so that it compiles
 // beside mm_fp32_d3.cu; the same FP32 flags, the same sweep code).
 #include <cstring>
@@ -52,9 +52,9 @@ bool mm_p32_d3_tma_encode(SweepTmaSet* out, void* const U[2], double* const E[2]
   if (nmat != 2 || nhist < 0 || nhist > 1 || n[0] % 4 != 0) return false;
   const EncodeTiled enc = encoder();
   if (!enc) return false;
-  static_assert(Tile<P32, 3, 1>::TW == Tile<P32, 3, 2>::TW, "one box width");
   const int oE = (nmat - 1) + nmat + 3;
   const int NF = oE + 1 + 9 + 2 * nhist + 3;  // float slots 0 .. NF (slot NF: last fraction)
+  static_assert(Tile<P32, 3, 1>::TW == Tile<P32, 3, 2>::TW, "one box width");
   const cuuint32_t TW = Tile<P32, 3, 1>::TW;
   const cuuint32_t TLs[2] = {Tile<P32, 3, 1>::TL, Tile<P32, 3, 2>::TL};
   const cuuint64_t n0 = n[0], n1 = n[1], n2 = n[2], ncell = n0 * n1 * n2;

@@ -227,15 +227,15 @@ struct SweepTmaSet {
   int nlo, nhi, TL[2], TW;
 };
 
-// Encodes s for a 3D FP32-split grid without void of n cells per axis,
-// nmat materials and nhist plastic materials whose state buffers are U[b]
-// ([nfield + 1][ncell] floats) and E[b] ([ncell] doubles).  Returns false
-// (s untouched) where a map cannot describe the grid: n[0] not a multiple
-// of 4 (row strides of 16 bytes), an encoder that is unavailable or refuses.
 // Launches the staged column sweep of a 3D FP32-split grid of two materials
 // (nhist 0 or 1) along axis 1 or 2: K tiles per CTA, grid CTAs, maps tm.
 cudaError_t mm_p32_d3_col_tma(int nhist, int axis, const KArgs& a, int K, unsigned grid,
                               const ColTma& tm, cudaStream_t s);
 
+// Encodes s for a 3D FP32-split grid without void of n cells per axis,
+// nmat materials and nhist plastic materials whose state buffers are U[b]
+// ([nfield + 1][ncell] floats) and E[b] ([ncell] doubles).  Returns false
+// (s untouched) where a map cannot describe the grid: n[0] not a multiple
+// of 4 (row strides of 16 bytes), an encoder that is unavailable or refuses.
 bool mm_p32_d3_tma_encode(SweepTmaSet* s, void* const U[2], double* const E[2], const int n[3],
                           int nmat, int nhist);

@@ -332,80 +332,102 @@ struct SweepShape {
   }
 };
 
-// TMA staging of a column sweep's tiles (3D FP32-split, y and z): the
-// state of the TL new cells x TW of a tile (axis positions 4 .. TL + 3, the
-// rows a0 + 2 .. a0 + TL + 1) as three boxes: float slots 0 .. oE - 1,
-// slots oE + 1 .. NF, then rho E (doubles); box element (slot s, position
-// p, column w) at (s TL + p - 4) TW + w.  The boxes sit in the half-step
-// records (r2) between the two items carried at the front and the two
-// carried from the end, which are dead from phase 4 of one tile (when the
-// next tile's copy is issued) to phase 1 of the next (when it is read).
+// TMA staging of the y and z sweeps' tiles (3D FP32-split; columns of
+// tiles per CTA, k_sweep_col_tma): the TL new cells x TW of a tile (axis
+// positions 4 .. TL + 3, the rows a0 + 2 .. a0 + TL + 1) as three boxes of
+// BE = TL TW elements per slot, each starting on a 128-byte boundary as the
+// copies require: float slots 0 .. oE - 1 (at 0), slots oE + 1 .. NF (at
+// OHI; slot oE is unused in the split form), then rho E (doubles, at OE);
+// element (slot s, position p, column w) at s BE + (p - 4) TW + w.  The
+// boxes sit in the half-step records (r2) between the two items carried at
+// the front and the two carried from the end, which are dead from phase 4
+// of one tile (when the next tile's copy is issued) to phase 1 of the next
+// (when it is read).
 template <class P, int DIM, int NMAT, int NH, int AX>
-struct ColStageShape {
+struct StageShape {
   typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
-  static_assert(P::split && sizeof(typename P::R) == 4 && sizeof(typename P::X) == 4 && AX != 0,
-                "staging of the FP32-split y and z sweeps");
+  static_assert(P::split && sizeof(typename P::R) == 4 && sizeof(typename P::X) == 4 &&
+                    DIM == 3 && AX != 0,
+                "staging of the 3D FP32-split y and z sweeps");
   typedef Lay<DIM, NMAT, NH> L;
   static constexpr int NLO = L::oE, NHI = L::NF - L::oE;
-  static constexpr uint32_t SLOT = uint32_t(SH::TL) * SH::TW * 4;
-  static constexpr uint32_t bytes = (NLO + NHI) * SLOT + uint32_t(SH::TL) * SH::TW * 8;
+  static constexpr int BE = SH::TL * SH::TW;
+  static constexpr uint32_t SLOT = uint32_t(BE) * 4;
+  static constexpr uint32_t OHI = (NLO * SLOT + 127u) & ~127u;
+  static constexpr uint32_t OE = (OHI + NHI * SLOT + 127u) & ~127u;
+  static constexpr uint32_t bytes = (NLO + NHI) * SLOT + uint32_t(BE) * 8;  // the copies deliver
+  static constexpr uint32_t span = OE + uint32_t(BE) * 8;                    // the boxes take
   static constexpr size_t r2 = 4 * size_t(SH::NX) * (size_t(SH::N1) + 2 * size_t(SH::N2) +
                                                      SH::NR * size_t(SH::N3)) +
                                4 * size_t(SH::N1) * SH::C1;
   // first byte past the front carried items, and the start of the end ones
   static constexpr size_t lo = r2 + 4 * size_t(4 * SH::TW) * SH::C2;
   static constexpr size_t hi = r2 + 4 * size_t(2 * SH::TL * SH::TW) * SH::C2;
-  static_assert(lo + 127 + bytes <= hi, "the staged boxes fit between the carried records");
+  static_assert(lo + 127 + span <= hi, "the staged boxes fit between the carried records");
+  __device__ static __forceinline__ int pos(int p, int w) { return (p - 4) * SH::TW + w; }
 };
 
 // The staging state of a CTA: maps, mbarrier, the wait's phase parity (per
-// thread), the boxes' offset from the dynamic shared memory, and whether
-// every wait so far completed.
+// thread), the boxes' offset from the dynamic shared memory, whether every
+// wait so far completed, and the tile whose copy the current tile issues
+// (next: there is one; its axis tile, first transverse cell, remaining
+// index).
 struct ColStage {
   const ColTma* tm;
+  DevErr* err;
   uint32_t bar;
   uint32_t parity;
   uint32_t dst;  // shared address of the boxes (128-byte aligned)
   uint32_t off;  // dst - shared address of the dynamic shared memory
   bool ok;
+  bool next;
+  int nta, nw0, nrr;
 };
 
-// Issues the copies of tile ta's new cells (one thread; after a barrier
-// that ends every generic access of the boxes' bytes).
+// Issues the copies of the new cells of tile (ta, w0, rr) (one thread;
+// after a barrier that ends every generic access of the boxes' bytes).
 template <class P, int DIM, int NMAT, int NH, int AX>
-__device__ __forceinline__ void col_issue(const ColStage& st, int ta, int w0, int rr) {
-  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+__device__ __forceinline__ void stage_issue(const ColStage& st, int ta, int w0, int rr) {
+  typedef StageShape<P, DIM, NMAT, NH, AX> CS;
   const int r0 = ta * CS::SH::TL + 2;
-  const int y = AX == 1 ? r0 : rr, z = AX == 1 ? rr : r0;
+  const int x = w0, y = AX == 1 ? r0 : rr, z = AX == 1 ? rr : r0;
+  static_assert(CS::OHI % 128 == 0 && CS::OE % 128 == 0, "box starts on 128-byte boundaries");
   fence_async_shared();
+  if (st.dst & 127u) {
+    // never by construction; the copies would fault: complete the phase
+    // without them and report
+    report(st.err, ST_ECUDA, 0, 0);
+    mbar_expect_tx(st.bar, 0);
+    return;
+  }
   mbar_expect_tx(st.bar, CS::bytes);
-  tma_load_4d(st.dst, &st.tm->lo, w0, y, z, 0, st.bar);
-  tma_load_4d(st.dst + CS::NLO * CS::SLOT, &st.tm->hi, w0, y, z, CS::NLO + 1, st.bar);
-  tma_load_3d(st.dst + (CS::NLO + CS::NHI) * CS::SLOT, &st.tm->e, w0, y, z, st.bar);
+  tma_load_4d(st.dst, &st.tm->lo, x, y, z, 0, st.bar);
+  tma_load_4d(st.dst + CS::OHI, &st.tm->hi, x, y, z, CS::NLO + 1, st.bar);
+  tma_load_3d(st.dst + CS::OE, &st.tm->e, x, y, z, st.bar);
 }
 
-// The conserved state of a staged cell (box position pos = (p - 4) TW + w):
-// the values load_at reads from global memory.
+// The conserved state of a staged cell (box position pos): the values
+// load_at reads from global memory.
 template <class P, int DIM, int NMAT, int NH, int AX>
 __device__ __forceinline__ void stage_at(const unsigned char* box, int pos, typename P::R* c,
                                          typename P::X* cx, double* rhoE) {
-  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+  typedef StageShape<P, DIM, NMAT, NH, AX> CS;
   typedef Lay<DIM, NMAT, NH> L;
   typedef typename P::R R;
   typedef typename P::X XT;
-  constexpr int NPX = Phys<P, DIM, NMAT, NH>::NPX, TLW = CS::SH::TL * CS::SH::TW;
+  constexpr int NPX = Phys<P, DIM, NMAT, NH>::NPX, BE = CS::BE;
   const float* lo = reinterpret_cast<const float*>(box);
-  const float* hi = lo + CS::NLO * TLW;
-  const double* ev = reinterpret_cast<const double*>(hi + CS::NHI * TLW);
+  const float* hi = reinterpret_cast<const float*>(box + CS::OHI);
+  const double* ev = reinterpret_cast<const double*>(box + CS::OE);
 #pragma unroll
   for (int f = 0; f < L::NF; ++f)
     c[f] = (f == L::oE || f < L::oARHO) ? R(0)
-                                        : R(f < L::oE ? lo[f * TLW + pos]
-                                                      : hi[(f - L::oE - 1) * TLW + pos]);
+                                        : R(f < L::oE ? lo[f * BE + pos]
+                                                      : hi[(f - L::oE - 1) * BE + pos]);
 #pragma unroll
   for (int l = 0; l < NPX; ++l) {
     const int slot = l < L::NPHI ? L::oPHI + l : L::NF;
-    cx[1 + l] = XT(slot < L::oE ? lo[slot * TLW + pos] : hi[(slot - L::oE - 1) * TLW + pos]);
+    cx[1 + l] = XT(slot < L::oE ? lo[slot * BE + pos] : hi[(slot - L::oE - 1) * BE + pos]);
   }
   const double e = ev[pos];
   cx[0] = XT(e);
@@ -432,10 +454,10 @@ __device__ __forceinline__ void stage_at(const unsigned char* box, int pos, type
 // computed.  Returns false then (no records to carry), true otherwise.
 //
 // TM = 1 (k_sweep_col_tma): the tile's new in-grid cells come from the
-// boxes staged by TMA (sc), whose copy was issued before the call; the
-// copy of tile ta + 1 is issued here when carry is set (after phase 3, or
-// at once for a still tile).  A wait that gives up reports MM_ETIMEOUT and
-// clears sc->ok; the call then returns false and the CTA stops.
+// boxes TMA copied (sc), whose copy was issued before the call; the copy of
+// the tile sc names next is issued here (after phase 3, or at once for a
+// still tile).  A wait that gives up reports MM_ETIMEOUT and clears sc->ok;
+// the call then returns false and the CTA stops.
 template <class P, int DIM, int NMAT, int NH, int AX, int V, int TM = 0>
 __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int rr, bool first,
                                            bool carry, unsigned char* smem, unsigned char* ok1,
@@ -495,7 +517,8 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
           sc->ok = false;
           return false;
         }
-        if (carry && threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(*sc, ta + 1, w0, rr);
+        if (sc->next && threadIdx.x == 0)
+          stage_issue<P, DIM, NMAT, NH, AX>(*sc, sc->nta, sc->nw0, sc->nrr);
       }
       for (int it = threadIdx.x; it < N4; it += NT) {
         int p4, w;
@@ -539,13 +562,14 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
       long long idx = 0;
       bool staged = false;
       if constexpr (TM) {
+        typedef StageShape<P, DIM, NMAT, NH, AX> CS;
         if (p >= 4 && gi < na) {
           int co[3];
           co[AX] = gi;
           co[TD] = w0 + w;
           co[3 - AX - TD] = rr;
           idx = cell_index(a, co[0], co[1], co[2]);
-          stage_at<P, DIM, NMAT, NH, AX>(smem + sc->off, (p - 4) * TW + w, c, cx, &eE);
+          stage_at<P, DIM, NMAT, NH, AX>(smem + sc->off, CS::pos(p, w), c, cx, &eE);
           staged = true;
         }
       }
@@ -805,7 +829,8 @@ __device__ __forceinline__ bool sweep_tile(const KArgs& a, int ta, int tw, int r
 
   // the next tile's boxes are copied while this one is updated
   if constexpr (TM)
-    if (carry && threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(*sc, ta + 1, w0, rr);
+    if (sc->next && threadIdx.x == 0)
+      stage_issue<P, DIM, NMAT, NH, AX>(*sc, sc->nta, sc->nw0, sc->nrr);
 
   // 4. conservative update with the non-conservative terms
   for (int it = threadIdx.x; it < N4; it += NT) {
@@ -928,6 +953,31 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT) k_sweep_col(KArgs a, int
                                                  ok2);
 }
 
+// Setup of the staged sweep kernel: the map's alignment (a map the
+// TMA unit reads must sit on a 64-byte boundary; parameters keep the type's
+// 128-byte alignment, checked, not assumed), the mbarrier, the boxes'
+// place.  False (error reported) if the map is misaligned.
+template <class P, int DIM, int NMAT, int NH, int AX>
+__device__ __forceinline__ bool stage_setup(const KArgs& a, const ColTma& tm, ColStage& sc,
+                                            unsigned char* smem, unsigned long long* bar) {
+  if (reinterpret_cast<uintptr_t>(&tm) & 63) {
+    if (threadIdx.x == 0) report(a.err, ST_ECUDA, blockIdx.x, a.info->steps);
+    return false;
+  }
+  sc.tm = &tm;
+  sc.err = a.err;
+  sc.bar = smem_u32(bar);
+  sc.parity = 0;
+  const uint32_t base = smem_u32(smem);
+  sc.dst = (base + uint32_t(StageShape<P, DIM, NMAT, NH, AX>::lo) + 127u) & ~127u;
+  sc.off = sc.dst - base;
+  sc.ok = true;
+  sc.next = false;
+  if (threadIdx.x == 0) mbar_init(sc.bar);
+  __syncthreads();
+  return true;
+}
+
 // k_sweep_col with the tiles' new cells staged by TMA (3D FP32-split y and
 // z sweeps; maps of the launch's Uin and Ein in tm): the copy of a CTA's
 // first tile is issued before its loop, each later one during the update
@@ -938,9 +988,8 @@ template <class P, int DIM, int NMAT, int NH, int AX>
 __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT, 3)
     k_sweep_col_tma(const __grid_constant__ KArgs a, int K, const __grid_constant__ ColTma tm) {
   typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
-  typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
   constexpr int TD = 0;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned char ok1[SH::N1], ok2[SH::N2];
   __shared__ __align__(8) unsigned long long bar;
   const int nta = (a.n[AX] + SH::TL - 1) / SH::TL, ntt = (a.n[TD] + SH::TW - 1) / SH::TW;
@@ -950,27 +999,18 @@ __global__ void __launch_bounds__(Tile<P, DIM, AX>::NT, 3)
   b /= nch;
   const int tw = int(b % ntt), rr = int(b / ntt);
   const int t0 = ch * K, t1 = t0 + K < nta ? t0 + K : nta;
-  // a map the TMA unit reads must sit on a 64-byte boundary (parameters
-  // keep the type's 128-byte alignment; checked, not assumed)
-  if (reinterpret_cast<uintptr_t>(&tm) & 63) {
-    if (threadIdx.x == 0) report(a.err, ST_ECUDA, blockIdx.x, a.info->steps);
-    return;
-  }
   ColStage sc;
-  sc.tm = &tm;
-  sc.bar = smem_u32(&bar);
-  sc.parity = 0;
-  const uint32_t base = smem_u32(smem);
-  sc.dst = (base + uint32_t(CS::lo) + 127u) & ~127u;
-  sc.off = sc.dst - base;
-  sc.ok = true;
-  if (threadIdx.x == 0) mbar_init(sc.bar);
-  __syncthreads();
-  if (threadIdx.x == 0) col_issue<P, DIM, NMAT, NH, AX>(sc, t0, tw * SH::TW, rr);
+  if (!stage_setup<P, DIM, NMAT, NH, AX>(a, tm, sc, smem, &bar)) return;
+  if (threadIdx.x == 0) stage_issue<P, DIM, NMAT, NH, AX>(sc, t0, tw * SH::TW, rr);
+  sc.nw0 = tw * SH::TW;
+  sc.nrr = rr;
   bool first = true;
-  for (int ta = t0; ta < t1 && sc.ok; ++ta)
-    first = !sweep_tile<P, DIM, NMAT, NH, AX, 0, 1>(a, ta, tw, rr, first, ta + 1 < t1, smem, ok1,
+  for (int ta = t0; ta < t1 && sc.ok; ++ta) {
+    sc.next = ta + 1 < t1;
+    sc.nta = ta + 1;
+    first = !sweep_tile<P, DIM, NMAT, NH, AX, 0, 1>(a, ta, tw, rr, first, sc.next, smem, ok1,
                                                     ok2, &sc);
+  }
 }
 
 // ------------------------------------------------------------ batches ----

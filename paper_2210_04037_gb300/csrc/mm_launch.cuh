@@ -69,7 +69,7 @@ struct Launch {
     if constexpr (std::is_same<P, P32>::value && DIM == 3 && AX != 0 && NMAT == 2 && NH <= 1) {
       // tiles staged by TMA where the grid has maps for this state buffer
       // (two materials; mm_fp32_d3_tma.cu)
-      typedef ColStageShape<P, DIM, NMAT, NH, AX> CS;
+      typedef StageShape<P, DIM, NMAT, NH, AX> CS;
       const SweepTmaSet* ts = static_cast<const SweepTmaSet*>(a.tma);
       const int b = !ts ? -1 : (a.Uin == ts->U[0] ? 0 : (a.Uin == ts->U[1] ? 1 : -1));
       if (b >= 0 && ts->nlo == CS::NLO && ts->nhi == CS::NHI && ts->TL[AX - 1] == SH::TL &&
