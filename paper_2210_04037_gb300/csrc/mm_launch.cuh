@@ -19,6 +19,14 @@ __global__ void k_totals_final(const double* partial, int nblocks, int nq, doubl
 #define MM_SRC_BATCHES 4
 #endif
 
+// Whole waves of resident CTAs the bounded FP32-split source kernel runs
+// as (0: the 2432-CTA cap, 3.2 waves at 5 CTAs per SM, whose last part-wave
+// left most SMs idle).  Measured on the 256^3 cylinder (steps 6-35): cap
+// 1.66 ms, one wave 1.48, two 1.53, four 1.55.
+#ifndef MM_SRC_WAVES
+#define MM_SRC_WAVES 1
+#endif
+
 inline int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 16) b = 152LL * 16;
@@ -143,7 +151,21 @@ struct Launch {
         bool bounded = false;
         if constexpr (P::split) {
           if (a.ncell >= 152LL * 16 * 128 * MM_SRC_BATCHES) {
-            k_sources<P, DIM, NMAT, NH, 5><<<g, 128, 0, s>>>(a);
+            // MM_SRC_WAVES whole waves of resident CTAs (> 0), or the
+            // 2432-CTA cap (0)
+            int gw = g;
+            if (MM_SRC_WAVES > 0) {
+              int dev = 0, sms = 0, per = 0;
+              cudaError_t e = cudaGetDevice(&dev);
+              if (e == cudaSuccess)
+                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+              if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per, k_sources<P, DIM, NMAT, NH, 5>, 128, 0);
+              if (e != cudaSuccess) return e;
+              gw = sms * (per > 0 ? per : 1) * MM_SRC_WAVES;
+            }
+            k_sources<P, DIM, NMAT, NH, 5><<<gw, 128, 0, s>>>(a);
             bounded = true;
           }
         }
