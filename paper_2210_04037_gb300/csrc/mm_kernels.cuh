@@ -284,12 +284,22 @@ template <> struct Tile<P64, 3, 0> { static constexpr int TL = 28, TW = 2, NT = 
 template <> struct Tile<P64, 3, 1> { static constexpr int TL = 12, TW = 4, NT = 64; };
 template <> struct Tile<P64, 3, 2> { static constexpr int TL = 12, TW = 4, NT = 64; };
 // FP32-split: 128-thread CTAs, transverse width 8 (32-byte sectors of x).
+// 3D: 192-thread CTAs, two per SM (the same twelve warps as three of 128,
+// which the registers and shared memory allow either way).  The x sweep's
+// tile is one 32-cell row per warp in phase 1 (28 x 6); the y and z sweeps
+// run columns of 12 x 16 tiles (each tile's 192 new cells, one per thread,
+// in rows of 64 bytes along x).  Measured on the 256^3 cylinder over steps
+// 16-25 (per-kernel CUDA events, identical results): x 28 x 4 -> 28 x 6
+// 3.81 -> 3.63 ms; y 16 x 8 -> 12 x 16 3.62 -> 3.08, z 3.07 -> 2.89.  Not
+// kept: one 384-thread CTA per SM (x 28 x 12: 3.91; y, z 16 x 24: 3.41,
+// 3.05), 16 x 12 (y 3.10, z 2.94), 8 x 24 (y 4.80, z 4.39), 16 x 16 with
+// 256 threads and one CTA per SM (y 3.66, z 3.29), x 60 x 3 (4.07).
 template <> struct Tile<P32, 1, 0> { static constexpr int TL = 124, TW = 1, NT = 128; };
 template <> struct Tile<P32, 2, 0> { static constexpr int TL = 60, TW = 2, NT = 128; };
 template <> struct Tile<P32, 2, 1> { static constexpr int TL = 28, TW = 8, NT = 256; };
-template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
-template <> struct Tile<P32, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
-template <> struct Tile<P32, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
+template <> struct Tile<P32, 3, 0> { static constexpr int TL = 28, TW = 6, NT = 192; };
+template <> struct Tile<P32, 3, 1> { static constexpr int TL = 12, TW = 16, NT = 192; };
+template <> struct Tile<P32, 3, 2> { static constexpr int TL = 12, TW = 16, NT = 192; };
 // Second shape per axis, one of the two the batched sweep's autotuner times
 // (the cell arithmetic does not depend on the tile, so either gives the same
 // bits): longer tiles along the sweep, narrower across it.
@@ -297,6 +307,11 @@ template <class P, int DIM, int AX> struct Tile<P, DIM, AX, 1> : Tile<P, DIM, AX
 // grids that can open void take the single-grid tiles of their precision
 template <int DIM, int AX> struct Tile<P64V, DIM, AX, 0> : Tile<P64, DIM, AX, 0> {};
 template <int DIM, int AX> struct Tile<P32V, DIM, AX, 0> : Tile<P32, DIM, AX, 0> {};
+// but 3D void grids keep 128-thread CTAs: their column kernels take 218-228
+// registers, so a 192-thread CTA would run alone on an SM
+template <> struct Tile<P32V, 3, 0> { static constexpr int TL = 28, TW = 4, NT = 128; };
+template <> struct Tile<P32V, 3, 1> { static constexpr int TL = 16, TW = 8, NT = 128; };
+template <> struct Tile<P32V, 3, 2> { static constexpr int TL = 16, TW = 8, NT = 128; };
 template <> struct Tile<P32, 1, 0, 1> { static constexpr int TL = 60, TW = 1, NT = 64; };
 template <> struct Tile<P32, 2, 0, 1> { static constexpr int TL = 60, TW = 2, NT = 128; };
 template <> struct Tile<P32, 2, 1, 1> { static constexpr int TL = 28, TW = 4, NT = 128; };
@@ -982,10 +997,10 @@ __device__ __forceinline__ bool stage_setup(const KArgs& a, const ColTma& tm, Co
 // z sweeps; maps of the launch's Uin and Ein in tm): the copy of a CTA's
 // first tile is issued before its loop, each later one during the update
 // of the tile before it, so a tile's loads overlap the previous tile's work.
-// Registers bounded for three CTAs per SM, as many as the shared memory of
-// the 16 x 8 tiles holds (unbounded, ptxas took 210: two CTAs).
+// Registers bounded for two 192-thread CTAs per SM, as many as the shared
+// memory of the 12 x 16 tiles holds (unbounded, ptxas took about 210).
 template <class P, int DIM, int NMAT, int NH, int AX>
-__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT, 3)
+__global__ void __launch_bounds__(Tile<P, DIM, AX>::NT, 2)
     k_sweep_col_tma(const __grid_constant__ KArgs a, int K, const __grid_constant__ ColTma tm) {
   typedef SweepShape<P, DIM, NMAT, NH, AX, 0> SH;
   constexpr int TD = 0;

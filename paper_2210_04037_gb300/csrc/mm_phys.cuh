@@ -360,6 +360,9 @@ __device__ __forceinline__ bool log_series(const R B[9], R L[9]) {
   int K;
   if (n2 <= R(4e-4)) K = 2;         // |z| <= 0.0102: z^4/5 < 3e-9
   else if (n2 <= R(1e-2)) K = 3;    // |z| <= 0.0527: z^6/7 < 4e-9
+  else if (n2 <= R(0.04)) K = 4;    // |z| <= 0.112: z^8/9 < 3e-9
+  else if (n2 <= R(0.09)) K = 5;    // |z| <= 0.177: z^10/11 < 3e-9
+  else if (n2 <= R(0.16)) K = 6;    // |z| <= 0.25: z^12/13 < 5e-9
   else if (n2 <= R(0.25)) K = 7;    // |z| <= 1/3: z^14/15 < 2e-8
   else return false;
   // C = 2I + B (eigenvalues in [1.5, 2.5]); C^-1 = adj(C)/det(C)
