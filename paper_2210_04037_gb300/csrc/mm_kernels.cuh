@@ -1520,6 +1520,26 @@ __device__ __forceinline__ void src_dequeue(const KArgs& a, SrcQueue<P, DIM, NMA
                                 q.v[4 * NMAT][s], q.v[4 * NMAT + 1][s], q.cy[s] != 0, dt, step);
 }
 
+// L2 prefetch of the stored state of the 32 cells c0 .. c0 + 31 (FP32-split
+// single grids; c0 < ncell): lane k of the warp asks for the line of float
+// slot k (slot oE holds nothing in the split form), two lanes for the FP64
+// rho E.  A hint only: nothing is read into registers, and every address lies
+// inside the state arrays.
+template <class P, int DIM, int NMAT, int NH>
+__device__ __forceinline__ void prefetch_cells_l2(const KArgs& a, long long c0) {
+  typedef Lay<DIM, NMAT, NH> L;
+  static_assert(P::split && sizeof(typename P::S) == 4 && L::NF + 2 < 32, "one lane per slot");
+  const int lane = threadIdx.x & 31;
+  const void* p = nullptr;
+  if (lane <= L::NF && lane != L::oE && lane < a.nfield)
+    p = static_cast<const float*>(a.Uin) + (long long)lane * a.ncell + c0;
+  else if (lane == L::NF + 1)
+    p = a.Ein + c0;
+  else if (lane == L::NF + 2)
+    p = a.Ein + (c0 + 16 < a.ncell ? c0 + 16 : a.ncell - 1);
+  if (p) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Per-cell sources after the sweeps (in place): renormalise det Fbar = 1,
 // radial return in Hencky space to the perturbed yield stress (Newton on
 // the plastic increment in FP64), then RK4 damage.  Split path: cells
@@ -1706,8 +1726,19 @@ __global__ void __launch_bounds__(128, MINB) k_sources(KArgs a) {
     __syncthreads();
   }
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < a.ncell; base += stride)
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < a.ncell; base += stride) {
+    // the warp's cells of the next pass are asked into L2 while this pass
+    // computes.  Measured on the 256^3 cylinder (one wave, 5 CTAs per SM),
+    // ms per step over steps 6-15 / 16-25 / 26-35: 1.09 / 1.38 / 1.93 ->
+    // 1.03 / 1.32 / 1.89 (the same prefetch in the CFL kernel, 64 registers,
+    // made it slower: 0.447 -> 0.529 ms; in the x sweep, one wave of tiles
+    // ahead, it gained 1 %)
+    if constexpr (std::is_same<P, P32>::value) {
+      const long long nb = base + stride + (threadIdx.x & ~31);
+      if (nb < a.ncell) prefetch_cells_l2<P, DIM, NMAT, NH>(a, nb);
+    }
     sources_cells<P, DIM, NMAT, NH>(a, base, qs, dt, step);
+  }
   sources_flush<P, DIM, NMAT, NH>(a, qs, dt, step);
 }
 
