@@ -283,7 +283,7 @@ template <> struct Tile<P64, 2, 1> { static constexpr int TL = 12, TW = 4, NT = 
 template <> struct Tile<P64, 3, 0> { static constexpr int TL = 28, TW = 2, NT = 64; };
 template <> struct Tile<P64, 3, 1> { static constexpr int TL = 12, TW = 4, NT = 64; };
 template <> struct Tile<P64, 3, 2> { static constexpr int TL = 12, TW = 4, NT = 64; };
-// FP32-split: 128-thread CTAs, transverse width 8 (32-byte sectors of x).
+// FP32-split 1D and 2D: 128-thread CTAs (256 for the 2D y sweep).
 // 3D: 192-thread CTAs, two per SM (the same twelve warps as three of 128,
 // which the registers and shared memory allow either way).  The x sweep's
 // tile is one 32-cell row per warp in phase 1 (28 x 6); the y and z sweeps
