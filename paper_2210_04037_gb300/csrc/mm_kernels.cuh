@@ -1732,8 +1732,10 @@ __global__ void __launch_bounds__(128, MINB) k_sources(KArgs a) {
     // ms per step over steps 6-15 / 16-25 / 26-35: 1.09 / 1.38 / 1.93 ->
     // 1.03 / 1.32 / 1.89 (the same prefetch in the CFL kernel, 64 registers,
     // made it slower: 0.447 -> 0.529 ms; in the x sweep, one wave of tiles
-    // ahead, it gained 1 %)
-    if constexpr (std::is_same<P, P32>::value) {
+    // ahead, it gained 1 %).  Only the one-wave instantiation (MINB 5) takes
+    // it: on the 512^2 ring (512 CTAs, four passes each) it cost 2-3 % of
+    // the source kernel (44.4 / 48.0 / 51.3 -> 45.6 / 49.3 / 52.8 us).
+    if constexpr (std::is_same<P, P32>::value && MINB > 1) {
       const long long nb = base + stride + (threadIdx.x & ~31);
       if (nb < a.ncell) prefetch_cells_l2<P, DIM, NMAT, NH>(a, nb);
     }
