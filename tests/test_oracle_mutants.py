@@ -3,8 +3,13 @@ planted (a sign, a side, an index, a skipped term in the shear-wave branch
 of the Riemann solver, the reflective ghosts, the 3D tangential loop, the
 totals' cell volume, the rule for a contact at rest, the void-opening
 modifier's tension test, critical-damage test, surface speed, gap volume,
-mass flux and the void's share of the stress) are each caught by at least
-one check of tests/pins_void.py or tests/pins_waves.py.  Each copy is compiled to a
+mass flux and the void's share of the stress, the seeding; the cold and
+shear pressures, the Steinberg modulus and Grueneisen derivative, the
+Hencky strain, the perturbed yield stress, the return factor and
+equivalent stress, the unimodular normalisation, the RK4 weights, the
+Bonora exponent, the rate term, the triaxiality and the lattice weights)
+are each caught by at least one check of tests/pins_sources.py,
+tests/pins_void.py or tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
 import concurrent.futures as cf
 import os
@@ -93,6 +98,49 @@ MUTANTS = [
     ("seed_threshold_inverted",
      "if (!(void_at(g, ix) > 0.5)) continue;",
      "if (!(void_at(g, ix) < 0.5)) continue;"),
+    # closures, Hencky strain, plastic return, damage, lookup (pins_sources.py)
+    ("cold_pressure_sign",
+     "const double pc = psi * m->K0 / (2.0 * a * a) * (2.0 * a * q * ea - q * q);",
+     "const double pc = psi * m->K0 / (2.0 * a * a) * (2.0 * a * q * ea + q * q);"),
+    ("shear_pressure_exponent",
+     "const double ps = m->beta * G * J2;",
+     "const double ps = (m->beta + 1.0) * G * J2;"),
+    ("steinberg_dG_sign",
+     "const double q1 = u * (pc1 - pc0 / (3.0 * rho));",
+     "const double q1 = u * (pc1 + pc0 / (3.0 * rho));"),
+    ("grueneisen_derivative_sign",
+     "out[5] = (-m->Gamma1 * u / 3.0 - m->gamma_s * m->Gamma2 * g2) / Gam;",
+     "out[5] = (-m->Gamma1 * u / 3.0 + m->gamma_s * m->Gamma2 * g2) / Gam;"),
+    ("hencky_without_half",
+     "for (int k = 0; k < 3; ++k) h[k] = 0.5 * log(lam[k]);",
+     "for (int k = 0; k < 3; ++k) h[k] = log(lam[k]);"),
+    ("yield_without_perturbation",
+     "const double wgt = phi[l] * phihat * psi;",
+     "const double wgt = phi[l] * psi;"),
+    ("return_factor_2G",
+     "const double k = (str - 3.0 * Gm * dl) / str;",
+     "const double k = (str - 2.0 * Gm * dl) / str;"),
+    ("equivalent_stress_factor",
+     "const double str = sqrt(6.0) * Gm * J;",
+     "const double str = sqrt(3.0) * Gm * J;"),
+    ("det_not_renormalised",
+     "const double dt3 = cbrt(det3(F));",
+     "const double dt3 = 1.0;"),
+    ("rk4_drops_k3",
+     "double Dn = D + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);",
+     "double Dn = D + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k2 + k4);"),
+    ("bonora_exponent",
+     "pow(Dc - D, (aD - 1.0) / aD)",
+     "pow(Dc - D, (aD - 1.0))"),
+    ("rate_log_inverted",
+     "const double r = 1.0 + m->c3 * log(dl / (dt * m->edot0));",
+     "const double r = 1.0 + m->c3 * log(dt * m->edot0 / dl);"),
+    ("lookup_weights_swapped",
+     "wt *= b ? w[k] : 1.0 - w[k];",
+     "wt *= b ? 1.0 - w[k] : w[k];"),
+    ("triaxiality_poisson_factor",
+     "3.0 * (1.0 - 2.0 * poisson) * (rho0 / rho) * (x * x);",
+     "3.0 * (1.0 - poisson) * (rho0 / rho) * (x * x);"),
     ("void_stress_not_scaled",
      "const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;",
      "const double pm = ax->p;"),
@@ -109,10 +157,11 @@ def _build(name, old, new, tmp):
 
 
 def _check(lib):
-    # the void checks first (a second or so), then the shear, wall, 3D and
-    # totals checks
+    # the closure, return, damage and lookup checks first (a second), then
+    # the void checks (a second or so), then the shear, wall, 3D and totals
+    # checks
     out = ""
-    for mod in ("pins_void.py", "pins_waves.py"):
+    for mod in ("pins_sources.py", "pins_void.py", "pins_waves.py"):
         r = subprocess.run([sys.executable, os.path.join(HERE, mod), lib, "all"],
                            capture_output=True, text=True, timeout=900,
                            env=dict(os.environ, OMP_NUM_THREADS="2"))

@@ -262,6 +262,20 @@ def test_elastic_state_is_unchanged_and_critical_damage_removes_strength():
     assert de > 0 and _seq(Fn, G) == pytest.approx((1 - Dout) * m["c1"], rel=1e-9)
 
 
+def test_source_step_makes_fbar_unimodular():
+    """Sec. 2.1 takes the unimodular part Vbar = det(V)^(-1/3) V (reading R2:
+    det Fbar is set to 1 at the start of the source step): an elastic state
+    with det Fbar != 1 leaves the return as F / cbrt(det F), with no plastic
+    increment."""
+    m = W.cube()
+    F = np.diag([1.0003, 0.9999, 1.0])
+    F[0, 1] = 1e-6
+    Fn, de = _return([m], [1.0], [m["rho0"]], [0.0], [0.0], 1.0, 1e-9, F.copy())
+    assert de == 0.0
+    assert np.allclose(Fn, F / np.cbrt(np.linalg.det(F)), rtol=0, atol=1e-15)
+    assert np.linalg.det(Fn) == pytest.approx(1.0, abs=1e-14)
+
+
 def test_rate_dependent_return_satisfies_yield_condition():
     """With hardening and rate terms the returned state still satisfies
     sigma_eq = phi sigma_Y(eps + d, d/dt) (Johnson-Cook: (c1 + c2 eps^n)
