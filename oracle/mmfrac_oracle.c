@@ -1141,7 +1141,10 @@ double or_lookup(int dim, const float* phi0, const long pn[3],
 /* Sec. 4.3: simple model), RK4 over the step (Sec. 3.1).                    */
 /* ------------------------------------------------------------------------ */
 
-/* Triaxiality-dependent threshold plastic strain (Eq. after the gate). */
+/* Triaxiality-dependent threshold plastic strain (Eq. after the gate).
+ * Pinned at R_t = 1 only (it reduces to eps_thresh there, and the Bonora
+ * closed form runs at R_t = 1): away from R_t = 1 the printed formula is
+ * written out with no independent check, parity unpinned there. */
 double or_eps_thresh(double eps_t, double eps_c, double n, double Rt) {
   const double num = pow(eps_c, 2.0 * n) - pow(eps_t, 2.0 * n);
   const double den = pow(eps_c, 2.0 * n / Rt) - pow(eps_t, 2.0 * n / Rt);
