@@ -7,9 +7,12 @@ mass flux and the void's share of the stress, the seeding; the cold and
 shear pressures, the Steinberg modulus and Grueneisen derivative, the
 Hencky strain, the perturbed yield stress, the return factor and
 equivalent stress, the unimodular normalisation, the RK4 weights, the
-Bonora exponent, the rate term, the triaxiality and the lattice weights)
-are each caught by at least one check of tests/pins_sources.py,
-tests/pins_void.py or tests/pins_waves.py.  Each copy is compiled to a
+Bonora exponent, the rate term, the triaxiality and the lattice weights;
+the half step's length, the limiter, the slope's sign, the signs of the
+non-conservative terms of Fbar, phi and the update, X's term dropped, the
+CFL speed without c_L, the WENO3 weights) are each caught by at least one
+check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
+tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
 import concurrent.futures as cf
 import os
@@ -141,6 +144,34 @@ MUTANTS = [
     ("triaxiality_poisson_factor",
      "3.0 * (1.0 - 2.0 * poisson) * (rho0 / rho) * (x * x);",
      "3.0 * (1.0 - poisson) * (rho0 / rho) * (x * x);"),
+    # the sweep (pins_step.py, pins_waves.py)
+    ("half_step_full_length",
+     "      const double inc = 0.5 * lam * ((FL[k] - FR[k]) + nc[k]);",
+     "      const double inc = lam * ((FL[k] - FR[k]) + nc[k]);"),
+    ("limiter_not_harmonic",
+     "  if (a * b > 0.0) return 2.0 * a * b / (a + b);",
+     "  if (a * b > 0.0) return a * b / (a + b);"),
+    ("slope_sign_left_face",
+     "    wL[k] = wc[k] - 0.5 * s;",
+     "    wL[k] = wc[k] + 0.5 * s;"),
+    ("fbar_advection_sign",
+     "    nc[g->o_F + c] = (2.0 / 3.0) * ac->F[3 * i + j] * du - ac->u[i] * dFrow[j];",
+     "    nc[g->o_F + c] = (2.0 / 3.0) * ac->F[3 * i + j] * du + ac->u[i] * dFrow[j];"),
+    ("phi_noncons_sign",
+     "  for (int l = 0; l + 1 < g->nmat; ++l) nc[g->o_phi + l] = wc[g->o_phi + l] * du;",
+     "  for (int l = 0; l + 1 < g->nmat; ++l) nc[g->o_phi + l] = -wc[g->o_phi + l] * du;"),
+    ("X_noncons_dropped",
+     "  for (int k = 0; k < g->dim; ++k) nc[g->o_X + k] = wc[g->o_X + k] * du;",
+     "  for (int k = 0; k < g->dim; ++k) nc[g->o_X + k] = 0.0;"),
+    ("update_noncons_sign",
+     "          uc[k] + lam * ((FXr[(e - 1) * nf + k] - FX[e * nf + k]) + nc[k]);",
+     "          uc[k] + lam * ((FXr[(e - 1) * nf + k] - FX[e * nf + k]) - nc[k]);"),
+    ("cfl_without_sound_speed",
+     "    v += ax.cL;",
+     "    v += 0.0 * ax.cL + 1.0;"),
+    ("weno3_weights_swapped",
+     "  const double a1 = (2.0 / 3.0) / (e1 * e1);",
+     "  const double a1 = (1.0 / 3.0) / (e1 * e1);"),
     ("void_stress_not_scaled",
      "const double pm = g->void_l >= 0 ? ax->p * (1.0 - phi[g->void_l]) : ax->p;",
      "const double pm = ax->p;"),
@@ -156,12 +187,22 @@ def _build(name, old, new, tmp):
     return O.compile_oracle(path, os.path.join(tmp, f"lib{name}.so"))
 
 
-def _check(lib):
-    # the closure, return, damage and lookup checks first (a second), then
-    # the void checks (a second or so), then the shear, wall, 3D and totals
-    # checks
+# mistakes in the sweep are looked for first by the whole-step checks
+STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_face",
+              "phi_noncons_sign", "X_noncons_dropped", "update_noncons_sign",
+              "weno3_weights_swapped"}
+
+
+def _check(name, lib):
+    # the closure, return, damage and lookup checks first (a second), the
+    # void checks (a second or so), the shear, wall, 3D and totals checks,
+    # then the whole-step checks (ten seconds), which go first for a mistake
+    # in the sweep
+    mods = ["pins_sources.py", "pins_void.py", "pins_waves.py", "pins_step.py"]
+    if name in STEP_FIRST:
+        mods = ["pins_step.py"] + [m for m in mods if m != "pins_step.py"]
     out = ""
-    for mod in ("pins_sources.py", "pins_void.py", "pins_waves.py"):
+    for mod in mods:
         r = subprocess.run([sys.executable, os.path.join(HERE, mod), lib, "all"],
                            capture_output=True, text=True, timeout=900,
                            env=dict(os.environ, OMP_NUM_THREADS="2"))
@@ -175,7 +216,7 @@ def test_every_planted_mistake_is_caught():
     with tempfile.TemporaryDirectory() as tmp:
         libs = {name: _build(name, old, new, tmp) for name, old, new in MUTANTS}
         with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-            res = dict(zip(libs, ex.map(_check, libs.values())))
+            res = dict(zip(libs, ex.map(_check, libs, libs.values())))
     survived = {k: v[1] for k, v in res.items() if v[0] == 0}
     assert not survived, f"mistakes no pin catches: {survived}"
     for k, (rc, out) in res.items():
@@ -186,5 +227,5 @@ def test_unplanted_copy_passes():
     # the same build route with nothing changed passes every check
     with tempfile.TemporaryDirectory() as tmp:
         lib = _build("unchanged", "#include <float.h>", "#include <float.h>", tmp)
-        rc, out = _check(lib)
+        rc, out = _check("unchanged", lib)
     assert rc == 0, out
