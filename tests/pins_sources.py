@@ -1,5 +1,6 @@
-"""The closure, Hencky-strain, plastic-return, damage and perturbation-lookup
-pins of tests/test_oracle_pins.py, run against a given oracle library, so
+"""The closure (with the mixture rule and sound speed), Hencky-strain,
+plastic-return, damage and perturbation-lookup pins of
+tests/test_oracle_pins.py, run against a given oracle library, so
 that copies of the oracle with a planted mistake in those parts can be
 checked too (tests/test_oracle_mutants.py).  No GPU.
 
@@ -23,6 +24,8 @@ CHECKS = {
     "moduli": T.test_linear_moduli_at_reference_density,
     "steinberg": T.test_steinberg_closure_at_reference_and_its_grueneisen_derivative,
     "steinberg_sound_speed": T.test_steinberg_sound_speed_is_isentropic_derivative,
+    "mixture_rule": T.test_ideal_gas_mixture_pressure_is_textbook_rule,
+    "mixture_sound_speed": T.test_mixture_sound_speed_is_isentropic_derivative,
     "return_on_yield_surface": lambda: [
         T.test_perfectly_plastic_return_lands_on_perturbed_yield_surface(ph, Dm)
         for ph, Dm in ((1.0, 0.0), (1.13, 0.0), (0.87, 0.3))],

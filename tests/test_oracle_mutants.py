@@ -8,9 +8,11 @@ shear pressures, the Steinberg modulus and Grueneisen derivative, the
 Hencky strain, the perturbed yield stress, the return factor and
 equivalent stress, the unimodular normalisation, the RK4 weights, the
 Bonora exponent, the rate term, the triaxiality and the lattice weights;
-the half step's length, the limiter, the slope's sign, the signs of the
-non-conservative terms of Fbar, phi and the update, X's term dropped, the
-CFL speed without c_L, the WENO3 weights) are each caught by at least one
+the mixture's 1/Gamma weights, mass weights, Gamma' term and shear part
+of the sound speed; the half step's length, the limiter, the slope's sign,
+the signs of the non-conservative terms of Fbar, phi and the update, X's
+term dropped, the CFL speed without c_L, the WENO3 weights, the Riemann
+solver's wave speed, star speed and star side) are each caught by at least one
 check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
 tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
@@ -144,6 +146,32 @@ MUTANTS = [
     ("triaxiality_poisson_factor",
      "3.0 * (1.0 - 2.0 * poisson) * (rho0 / rho) * (x * x);",
      "3.0 * (1.0 - poisson) * (rho0 / rho) * (x * x);"),
+    # the mixture rule and sound speed (pins_sources.py)
+    ("sound_speed_without_inverse_gamma",
+     "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
+     "    s += (arho[l] / ax->rho) * cl2;"),
+    ("sound_speed_volume_weights",
+     "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
+     "    s += phi[l] * (1.0 / Gam) * cl2;"),
+    ("sound_speed_without_dgamma",
+     "    const double cl2 = mx->th[l][2] + (Gam + 1.0 + mx->th[l][5]) * (ax->p - mx->th[l][1]) /",
+     "    const double cl2 = mx->th[l][2] + (Gam + 1.0) * (ax->p - mx->th[l][1]) /"),
+    ("mixture_xi_times_gamma",
+     "    mx->xi += phi[l] / mx->th[l][4];",
+     "    mx->xi += phi[l] * mx->th[l][4];"),
+    ("shear_speed_factor",
+     "  const double cL2 = c2 + (4.0 / 3.0) * mx->Gmix / ax->rho;",
+     "  const double cL2 = c2 + mx->Gmix / ax->rho;"),
+    # the Riemann solver's wave and star speeds (pins_step.py)
+    ("wave_speed_left_only",
+     "  const double SL = a1 < a2 ? a1 : a2;",
+     "  const double SL = a1;"),
+    ("star_speed_traction_sign",
+     "  const double Ss = (sL - sR + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /",
+     "  const double Ss = (sR - sL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /"),
+    ("star_side_swapped",
+     "  star_side_flux(g, d, Ss >= 0.0, UL, aL, UR, aR, SL, SR, Ss, Fo, uface, Frow);",
+     "  star_side_flux(g, d, Ss < 0.0, UL, aL, UR, aR, SL, SR, Ss, Fo, uface, Frow);"),
     # the sweep (pins_step.py, pins_waves.py)
     ("half_step_full_length",
      "      const double inc = 0.5 * lam * ((FL[k] - FR[k]) + nc[k]);",
@@ -190,7 +218,8 @@ def _build(name, old, new, tmp):
 # mistakes in the sweep are looked for first by the whole-step checks
 STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_face",
               "phi_noncons_sign", "X_noncons_dropped", "update_noncons_sign",
-              "weno3_weights_swapped"}
+              "weno3_weights_swapped", "wave_speed_left_only", "star_speed_traction_sign",
+              "star_side_swapped"}
 
 
 def _check(name, lib):

@@ -154,6 +154,54 @@ def test_steinberg_sound_speed_is_isentropic_derivative():
         assert cL**2 - 4 / 3 * G / rho == pytest.approx(c2, rel=1e-6), (eta, e)
 
 
+def _mixture_state(mats, phi0, rho, p, scale=0.0, e_add=0.0):
+    """A uniform 1D two-material grid at rest (F = I): material 0 at volume
+    fraction phi0, phase densities rho, pressure p; then every partial
+    density scaled by 1 + scale at fixed fractions and rho e raised by
+    e_add.  Returns its pressure, its CFL signal speed (c_L at rest), the
+    density and rho e of the unscaled state."""
+    n = 4
+    c = W.Case("mix", 1, [n, 1, 1], [0.0, 0.0, 0.0], [1e-3, 1.0, 1.0], [0, 0], mats, None)
+    lay = c.layout
+    c.prim = W.blank_prim(lay, n)
+    c.prim[lay.o_phi] = phi0
+    c.prim[lay.o_rho] = rho[0]
+    c.prim[lay.o_rho + 1] = rho[1]
+    c.prim[lay.o_p] = p
+    c.prim[lay.o_X] = c.centres()[0]
+    g = OracleGrid(c)
+    U = g.read(False)
+    r0 = U[lay.o_rho][0] + U[lay.o_rho + 1][0]
+    re0 = U[lay.o_p][0]
+    U[lay.o_rho] *= 1.0 + scale
+    U[lay.o_rho + 1] *= 1.0 + scale
+    U[lay.o_p] += e_add
+    g.write_conserved(U)
+    _, smax = g.cfl_dt()
+    return g.read()[lay.o_p][0], smax, r0, re0
+
+
+def test_mixture_sound_speed_is_isentropic_derivative():
+    """The mixture's sound speed (the CFL signal speed at rest less the
+    shear part 4/3 G_mix/rho, R6) equals dp/drho of whole two-material cell
+    states compressed at fixed volume fractions (phi is carried with the
+    flow, Sec. 2.1) along d(rho e) = (rho e + p) drho/rho (de = p drho/rho^2),
+    by central differences: two ideal gases of unequal gamma, and CuBe in
+    air (Gamma 2.0 and 0.4, shear on)."""
+    mats = [dict(W.air(), gamma_gas=1.4), dict(W.air(), gamma_gas=1.67)]
+    cube = W.cube(damage="none", plastic=False)
+    for mats, phi0, rho, p in ((mats, 0.3, (1.2, 0.4), 2e5),
+                               ([cube, W.air()], 0.4, (cube["rho0"] * 1.01, 1.5), 3e8),
+                               ([cube, W.air()], 0.02, (cube["rho0"] * 0.995, 1.1), 1e5)):
+        p0, cL, r0, re0 = _mixture_state(mats, phi0, rho, p)
+        eps = 1e-6
+        pp = _mixture_state(mats, phi0, rho, p, eps, eps * (re0 + p0))[0]
+        pm = _mixture_state(mats, phi0, rho, p, -eps, -eps * (re0 + p0))[0]
+        c2 = (pp - pm) / (2 * eps * r0)
+        G = phi0 * thermo(mats[0], rho[0])["G"]
+        assert cL ** 2 - 4 / 3 * G / r0 == pytest.approx(c2, rel=1e-5), (mats[0].get("K0"), phi0)
+
+
 def test_longitudinal_sound_speed_of_cube_and_air():
     """The CFL signal speed at rest equals sqrt((K0 + 4/3 G0)/rho0) for CuBe
     (about 4922 m/s, 1D-strain textbook speed) and sqrt(gamma p/rho) for air."""
