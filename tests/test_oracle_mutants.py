@@ -12,7 +12,8 @@ the mixture's 1/Gamma weights, mass weights, Gamma' term and shear part
 of the sound speed; the half step's length, the limiter, the slope's sign,
 the signs of the non-conservative terms of Fbar, phi and the update, X's
 term dropped, the CFL speed without c_L, the WENO3 weights, the Riemann
-solver's wave speed, star speed and star side) are each caught by at least one
+solver's wave speed, star speed and star side, the physical flux's stress
+sign, stress row, Fbar row and history transport) are each caught by at least one
 check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
 tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
@@ -146,6 +147,19 @@ MUTANTS = [
     ("triaxiality_poisson_factor",
      "3.0 * (1.0 - 2.0 * poisson) * (rho0 / rho) * (x * x);",
      "3.0 * (1.0 - poisson) * (rho0 / rho) * (x * x);"),
+    # the physical flux (pins_step.py)
+    ("momentum_flux_stress_sign",
+     "    f[g->o_mom + k] = u[g->o_mom + k] * ud - ax->sig[3 * k + d];",
+     "    f[g->o_mom + k] = u[g->o_mom + k] * ud + ax->sig[3 * k + d];"),
+    ("energy_flux_stress_row",
+     "              (ax->sig[3 * d + 0] * ax->u[0] + ax->sig[3 * d + 1] * ax->u[1] +",
+     "              (ax->sig[3 * d + 0] * ax->u[0] + ax->sig[3 * d + 1] * ax->u[0] +"),
+    ("fbar_flux_row",
+     "                             : u[g->o_F + c] * ud - ax->F[3 * d + j] * ax->u[i];",
+     "                             : u[g->o_F + c] * ud - ax->F[3 * i + j] * ax->u[d];"),
+    ("history_not_advected",
+     "  for (int k = 0; k < 2 * g->nhist; ++k) f[g->o_hist + k] = u[g->o_hist + k] * ud;",
+     "  for (int k = 0; k < 2 * g->nhist; ++k) f[g->o_hist + k] = 0.0;"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
@@ -219,7 +233,8 @@ def _build(name, old, new, tmp):
 STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_face",
               "phi_noncons_sign", "X_noncons_dropped", "update_noncons_sign",
               "weno3_weights_swapped", "wave_speed_left_only", "star_speed_traction_sign",
-              "star_side_swapped"}
+              "star_side_swapped", "momentum_flux_stress_sign", "energy_flux_stress_row",
+              "fbar_flux_row", "history_not_advected"}
 
 
 def _check(name, lib):
