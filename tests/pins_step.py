@@ -26,6 +26,7 @@ CHECKS = {
     "equilibrium_copper_in_gas": T.test_interface_equilibrium_copper_in_gas,
     "conservation": T.test_conservation_on_periodic_box,
     "mirror": T.test_mirror_symmetry,
+    "anisotropic_time_step": T.test_time_step_is_stable_on_an_anisotropic_grid,
     "elastic_wave_speed": T.test_elastic_wave_speed_in_cube,
     "elastic_precursor": T.test_elastic_precursor_of_plastic_impact,
     "second_order": T.test_second_order_convergence_on_smooth_elastic_wave,

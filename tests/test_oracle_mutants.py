@@ -13,7 +13,8 @@ of the sound speed; the half step's length, the limiter, the slope's sign,
 the signs of the non-conservative terms of Fbar, phi and the update, X's
 term dropped, the CFL speed without c_L, the WENO3 weights, the Riemann
 solver's wave speed, star speed and star side, the physical flux's stress
-sign, stress row, Fbar row and history transport) are each caught by at least one
+sign, stress row, Fbar row and history transport, the time step from the
+largest spacing, a phase-density bound of 2 for e) are each caught by at least one
 check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
 tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
@@ -160,6 +161,12 @@ MUTANTS = [
     ("history_not_advected",
      "  for (int k = 0; k < 2 * g->nhist; ++k) f[g->o_hist + k] = u[g->o_hist + k] * ud;",
      "  for (int k = 0; k < 2 * g->nhist; ++k) f[g->o_hist + k] = 0.0;"),
+    ("cfl_largest_spacing",
+     "    if (g->dx[k] < dxm) dxm = g->dx[k];",
+     "    if (g->dx[k] > dxm) dxm = g->dx[k];"),
+    ("phase_bound_factor_two",
+     "  const double e = 2.718281828459045;\n  for (int l = 0; l < g->nmat; ++l) {\n    const double r0 = w_rec",
+     "  const double e = 2.0;\n  for (int l = 0; l < g->nmat; ++l) {\n    const double r0 = w_rec"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
@@ -234,7 +241,8 @@ STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_
               "phi_noncons_sign", "X_noncons_dropped", "update_noncons_sign",
               "weno3_weights_swapped", "wave_speed_left_only", "star_speed_traction_sign",
               "star_side_swapped", "momentum_flux_stress_sign", "energy_flux_stress_row",
-              "fbar_flux_row", "history_not_advected"}
+              "fbar_flux_row", "history_not_advected", "cfl_largest_spacing",
+              "phase_bound_factor_two"}
 
 
 def _check(name, lib):
