@@ -14,12 +14,15 @@ the signs of the non-conservative terms of Fbar, phi and the update, X's
 term dropped, the CFL speed without c_L, the WENO3 weights, the Riemann
 solver's wave speed, star speed and star side, the physical flux's stress
 sign, stress row, Fbar row and history transport, the time step from the
-largest spacing, a phase-density bound of 2 for e) are each caught by at least one
+largest spacing, a phase-density bound of 2 for e, the RK3 stage weights
+and stage order, the WENO3 left candidate) are each caught by at least one
 check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
 tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
 import concurrent.futures as cf
+import functools
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -167,6 +170,15 @@ MUTANTS = [
     ("phase_bound_factor_two",
      "  const double e = 2.718281828459045;\n  for (int l = 0; l < g->nmat; ++l) {\n    const double r0 = w_rec",
      "  const double e = 2.0;\n  for (int l = 0; l < g->nmat; ++l) {\n    const double r0 = w_rec"),
+    ("rk3_second_stage_weights",
+     "      X2[q] = 0.75 * X0[q] + 0.25 * (X1[q] + dt * x_rhs(g, X1, vel, c, k));",
+     "      X2[q] = 0.5 * X0[q] + 0.5 * (X1[q] + dt * x_rhs(g, X1, vel, c, k));"),
+    ("rk3_last_stage_from_X1",
+     "      Xn[q] = (1.0 / 3.0) * X0[q] + (2.0 / 3.0) * (X2[q] + dt * x_rhs(g, X2, vel, c, k));",
+     "      Xn[q] = (1.0 / 3.0) * X0[q] + (2.0 / 3.0) * (X2[q] + dt * x_rhs(g, X1, vel, c, k));"),
+    ("weno3_left_candidate",
+     "  const double q0 = -0.5 * a + 1.5 * b;",
+     "  const double q0 = 0.5 * a + 0.5 * b;"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
@@ -242,7 +254,8 @@ STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_
               "weno3_weights_swapped", "wave_speed_left_only", "star_speed_traction_sign",
               "star_side_swapped", "momentum_flux_stress_sign", "energy_flux_stress_row",
               "fbar_flux_row", "history_not_advected", "cfl_largest_spacing",
-              "phase_bound_factor_two"}
+              "phase_bound_factor_two", "rk3_second_stage_weights", "rk3_last_stage_from_X1",
+              "weno3_left_candidate"}
 
 
 def _check(name, lib):
@@ -264,11 +277,27 @@ def _check(name, lib):
     return 0, out
 
 
-def test_every_planted_mistake_is_caught():
-    with tempfile.TemporaryDirectory() as tmp:
-        libs = {name: _build(name, old, new, tmp) for name, old, new in MUTANTS}
+@functools.lru_cache(maxsize=None)
+def _results():
+    """Every copy built and checked once, in parallel (the unchanged copy,
+    which runs every check, first)."""
+    tmp = tempfile.mkdtemp(prefix="oracle_mutants_")
+    jobs = [("unchanged", "#include <float.h>", "#include <float.h>")] + MUTANTS
+
+    def run(job):
+        name, old, new = job
+        return name, _check(name, _build(name, old, new, tmp))
+
+    try:
         with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-            res = dict(zip(libs, ex.map(_check, libs, libs.values())))
+            return dict(ex.map(run, jobs))
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+def test_every_planted_mistake_is_caught():
+    res = {k: v for k, v in _results().items() if k != "unchanged"}
+    assert len(res) == len(MUTANTS)
     survived = {k: v[1] for k, v in res.items() if v[0] == 0}
     assert not survived, f"mistakes no pin catches: {survived}"
     for k, (rc, out) in res.items():
@@ -277,7 +306,5 @@ def test_every_planted_mistake_is_caught():
 
 def test_unplanted_copy_passes():
     # the same build route with nothing changed passes every check
-    with tempfile.TemporaryDirectory() as tmp:
-        lib = _build("unchanged", "#include <float.h>", "#include <float.h>", tmp)
-        rc, out = _check("unchanged", lib)
+    rc, out = _results()["unchanged"]
     assert rc == 0, out
