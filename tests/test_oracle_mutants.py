@@ -15,9 +15,11 @@ term dropped, the CFL speed without c_L, the WENO3 weights, the Riemann
 solver's wave speed, star speed and star side, the physical flux's stress
 sign, stress row, Fbar row and history transport, the time step from the
 largest spacing, a phase-density bound of 2 for e, the RK3 stage weights
-and stage order, the WENO3 left candidate) are each caught by at least one
-check of tests/pins_sources.py, tests/pins_step.py, tests/pins_void.py or
-tests/pins_waves.py.  Each copy is compiled to a
+and stage order, the WENO3 left candidate; the fragment labelling's
+periodic faces, cut-off side, critical-damage exclusion, solid-only mass and
+neighbour stride) are each caught by at least one check of
+tests/pins_sources.py, tests/pins_fragments.py, tests/pins_step.py,
+tests/pins_void.py or tests/pins_waves.py.  Each copy is compiled to a
 temporary library and checked in a child process.  CPU only."""
 import concurrent.futures as cf
 import functools
@@ -179,6 +181,22 @@ MUTANTS = [
     ("weno3_left_candidate",
      "  const double q0 = -0.5 * a + 1.5 * b;",
      "  const double q0 = 0.5 * a + 0.5 * b;"),
+    # fragment labelling (pins_fragments.py)
+    ("fragment_periodic_ignored",
+     "            if (g->bc[d][side] != OR_BC_PERIODIC) continue;",
+     "            continue;"),
+    ("fragment_cut_off_side",
+     "  return phis > 1.0 - theta;",
+     "  return phis > theta;"),
+    ("fragment_critical_kept",
+     "      if (is_critical(&g->mat[l], U[(size_t)(g->o_hist + 2 * h + 1) * n + c] / arho)) return 0;",
+     "      if (is_critical(&g->mat[l], U[(size_t)(g->o_hist + 2 * h + 1) * n + c] / arho)) (void)0;"),
+    ("fragment_mass_with_gas",
+     "      for (int l = 0; l < g->nmat; ++l) {\n        if (g->mat[l].eos != 1) continue;\n        const double y",
+     "      for (int l = 0; l < g->nmat; ++l) {\n        const double y"),
+    ("fragment_neighbours_along_x_only",
+     "          const long nb = c + (j - i) * stride;",
+     "          const long nb = c + (j - i);"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
@@ -260,10 +278,12 @@ STEP_FIRST = {"half_step_full_length", "limiter_not_harmonic", "slope_sign_left_
 
 def _check(name, lib):
     # the closure, return, damage and lookup checks first (a second), the
-    # void checks (a second or so), the shear, wall, 3D and totals checks,
+    # fragment checks (a second or two), the void checks (a second or so),
+    # the shear, wall, 3D and totals checks,
     # then the whole-step checks (ten seconds), which go first for a mistake
     # in the sweep
-    mods = ["pins_sources.py", "pins_void.py", "pins_waves.py", "pins_step.py"]
+    mods = ["pins_sources.py", "pins_fragments.py", "pins_void.py", "pins_waves.py",
+            "pins_step.py"]
     if name in STEP_FIRST:
         mods = ["pins_step.py"] + [m for m in mods if m != "pins_step.py"]
     out = ""
