@@ -7,7 +7,9 @@ mass flux and the void's share of the stress, the seeding; the cold and
 shear pressures, the Steinberg modulus and Grueneisen derivative, the
 Hencky strain, the perturbed yield stress, the return factor and
 equivalent stress, the unimodular normalisation, the RK4 weights, the
-Bonora exponent, the rate term, the triaxiality and the lattice weights;
+Bonora exponent, the rate term, the triaxiality and the lattice weights,
+damage in compression, the simple law's 1 - D, the hardening exponent, the
+strength kept at critical damage;
 the mixture's 1/Gamma weights, mass weights, Gamma' term and shear part
 of the sound speed; the half step's length, the limiter, the slope's sign,
 the signs of the non-conservative terms of Fbar, phi and the update, X's
@@ -197,6 +199,19 @@ MUTANTS = [
     ("fragment_neighbours_along_x_only",
      "          const long nb = c + (j - i) * stride;",
      "          const long nb = c + (j - i);"),
+    # damage gate and laws, hardening, strength at critical damage (pins_sources.py)
+    ("damage_in_compression",
+     "  if (!(p < 0.0) || !(eps > thresh)) return 0.0;",
+     "  if (!(eps > thresh)) return 0.0;"),
+    ("simple_damage_without_1_minus_D",
+     "  if (m->damage == 2) return m->Ddot0 * (1.0 - D) * epsdot;",
+     "  if (m->damage == 2) return m->Ddot0 * epsdot;"),
+    ("hardening_exponent_inverted",
+     "      hard += m->c2 * pow(e, m->n_hard);",
+     "      hard += m->c2 * pow(e, 1.0 / m->n_hard);"),
+    ("critical_keeps_strength",
+     "    if (is_critical(m, D[l])) continue;\n    const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;\n    /* advection",
+     "    const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;\n    /* advection"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",
