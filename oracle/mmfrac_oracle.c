@@ -1142,9 +1142,9 @@ double or_lookup(int dim, const float* phi0, const long pn[3],
 /* ------------------------------------------------------------------------ */
 
 /* Triaxiality-dependent threshold plastic strain (Eq. after the gate).
- * Pinned at R_t = 1 only (it reduces to eps_thresh there, and the Bonora
- * closed form runs at R_t = 1): away from R_t = 1 the printed formula is
- * written out with no independent check, parity unpinned there. */
+ * Pinned by two closed forms: it reduces to eps_thresh at R_t = 1, and it
+ * tends to eps_thresh R_t^(-1/(2n)) as eps_crit -> eps_thresh for any R_t
+ * (every power in it enters that limit). */
 double or_eps_thresh(double eps_t, double eps_c, double n, double Rt) {
   const double num = pow(eps_c, 2.0 * n) - pow(eps_t, 2.0 * n);
   const double den = pow(eps_c, 2.0 * n / Rt) - pow(eps_t, 2.0 * n / Rt);

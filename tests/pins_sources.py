@@ -35,6 +35,7 @@ CHECKS = {
     "damage_simple": T.test_simple_damage_matches_closed_form,
     "damage_bonora": T.test_bonora_damage_matches_closed_form_at_unit_triaxiality,
     "threshold_at_unit_triaxiality": T.test_threshold_strain_reduces_to_eps_thresh_at_unit_triaxiality,
+    "threshold_limit": T.test_threshold_strain_in_the_limit_of_equal_strains,
     "triaxiality_forms": T.test_triaxiality_forms_agree_under_log_eos,
     "lookup": lambda: [T.test_lookup_is_multilinear(d) for d in (1, 2, 3)],
 }

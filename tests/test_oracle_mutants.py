@@ -9,7 +9,7 @@ Hencky strain, the perturbed yield stress, the return factor and
 equivalent stress, the unimodular normalisation, the RK4 weights, the
 Bonora exponent, the rate term, the triaxiality and the lattice weights,
 damage in compression, the simple law's 1 - D, the hardening exponent, the
-strength kept at critical damage;
+strength kept at critical damage, four powers of the threshold strain;
 the mixture's 1/Gamma weights, mass weights, Gamma' term and shear part
 of the sound speed; the half step's length, the limiter, the slope's sign,
 the signs of the non-conservative terms of Fbar, phi and the update, X's
@@ -212,6 +212,18 @@ MUTANTS = [
     ("critical_keeps_strength",
      "    if (is_critical(m, D[l])) continue;\n    const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;\n    /* advection",
      "    const double psi = is_damaged(m) ? 1.0 - D[l] : 1.0;\n    /* advection"),
+    ("threshold_Rt_power",
+     "  return pow(eps_t, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));",
+     "  return pow(eps_t, 1.0 / Rt) / pow(Rt, n) * pow(num / den, 1.0 / (2.0 * n));"),
+    ("threshold_eps_power",
+     "  return pow(eps_t, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));",
+     "  return pow(eps_t, Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));"),
+    ("threshold_outer_power",
+     "  return pow(eps_t, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / (2.0 * n));",
+     "  return pow(eps_t, 1.0 / Rt) / pow(Rt, 1.0 / n) * pow(num / den, 1.0 / n);"),
+    ("threshold_den_power",
+     "  const double den = pow(eps_c, 2.0 * n / Rt) - pow(eps_t, 2.0 * n / Rt);",
+     "  const double den = pow(eps_c, 2.0 * n * Rt) - pow(eps_t, 2.0 * n * Rt);"),
     # the mixture rule and sound speed (pins_sources.py)
     ("sound_speed_without_inverse_gamma",
      "    s += (arho[l] / ax->rho) * (1.0 / Gam) * cl2;",

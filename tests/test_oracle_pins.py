@@ -398,6 +398,24 @@ def test_threshold_strain_reduces_to_eps_thresh_at_unit_triaxiality():
         assert lib.or_eps_thresh(et, ec, n, 1.0) == pytest.approx(et, rel=1e-14)
 
 
+def test_threshold_strain_in_the_limit_of_equal_strains():
+    """The triaxiality-dependent threshold strain (Sec. 2.1.1, Eq. for
+    eps_p,thresh) has the limit eps_t R_t^(-1/(2n)) as eps_crit -> eps_thresh
+    (the ratio of the differences of powers tends to the ratio of their
+    derivatives, R_t eps_t^(2n - 2n/R_t)): checked at eps_crit =
+    eps_t (1 + 1e-7) for several R_t and n, and the formula is continuous
+    in eps_crit there."""
+    lib = load()
+    for et in (0.08, 0.002, 0.5):
+        for n in (0.31, 0.42, 0.22):
+            for Rt in (0.5, 0.8, 1.7, 3.0):
+                lim = et * Rt ** (-1.0 / (2.0 * n))
+                v = lib.or_eps_thresh(et, et * (1 + 1e-7), n, Rt)
+                assert v == pytest.approx(lim, rel=1e-6), (et, n, Rt)
+                w = lib.or_eps_thresh(et, et * (1 + 1e-4), n, Rt)
+                assert w == pytest.approx(lim, rel=1e-3)
+
+
 def test_triaxiality_forms_agree_under_log_eos():
     """R_t written with the cold energy (2E rho e_c/sigma^2 + E/(3G), printed
     with the energy release rate) equals the rho0/rho (p/sigma)^2 form when
